@@ -1,0 +1,349 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: numbers the
+paper prints, closed forms for planted signals, identities (Parseval, trace,
+W-orthonormality, reconstruction), independent library routines (numpy FFT,
+LAPACK eigvalsh, scipy windows) and brute force on tiny inputs.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import planted, w_orthonormal_modes
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- sizes
+def test_block_counts_printed_in_paper():
+    with open(os.path.join(HERE, "golden", "paper_block_counts.json")) as fh:
+        cases = json.load(fh)["cases"]
+    for c in cases:
+        assert O.n_blocks(c["nt"], c["nfft"], c["noverlap"]) == c["L"], c["cite"]
+
+
+def test_block_counts_workloads():
+    assert O.n_blocks(2048, 256, 128) == 15
+    assert O.n_blocks(10000, 512, 256) == 38
+    assert O.n_blocks(4096, 256, 128) == 31
+    # tail dropped, blocks from t = 0
+    assert O.n_blocks(300, 100, 0) == 3 and O.n_blocks(299, 100, 0) == 2
+    with pytest.raises(ValueError):
+        O.n_blocks(10, 16, 0)
+    with pytest.raises(ValueError):
+        O.n_blocks(100, 16, 16)
+
+
+def test_one_sided_count():
+    # floor(N/2)+1: for even N this equals the paper's ceil(N/2)+1
+    for n in (2, 6, 256, 512, 720):
+        assert O.n_freqs(n) == math.ceil(n / 2) + 1
+    assert O.n_freqs(15) == 8
+
+
+# ---------------------------------------------------------------- window
+def test_windows_match_scipy():
+    sig = pytest.importorskip("scipy.signal")
+    for n in (6, 15, 256, 384):
+        np.testing.assert_allclose(O.window(O.WIN_HAMMING, n), sig.windows.hamming(n, sym=True), atol=1e-15)
+        np.testing.assert_allclose(O.window(O.WIN_HAMMING_PERIODIC, n), sig.windows.hamming(n, sym=False), atol=1e-15)
+        np.testing.assert_allclose(O.window(O.WIN_HANN, n), sig.windows.hann(n, sym=True), atol=1e-15)
+    assert np.all(O.window(O.WIN_RECT, 7) == 1.0)
+
+
+# ---------------------------------------------------------------- DFT
+@pytest.mark.parametrize("nfft,nov", [(16, 8), (15, 5), (30, 0), (6, 3), (24, 12)])
+def test_direct_dft_matches_numpy_fft(nfft, nov):
+    r = _rng(nfft)
+    nt, M = 3 * nfft + 5, 7
+    X = r.standard_normal((nt, M)) + 2.0
+    w = O.window(O.WIN_HAMMING, nfft)
+    mu = X.mean(axis=0)
+    Qd = O.block_dft(X, nfft, nov, w, mu, method="direct")
+    # independent: numpy FFT of each windowed block, one-sided part
+    step = nfft - nov
+    nb = O.n_blocks(nt, nfft, nov)
+    for l in range(nb):
+        ref = np.fft.fft(w[:, None] * (X[l * step:l * step + nfft] - mu), axis=0)[: nfft // 2 + 1] / w.sum()
+        np.testing.assert_allclose(Qd[:, l, :], ref, atol=1e-13)
+    Qf = O.block_dft(X, nfft, nov, w, mu, method="fft")
+    np.testing.assert_allclose(Qd, Qf, atol=1e-13)
+
+
+def test_dft_bin_centred_sinusoid_amplitude():
+    # a bin-centred sinusoid of amplitude a under the periodic Hamming window gives
+    # |q_hat| = a/2 at its bin (c = 1/sum w, Sec. 2.2 DFT reading)
+    nfft, k, a = 64, 5, 3.0
+    t = np.arange(nfft)
+    X = (a * np.sin(2 * np.pi * k * t / nfft + 0.3))[:, None]
+    Q = O.block_dft(X, nfft, 0, O.window(O.WIN_HAMMING_PERIODIC, nfft), None)
+    assert abs(abs(Q[k, 0, 0]) - a / 2) < 1e-13
+    assert abs(abs(Q[k + 1, 0, 0]) - (a / 2) * 0.23 / 0.54) < 1e-13
+    assert abs(Q[k + 3, 0, 0]) < 1e-13
+
+
+# ---------------------------------------------------------------- eig
+def _rand_herm(r, B, n, rank=None):
+    A = r.standard_normal((B, n, n)) + 1j * r.standard_normal((B, n, n))
+    if rank is not None:
+        A = A[:, :, :rank] @ np.conj(np.transpose(A[:, :, :rank], (0, 2, 1)))
+    else:
+        A = A + np.conj(np.transpose(A, (0, 2, 1)))
+    return A
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 15, 38])
+def test_jacobi_matches_lapack(n):
+    r = _rng(n)
+    A = _rand_herm(r, 5, n)
+    lam, V, sweeps, conv = O.jacobi_eigh(A)
+    assert conv
+    ref = np.linalg.eigvalsh(A)[:, ::-1]
+    np.testing.assert_allclose(lam, ref, atol=1e-12 * np.abs(ref).max())
+    # residual, unitarity, phase rule
+    R = A @ V - V * lam[:, None, :]
+    assert np.abs(R).max() < 1e-11 * np.abs(ref).max()
+    VV = np.conj(np.transpose(V, (0, 2, 1))) @ V
+    np.testing.assert_allclose(VV, np.broadcast_to(np.eye(n), VV.shape), atol=1e-12)
+    idx = np.argmax(np.abs(V), axis=1)
+    piv = np.take_along_axis(V, idx[:, None, :], axis=1)
+    assert np.all(np.abs(piv.imag) < 1e-14) and np.all(piv.real > 0)
+
+
+def test_jacobi_special_cases():
+    D = np.diag([3.0, 1.0, 2.0]).astype(complex)[None]
+    lam, V, sweeps, conv = O.jacobi_eigh(D)
+    assert conv and sweeps == 0
+    np.testing.assert_array_equal(lam[0], [3.0, 2.0, 1.0])
+    # ties keep the lower diagonal index first
+    I = np.eye(4, dtype=complex)[None] * 2.0
+    lam, V, _, _ = O.jacobi_eigh(I)
+    np.testing.assert_array_equal(lam[0], [2.0] * 4)
+    np.testing.assert_array_equal(np.abs(V[0]), np.eye(4))
+    # PSD rank-deficient (the Gram when nb > M)
+    r = _rng(3)
+    A = _rand_herm(r, 2, 6, rank=2)
+    lam, V, _, conv = O.jacobi_eigh(A)
+    assert conv
+    assert np.all(np.abs(lam[:, 2:]) < 1e-12 * lam[:, :1])
+    # zero matrix
+    lam, V, sweeps, conv = O.jacobi_eigh(np.zeros((1, 3, 3), complex))
+    assert conv and np.all(lam == 0)
+
+
+# ---------------------------------------------------------------- whole fit
+def _small_desc(nt=160, M=24, nfft=32, nov=16, window=O.WIN_HAMMING, seed=0, W=None):
+    r = _rng(seed)
+    if W is None:
+        W = 0.5 + r.random(M)
+    return O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, window=window, weights=W)
+
+
+def test_snapshot_method_equals_direct_csd():
+    # Eq. csd-discrete / spod-discrete vs Eq. spod-discrete-snapshots: the M x M
+    # problem C_k W phi = lambda phi and the nb x nb Gram share nonzero eigenvalues;
+    # the oracle's modes solve the M x M problem.
+    d = _small_desc(nt=200, M=12, nfft=32, nov=16)
+    X = _rng(1).standard_normal((d.nt, d.M)) * 1.5 + 0.7
+    fit = O.spod_fit(X, d)
+    nb = d.nb
+    Phi = O.spod_modes(fit, d, nb)
+    W = d.W()
+    for f in (0, 3, d.nf - 1):
+        Qk = fit.Qhat[f].T                                   # M x nb
+        C = Qk @ np.conj(Qk.T) / nb                          # Eq. csd-discrete with 1/nb
+        ev = np.sort(np.linalg.eigvals(C @ np.diag(W)).real)[::-1]
+        r = min(nb, d.M)
+        np.testing.assert_allclose(fit.lam[f, :r], ev[:r], rtol=1e-9, atol=1e-12 * ev[0])
+        for k in range(r):
+            phi = Phi[f, k]
+            res = C @ (W * phi) - fit.lam[f, k] * phi
+            assert np.linalg.norm(res) < 1e-9 * fit.lam[f, 0]
+
+
+@pytest.mark.parametrize("nfft,nov", [(32, 16), (31, 10), (30, 0)])
+def test_parseval_identity(nfft, nov):
+    d = _small_desc(nt=7 * nfft + 3, M=10, nfft=nfft, nov=nov, seed=nfft)
+    X = _rng(nfft + 1).standard_normal((d.nt, d.M)) + 5.0
+    fit = O.spod_fit(X, d)
+    g = O.one_sided_multiplicity(nfft)
+    lhs = float((g * np.trace(fit.M, axis1=1, axis2=2).real).sum())
+    rhs = O.parseval_rhs(X, d)
+    assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+def test_trace_orthonormality_reconstruction():
+    d = _small_desc(nt=180, M=40, nfft=24, nov=12, seed=5)
+    X = _rng(6).standard_normal((d.nt, d.M))
+    fit = O.spod_fit(X, d)
+    tr = np.trace(fit.M, axis1=1, axis2=2).real
+    np.testing.assert_allclose(fit.lam.sum(axis=1), tr, rtol=1e-12)
+    nb = d.nb
+    Phi = O.spod_modes(fit, d, nb)
+    W = d.W()
+    for f in range(d.nf):
+        P = Phi[f].T                                         # M x nb
+        G = np.conj(P.T) @ (W[:, None] * P)
+        np.testing.assert_allclose(G, np.eye(nb), atol=1e-10)  # Sec. 2.2: Phi^* W Phi = I
+        # full-rank reconstruction: sqrt(nb) Phi Lambda^{1/2} Psi^H = Qhat_f
+        Qr = math.sqrt(nb) * (P * np.sqrt(fit.lam[f])[None, :]) @ np.conj(fit.Psi[f].T)
+        np.testing.assert_allclose(Qr, fit.Qhat[f].T, atol=1e-10 * np.abs(fit.Qhat[f]).max())
+
+
+def test_planted_closed_form_periodic_hamming():
+    # Planted W-orthonormal modes x bin-centred sinusoids, periodic Hamming:
+    # lambda_1 = a^2/4 at the planted bin, (a^2/4)(0.23/0.54)^2 at its neighbours,
+    # and 0 elsewhere.  A per-point offset and a tail outside the last block test
+    # the mean subtraction (over all nt) and the block layout.
+    npts, nt, nfft = 64 * 32, 2048 + 77, 256
+    W = torch.tensor(0.5 + _rng(9).random(npts))
+    off = torch.tensor(_rng(10).standard_normal(npts) * 10.0)
+    wl = planted(npts, 1, nt, nfft, nfft // 2, noise_std=0.0, weights=W, seed=4, offset=off)
+    d = O.Desc(nt=nt, M=npts, nfft=nfft, noverlap=nfft // 2, window=O.WIN_HAMMING_PERIODIC,
+               weights=W.numpy())
+    fit = O.spod_fit(wl.X.numpy(), d, dft="fft")
+    r = (0.23 / 0.54) ** 2
+    expect = np.zeros(d.nf)
+    for k, a in zip((10, 25, 60), (3.0, 2.0, 1.0)):
+        expect[k] = a * a / 4
+        expect[k - 1] = expect[k + 1] = a * a / 4 * r
+    # the tail makes the sinusoids' sample mean nonzero: that constant only
+    # reaches bins 0 and 1 through the window, so compare from bin 3 on
+    np.testing.assert_allclose(fit.lam[3:, 0], expect[3:], atol=1e-12)
+    assert np.all(fit.lam[3:, 1] < 1e-12)
+
+
+def test_planted_closed_form_no_tail_all_bins():
+    npts, nt, nfft = 256, 1024, 128
+    wl = planted(npts, 1, nt, nfft, nfft // 2, bins=(3, 17, 40), amps=(1.0, 2.0, 0.5),
+                 noise_std=0.0, seed=8)
+    d = O.Desc(nt=nt, M=npts, nfft=nfft, noverlap=nfft // 2, window=O.WIN_HAMMING_PERIODIC)
+    fit = O.spod_fit(wl.X.numpy(), d)
+    r = (0.23 / 0.54) ** 2
+    expect = np.zeros(d.nf)
+    for k, a in zip((3, 17, 40), (1.0, 2.0, 0.5)):
+        expect[k] = a * a / 4
+        expect[k - 1] = expect[k + 1] = a * a / 4 * r
+    np.testing.assert_allclose(fit.lam[:, 0], expect, atol=1e-12)
+
+
+def test_planted_closed_form_symmetric_hamming():
+    # With the symmetric window the planted part of Qhat_f is
+    #   sum_j phi_j c_j^T,  c_j[l] = (a_j c / 2i) (e^{i th_jl} Wh(f-k_j) - e^{-i th_jl} Wh(f+k_j)),
+    # th_jl = th_j + 2 pi k_j l step / nfft, Wh the window's DFT; with W-orthonormal
+    # phi the nonzero eigenvalues of M_f are those of (1/nb) C C^H (3 x 3).
+    npts, nt, nfft, nov = 512, 2048, 256, 128
+    W = torch.tensor(0.5 + _rng(2).random(npts))
+    wl = planted(npts, 1, nt, nfft, nov, noise_std=0.0, weights=W, seed=3)
+    d = O.Desc(nt=nt, M=npts, nfft=nfft, noverlap=nov, window=O.WIN_HAMMING, weights=W.numpy())
+    fit = O.spod_fit(wl.X.numpy(), d, dft="fft")
+    w = O.window(O.WIN_HAMMING, nfft)
+    c = 1.0 / w.sum()
+    n = np.arange(nfft)
+    step, nb = nfft - nov, d.nb
+
+    def Wh(k):
+        return np.sum(w * np.exp(-2j * np.pi * k * n / nfft))
+
+    th = wl.meta["theta"].numpy()
+    for f in (4, 10, 11, 25, 33, 60, 61, 100):
+        C = np.zeros((3, nb), complex)
+        for j, (k, a) in enumerate(zip(wl.meta["bins"], wl.meta["amps"])):
+            for l in range(nb):
+                thl = th[j] + 2 * np.pi * k * l * step / nfft
+                C[j, l] = a * c / 2j * (np.exp(1j * thl) * Wh(f - k) - np.exp(-1j * thl) * Wh(f + k))
+        ev = np.sort(np.linalg.eigvalsh(C @ np.conj(C.T) / nb))[::-1]
+        np.testing.assert_allclose(fit.lam[f, :3], ev, atol=1e-13 + 1e-11 * ev[0])
+
+
+def test_mean_offset_invariance_and_norm_option():
+    d = _small_desc(nt=150, M=9, nfft=20, nov=10, seed=2)
+    X = _rng(4).standard_normal((d.nt, d.M))
+    a = O.spod_fit(X, d)
+    b = O.spod_fit(X + 100.0 * _rng(5).standard_normal(d.M)[None, :], d)
+    np.testing.assert_allclose(a.lam, b.lam, rtol=1e-9, atol=1e-12 * a.lam.max())
+    # without mean subtraction the DC bin changes
+    d2 = O.Desc(**{**d.__dict__, "subtract_mean": False})
+    c2 = O.spod_fit(X + 100.0, d2)
+    assert c2.lam[0, 0] > 1e3 * a.lam[0, 0]
+    # Bessel normalisation of Eq. csd-discrete scales eigenvalues by nb/(nb-1)
+    d3 = O.Desc(**{**d.__dict__, "norm": O.NORM_NB_MINUS_1})
+    e = O.spod_fit(X, d3)
+    np.testing.assert_allclose(e.lam, a.lam * d.nb / (d.nb - 1), rtol=1e-12, atol=1e-15)
+    P1 = O.spod_modes(a, d, 3)
+    P3 = O.spod_modes(e, d3, 3)
+    np.testing.assert_allclose(P1, P3, atol=1e-12)
+
+
+def test_workload_modes_are_w_orthonormal():
+    W = torch.tensor(0.5 + _rng(1).random(50))
+    phi = w_orthonormal_modes(50, 3, W, 0)
+    G = phi.T @ (W[:, None] * phi)
+    np.testing.assert_allclose(G.numpy(), np.eye(3), atol=1e-13)
+
+
+# ---------------------------------------------------------------- gradient
+def _grad_case(seed=0, nt=96, M=10, nfft=16, nov=8):
+    d = _small_desc(nt=nt, M=M, nfft=nfft, nov=nov, seed=seed)
+    X = _rng(seed + 100).standard_normal((d.nt, d.M)) + 1.0
+    g = _rng(seed + 200).standard_normal((d.nf, d.nb))
+    return d, X, g
+
+
+def test_gradient_matches_finite_differences():
+    d, X, g = _grad_case()
+    fit = O.spod_fit(X, d)
+    gap = np.min(np.abs(np.diff(fit.lam, axis=1)) / fit.lam[:, :1])
+    assert gap > 1e-6        # simple eigenvalues
+    G = O.spod_grad(X, d, g, fit)
+
+    def L(Y):
+        return O.loss_from_fit(O.spod_fit(Y, d), g)
+
+    r = _rng(7)
+    for _ in range(5):
+        V = r.standard_normal(X.shape)
+        eps = 1e-5 * np.linalg.norm(X) / np.linalg.norm(V)
+        fd = (L(X + eps * V) - L(X - eps * V)) / (2 * eps)
+        an = float((G * V).sum())
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_gradient_homogeneity_and_shift():
+    d, X, g = _grad_case(seed=1)
+    fit = O.spod_fit(X, d)
+    G = O.spod_grad(X, d, g, fit)
+    L = O.loss_from_fit(fit, g)
+    # eigenvalues are quadratic in X: <grad L, X> = 2 L
+    assert abs(float((G * X).sum()) - 2 * L) <= 1e-10 * abs(L)
+    # mean subtraction: gradient sums to zero over time at every point
+    assert np.abs(G.sum(axis=0)).max() < 1e-12 * np.abs(G).max() * d.nt
+
+
+def test_gradient_identity_weights_is_time_domain_parseval():
+    # g[f, k] = multiplicity g_f for all k makes G_f = g_f I (full rank), so
+    # L = sum_f g_f tr M_f = parseval_rhs, whose gradient is 2 C w_n^2 W_m xt
+    # overlap-added, then mean-projected.
+    d, X, _ = _grad_case(seed=2, nt=60, M=30, nfft=12, nov=6)
+    assert d.nb <= d.M
+    mult = O.one_sided_multiplicity(d.nfft)
+    g = np.repeat(mult[:, None], d.nb, axis=1)
+    G = O.spod_grad(X, d, g)
+    w = d.w()
+    C = (1.0 / w.sum()) ** 2 * d.nfft / d.nb
+    xt = X - X.mean(axis=0)
+    ref = np.zeros_like(X)
+    step = d.nfft - d.noverlap
+    for l in range(d.nb):
+        ref[l * step:l * step + d.nfft] += 2 * C * (w ** 2)[:, None] * d.W()[None, :] * xt[l * step:l * step + d.nfft]
+    ref -= ref.mean(axis=0)
+    np.testing.assert_allclose(G, ref, atol=1e-12 * np.abs(ref).max())
