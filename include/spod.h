@@ -1,0 +1,227 @@
+/*
+ * spod.h -- C ABI of libspod.so, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of spectral proper orthogonal decomposition (SPOD)
+ * as stated in Rogowski et al., arXiv 2309.11808, Sec. 2.2 ("Practical
+ * implementation"):
+ *
+ *   Welch blocks (Eq. blocks) -> time-mean subtraction -> window ->
+ *   DFT of every block in time (Eq. blocks-ft, regrouped per frequency as in
+ *   Eq. blocks-k) -> weighted Gram  M_f = kappa * Qhat_f^* W Qhat_f
+ *   (Eq. spod-discrete-snapshots) -> Hermitian eigen-decomposition of every
+ *   M_f -> modes Phi_f = Qhat_f Psi_f Lambda_f^{-1/2} / sqrt(1/kappa)
+ *   (Eq. spod-discrete-snapshots; scaled so that Phi_f^* W Phi_f = I, the
+ *   property stated right after that equation).
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - X is real, laid out time-major: X[t][v][p], t < nt, v < nvars,
+ *     p < npoints, row-major; the flattened row index is m = v*npoints + p and
+ *     M = nvars*npoints (Eq. data-matrix stores the transpose, Q in R^{M x Nt}).
+ *   - step = nfft - noverlap; block l covers t in [l*step, l*step + nfft);
+ *     nb = floor((nt - noverlap) / step) (the paper's L); tail samples belong
+ *     to no block but do enter the mean.
+ *   - nf = floor(nfft/2) + 1 one-sided frequencies (real data, Eq. discrete_modes).
+ *   - qhat[f][l][m] = c * sum_n w_n (X[l*step+n][m] - mu_m) exp(-2 pi i f n / nfft),
+ *     c = 1 / sum_n w_n, mu_m the mean over all nt snapshots.
+ *   - kappa = 1/nb (SPOD_NORM_NB) or 1/(nb-1) (SPOD_NORM_NB_MINUS_1, the
+ *     factor printed in Eq. csd-discrete).
+ *   - eigenvalues descending; eigenvectors unit 2-norm, largest-modulus entry
+ *     (lowest index on ties) real positive.
+ *   - modes with lambda_k <= 1e-12 * lambda_1 (or not positive) are returned as zero.
+ *
+ * Ownership: the caller owns every buffer it passes.  A plan owns its device
+ * workspace and private copies of the window and weights.
+ * Streams: every call that takes a `stream` (a cudaStream_t, NULL = legacy
+ * default stream) is enqueued on it and returns without waiting, except the
+ * *_host calls and spod_get_* with on_device = 0, which synchronise the stream.
+ * Errors: every call returns a status; spod_last_error() gives a message for
+ * the calling thread.  Device-side conditions (non-finite input, eigen-solver
+ * not converged) are recorded in the plan and returned by the next call that
+ * synchronises (spod_get_eigs, spod_sync, the *_host calls).
+ * Threads: a plan may be used by one host thread at a time.
+ */
+#ifndef SPOD_H_
+#define SPOD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spod_plan_s* spod_plan_t;
+
+typedef enum {
+  SPOD_OK = 0,
+  SPOD_EINVAL = 1,          /* invalid argument or plan description */
+  SPOD_ENOMEM = 2,          /* device or host allocation failed */
+  SPOD_ECUDA = 3,           /* CUDA runtime error (message in spod_last_error) */
+  SPOD_ESTATE = 4,          /* call order: modes / backward / get_eigs before fit */
+  SPOD_ENANINPUT = 5,       /* X contained NaN or Inf */
+  SPOD_ENOTCONVERGED = 6,   /* eigen-solver hit its iteration cap */
+  SPOD_ETIMEOUT = 7,        /* a bounded device wait gave up */
+  SPOD_EUNSUPPORTED = 8     /* valid request this build does not implement */
+} spod_status;
+
+typedef enum { SPOD_F64 = 0, SPOD_F32 = 1, SPOD_BF16 = 2 } spod_dtype;
+
+/* Arithmetic of the bulk FFT / Gram / mode work.  The time mean is always
+ * accumulated in FP64 and the eigen-decomposition always runs in FP64.
+ *   FP64   : everything in FP64 (input F64 or F32).
+ *   FP32   : FFT, Gram and modes in FP32 SIMT arithmetic; Gram partial sums
+ *            promoted to FP64 every few hundred points.
+ *   BF16   : FFT in FP32; Gram and mode products on the tensor cores from
+ *            BF16-rounded operands, FP32 accumulation.
+ *   BF16X3 : as BF16 but every operand x is split x = hi + lo (hi = bf16(x),
+ *            lo = bf16(x - hi)) and the product is hi*hi + hi*lo + lo*hi. */
+typedef enum {
+  SPOD_PREC_FP64 = 0,
+  SPOD_PREC_FP32 = 1,
+  SPOD_PREC_BF16 = 2,
+  SPOD_PREC_BF16X3 = 3
+} spod_precision;
+
+typedef enum {
+  SPOD_WIN_HAMMING = 0,           /* symmetric: 0.54 - 0.46 cos(2 pi n / (N-1)) (default) */
+  SPOD_WIN_HAMMING_PERIODIC = 1,  /* 0.54 - 0.46 cos(2 pi n / N) */
+  SPOD_WIN_HANN = 2,              /* symmetric: 0.5 - 0.5 cos(2 pi n / (N-1)) */
+  SPOD_WIN_RECT = 3,
+  SPOD_WIN_USER = 4               /* user_window[nfft], copied at plan creation */
+} spod_window;
+
+typedef enum {
+  SPOD_NORM_NB = 0,               /* kappa = 1/nb (default) */
+  SPOD_NORM_NB_MINUS_1 = 1        /* kappa = 1/(nb-1), Eq. csd-discrete */
+} spod_norm;
+
+typedef struct {
+  int ndim;                  /* 1..3: spatial grid rank */
+  int64_t dims[3];           /* grid extents; npoints = prod(dims[0..ndim-1]) */
+  int nvars;                 /* variables per point (M_vars); M = nvars * npoints */
+  int64_t nt;                /* snapshots N_t */
+  int nfft;                  /* block length N_f, 2 <= nfft <= nt, nfft = 2^a 3^b 5^c */
+  int noverlap;              /* 0 <= noverlap < nfft */
+  spod_window window;
+  const double* user_window; /* host [nfft] when window == SPOD_WIN_USER, else ignored */
+  const double* weights;     /* host [M] quadrature weights W (all > 0, finite); NULL = all ones */
+  double dt;                 /* snapshot spacing, used by spod_get_freqs only (> 0) */
+  spod_dtype in_dtype;       /* element type of X */
+  spod_precision precision;
+  spod_norm norm;
+  int subtract_mean;         /* 1 (default): subtract the temporal mean; 0: use X as is */
+  int64_t chunk_points;      /* spatial points per FFT->Gram pass; 0 = automatic.  Bounds
+                                the device workspace (Qhat of one chunk). */
+} spod_plan_desc;
+
+typedef struct {
+  int64_t M;                 /* nvars * npoints */
+  int64_t nt;
+  int nfft, noverlap, step;
+  int nb;                    /* Welch blocks L */
+  int nf;                    /* one-sided frequencies */
+  int device;                /* CUDA device the plan lives on */
+  size_t workspace_bytes;    /* device memory owned by the plan */
+  int64_t chunk_points;      /* spatial points per FFT->Gram pass */
+} spod_plan_info;
+
+/* Fill *desc with defaults (Hamming, 50 % overlap unset = 0, FP32, NORM_NB,
+ * subtract_mean = 1, dt = 1).  Never fails for a non-NULL pointer. */
+spod_status spod_desc_init(spod_plan_desc* desc);
+
+/* Validate desc, copy window and weights, and allocate the plan's device
+ * workspace on the current CUDA device.  Errors: SPOD_EINVAL (bad sizes,
+ * non-positive or non-finite weights, unsupported nfft factorisation ->
+ * SPOD_EUNSUPPORTED), SPOD_ENOMEM, SPOD_ECUDA.  *out is NULL on failure. */
+spod_status spod_plan_create(const spod_plan_desc* desc, spod_plan_t* out);
+
+/* Free the plan and its workspace (device-synchronising).  NULL is a no-op. */
+spod_status spod_plan_destroy(spod_plan_t plan);
+
+spod_status spod_plan_get_info(spod_plan_t plan, spod_plan_info* info);
+
+/* Mean, blocks, window, batched FFT, weighted Gram, deterministic reduction and
+ * batched Hermitian eigen-decomposition (Sec. 2.2, Eqs. blocks to
+ * spod-discrete-snapshots).  d_X: device pointer to X[nt][M] of in_dtype,
+ * 16-byte aligned.  Results stay in the plan (see spod_get_eigs).  Stream-ordered. */
+spod_status spod_fit(spod_plan_t plan, const void* d_X, void* stream);
+
+/* Copy the eigenvalues lambda[nf][nb] (FP64, descending per frequency) and,
+ * when psi != NULL, the eigenvectors psi[nf][nb (entry)][nb (vector)] as
+ * interleaved complex FP64 (column k of psi[f] is the k-th eigenvector).
+ * on_device = 1: both pointers are device memory, the copy is enqueued on
+ * the stream of the last fit and the call does not wait.  on_device = 0: host
+ * memory; the call synchronises and also reports device-side conditions
+ * (SPOD_ENANINPUT, SPOD_ENOTCONVERGED).  SPOD_ESTATE before a fit. */
+spod_status spod_get_eigs(spod_plan_t plan, double* lambda, double* psi, int on_device);
+
+/* Copy the weighted Gram matrices M_f [nf][nb][nb] (interleaved complex
+ * FP64, kappa applied) to host memory; synchronising.  SPOD_ESTATE before a fit. */
+spod_status spod_get_gram(spod_plan_t plan, double* gram);
+
+/* Frequencies f / (nfft * dt), f = 0 .. nf-1, into host memory. */
+spod_status spod_get_freqs(spod_plan_t plan, double* freqs);
+
+/* SPOD modes of the last fit (Eq. spod-discrete-snapshots): recomputes Qhat
+ * from d_X (which must hold the same data as the fit) and writes
+ * Phi[f][k][m] = sum_l qhat[f][l][m] psi_f[l][k] / sqrt(lambda_k,f / kappa)
+ * for k < nmodes (1 <= nmodes <= nb), as interleaved complex FP32 (precision
+ * FP32/BF16/BF16X3) or FP64 (precision FP64).  d_Phi: device, nf*nmodes*M
+ * complex elements, 16-byte aligned.  SPOD_ESTATE before a fit. */
+spod_status spod_modes(spod_plan_t plan, const void* d_X, int nmodes, void* d_Phi, void* stream);
+
+/* Adjoint of the fit for losses on eigenvalues: given d_dLdlambda[nf][nb]
+ * (device FP64) writes dL/dX [nt][M] (device, FP32 for precision
+ * FP32/BF16/BF16X3, FP64 for FP64).  Valid for simple eigenvalues: with
+ * G_f = sum_k g_fk psi psi^H and R_f = 2 kappa W Qhat_f G_f,
+ * dL/dxt[l*step+n][m] += c w_n Re(sum_f R_f[m][l] e^{+2 pi i f n/nfft})
+ * (overlap-add over blocks), then the mean projection.  Qhat is recomputed
+ * from d_X.  SPOD_ESTATE before a fit. */
+spod_status spod_backward(spod_plan_t plan, const double* d_dLdlambda, const void* d_X,
+                          void* d_dX, void* stream);
+
+/* End-to-end call on HOST buffers: copies h_X to the device, fits, computes
+ * nmodes modes (0 = none) and copies eigenvalues (h_lambda[nf][nb], may be
+ * NULL) and modes (h_Phi, layout as spod_modes, may be NULL when nmodes = 0)
+ * back.  Device staging buffers are owned by the plan and kept for reuse.
+ * Pinned host memory gives the fastest copies.  Synchronises the stream. */
+spod_status spod_run_host(spod_plan_t plan, const void* h_X, int nmodes, void* h_Phi,
+                          double* h_lambda, void* stream);
+
+/* Wait for the plan's work on `stream` and report device-side conditions. */
+spod_status spod_sync(spod_plan_t plan, void* stream);
+
+/* Fit n plans on n inputs with one CUDA-graph launch (datasets of different
+ * grid size, nt and nfft).  Equivalent to n spod_fit calls.  */
+spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream);
+
+/* Phases of the hot path, for per-phase timing. */
+typedef enum {
+  SPOD_PHASE_MEAN = 0,     /* time mean */
+  SPOD_PHASE_FFT = 1,      /* blocks, window, batched DFT */
+  SPOD_PHASE_GRAM = 2,     /* weighted Gram partial sums */
+  SPOD_PHASE_REDUCE = 3,   /* fixed-order reduction of the partial Grams */
+  SPOD_PHASE_EIG = 4,      /* batched Hermitian eigen-decomposition */
+  SPOD_PHASE_MODES = 5,    /* mode coefficients and mode reconstruction */
+  SPOD_PHASE_BACKWARD = 6, /* adjoint kernels */
+  SPOD_NPHASES = 7
+} spod_phase;
+
+/* Per-phase timing (the paper reports per-phase wall times, Sec. 5.1): when
+ * enabled, every phase a call enqueues is bracketed by CUDA events recorded on
+ * that call's stream.  spod_profile_read synchronises on the recorded events,
+ * writes the summed milliseconds (ms[SPOD_NPHASES], may be NULL) and the number
+ * of kernels launched (launches[SPOD_NPHASES], may be NULL, counted whether or
+ * not timing is enabled) since the previous read, and resets both. */
+spod_status spod_profile_enable(spod_plan_t plan, int enable);
+spod_status spod_profile_read(spod_plan_t plan, double* ms, int64_t* launches);
+
+/* Thread-local message describing the last non-OK status. */
+const char* spod_last_error(void);
+
+/* Library version string. */
+const char* spod_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPOD_H_ */

@@ -1,0 +1,334 @@
+// Time mean (Sec. 2.2) and the batched windowed block DFT (Eqs. blocks,
+// blocks-ft, blocks-k) of the SPOD hot path.
+//
+// Mean: FP64 accumulation of FP32 runs of 16 samples (FP64 throughout for FP64
+// input), time axis split over grid.y, then a fixed-order FP64 sum.
+//
+// FFT: one CTA per (Welch block l, tile of TP spatial points).  Two real point
+// series are packed into one complex sequence (z = x_even + i x_odd), the
+// tile's TP/2 sequences are transformed together by a shared-memory Stockham
+// FFT of mixed radix 8/4/2/3/5, and the two real spectra are separated at the
+// end.  The mean is subtracted as a double-float pair, the window carries
+// c = 1/sum(w), and sqrt(W_m) is folded into the output so that the Gram is a
+// plain Qhat^H Qhat.  Output: Qhat[f][row][m_local], row = l (real part) or
+// nb + l (imaginary part), f = 0 .. nfft/2.
+#include "spod_internal.cuh"
+
+namespace spod {
+namespace {
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename R> __device__ __forceinline__ typename C2<R>::T mk(R x, R y) {
+  typename C2<R>::T v; v.x = x; v.y = y; return v;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// multiply by -i
+template <typename V> __device__ __forceinline__ V mul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
+template <typename V, typename R> __device__ __forceinline__ V cscale(V a, R s) { a.x *= s; a.y *= s; return a; }
+
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_f32<double>(double v) { return (float)v; }
+
+template <typename T> __device__ __forceinline__ double to_f64(T v) { return (double)to_f32<T>(v); }
+template <> __device__ __forceinline__ double to_f64<double>(double v) { return v; }
+
+// ---------------------------------------------------------------- mean
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_mean_partial(const Tin* __restrict__ X, int64_t M, int64_t nt,
+                                                      int64_t tper, double* __restrict__ part) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int64_t t0 = (int64_t)blockIdx.y * tper;
+  const int64_t t1 = min(nt, t0 + tper);
+  double acc = 0.0;
+  const Tin* p = X + t0 * M + m;
+  int64_t t = t0;
+  if constexpr (sizeof(Tin) == 8) {
+    for (; t < t1; ++t, p += M) acc += (double)(*p);
+  } else {
+    for (; t + 16 <= t1; t += 16) {
+      float r = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) r += to_f32<Tin>(p[i * M]);
+      acc += (double)r;
+      p += 16 * M;
+    }
+    for (; t < t1; ++t, p += M) acc += (double)to_f32<Tin>(*p);
+  }
+  part[(int64_t)blockIdx.y * M + m] = acc;
+}
+
+__global__ void k_mean_finish(const double* __restrict__ part, int splits, int64_t M, double inv_nt,
+                              double* __restrict__ mu) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double s = 0.0;
+  for (int i = 0; i < splits; ++i) s += part[(int64_t)i * M + m];
+  mu[m] = s * inv_nt;
+}
+
+// ---------------------------------------------------------------- FFT
+struct FftArgs {
+  int64_t M, m0, mcount, chunk;   // chunk = row stride of Qhat (points per chunk)
+  int nfft, step, nb, nf;
+  int subtract_mean;
+  FftPlan fp;
+};
+
+// R-point forward DFT in place, X_r = sum_q v_q exp(-2 pi i r q / R).
+template <int RAD, typename V, typename R>
+__device__ __forceinline__ void dft_small(V* v) {
+  if constexpr (RAD == 2) {
+    V a = v[0];
+    v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]);
+  } else if constexpr (RAD == 3) {
+    const R h = (R)0.86602540378443864676;   // sin(2 pi / 3)
+    V s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    V m = mk<R>(v[0].x - (R)0.5 * s.x, v[0].y - (R)0.5 * s.y);
+    V jd = mk<R>(h * d.y, -h * d.x);        // -i h d
+    v[0] = cadd(v[0], s);
+    v[1] = cadd(m, jd);
+    v[2] = csub(m, jd);
+  } else if constexpr (RAD == 4) {
+    V a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    V c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    v[0] = cadd(a, c); v[2] = csub(a, c);
+    v[1] = cadd(b, mul_mi(d)); v[3] = csub(b, mul_mi(d));
+  } else if constexpr (RAD == 5) {
+    const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
+    const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;
+    V a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    V a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    V p1 = mk<R>(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+    V p2 = mk<R>(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+    V q1 = mk<R>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);   // X1 = p1 - i q1
+    V q2 = mk<R>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);   // X2 = p2 - i q2
+    v[0] = cadd(v[0], cadd(a1, a2));
+    v[1] = cadd(p1, mul_mi(q1)); v[4] = csub(p1, mul_mi(q1));
+    v[2] = cadd(p2, mul_mi(q2)); v[3] = csub(p2, mul_mi(q2));
+  } else if constexpr (RAD == 8) {
+    const R r2 = (R)0.70710678118654752440;
+    V a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { a[q] = cadd(v[q], v[q + 4]); b[q] = csub(v[q], v[q + 4]); }
+    // b_q *= exp(-2 pi i q / 8)
+    b[1] = mk<R>(r2 * (b[1].x + b[1].y), r2 * (b[1].y - b[1].x));
+    b[2] = mul_mi(b[2]);
+    b[3] = mk<R>(r2 * (b[3].y - b[3].x), -r2 * (b[3].x + b[3].y));
+    dft_small<4, V, R>(a);
+    dft_small<4, V, R>(b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { v[2 * k] = a[k]; v[2 * k + 1] = b[k]; }
+  }
+}
+
+// One Stockham pass of radix RAD over `cols` interleaved sequences of length n.
+template <int RAD, typename V, typename R>
+__device__ __forceinline__ void stockham_pass(const V* __restrict__ src, V* __restrict__ dst,
+                                              const V* __restrict__ tw, int n, int cols, int Ns) {
+  const int nbut = n / RAD;
+  const int stride_tw = n / (Ns * RAD);
+  for (int idx = threadIdx.x; idx < nbut * cols; idx += blockDim.x) {
+    const int b = idx / cols, col = idx - b * cols;
+    V v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = src[(b + r * nbut) * cols + col];
+    const int k = b % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[r * k * stride_tw]);
+    }
+    dft_small<RAD, V, R>(v);
+    const int base = (b / Ns) * Ns * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) dst[(base + r * Ns) * cols + col] = v[r];
+  }
+}
+
+template <typename Tin, typename R, int TP>
+__global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R* __restrict__ win,
+                                             const typename C2<R>::T* __restrict__ tw_g,
+                                             const R* __restrict__ sqrtW, const double* __restrict__ mu,
+                                             R* __restrict__ qhat, FftArgs a) {
+  using V = typename C2<R>::T;
+  constexpr int C = TP / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* bufA = reinterpret_cast<V*>(smem_raw);
+  V* bufB = bufA + (size_t)a.nfft * C;
+  V* tw = bufB + (size_t)a.nfft * C;
+  const int N = a.nfft;
+
+  const int64_t ntiles = (a.mcount + TP - 1) / TP;
+  const int64_t item = blockIdx.x;
+  const int l = (int)(item % a.nb);
+  const int64_t tile = item / a.nb;
+  if (tile >= ntiles) return;
+  const int64_t lm0 = tile * TP;          // local (chunk) point index
+  const int64_t gm0 = a.m0 + lm0;         // global point index
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
+
+  // load block l, subtract the mean, apply c*w_n; columns pack points (2j, 2j+1)
+  const int64_t tbase = (int64_t)l * a.step;
+  for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+    const int n = idx / C, j = idx - n * C;
+    const int64_t m = gm0 + 2 * j;
+    const Tin* row = X + (tbase + n) * a.M;
+    R x0 = 0, x1 = 0;
+    if (m < a.m0 + a.mcount && m < a.M) {
+      if constexpr (sizeof(R) == 8) {
+        x0 = (R)to_f64<Tin>(row[m]);
+        if (a.subtract_mean) x0 -= (R)mu[m];
+      } else {
+        x0 = to_f32<Tin>(row[m]);
+        if (a.subtract_mean) {
+          const double mm = mu[m];
+          const float hi = (float)mm, lo = (float)(mm - (double)hi);
+          x0 = (x0 - hi) - lo;
+        }
+      }
+    }
+    if (m + 1 < a.m0 + a.mcount && m + 1 < a.M) {
+      if constexpr (sizeof(R) == 8) {
+        x1 = (R)to_f64<Tin>(row[m + 1]);
+        if (a.subtract_mean) x1 -= (R)mu[m + 1];
+      } else {
+        x1 = to_f32<Tin>(row[m + 1]);
+        if (a.subtract_mean) {
+          const double mm = mu[m + 1];
+          const float hi = (float)mm, lo = (float)(mm - (double)hi);
+          x1 = (x1 - hi) - lo;
+        }
+      }
+    }
+    const R wn = win[n];
+    bufA[idx] = mk<R>(x0 * wn, x1 * wn);
+  }
+  __syncthreads();
+
+  V* src = bufA;
+  V* dst = bufB;
+  int Ns = 1;
+  for (int ps = 0; ps < a.fp.npass; ++ps) {
+    const int rad = a.fp.radix[ps];
+    switch (rad) {
+      case 8: stockham_pass<8, V, R>(src, dst, tw, N, C, Ns); break;
+      case 4: stockham_pass<4, V, R>(src, dst, tw, N, C, Ns); break;
+      case 2: stockham_pass<2, V, R>(src, dst, tw, N, C, Ns); break;
+      case 3: stockham_pass<3, V, R>(src, dst, tw, N, C, Ns); break;
+      default: stockham_pass<5, V, R>(src, dst, tw, N, C, Ns); break;
+    }
+    Ns *= rad;
+    __syncthreads();
+    V* t = src; src = dst; dst = t;
+  }
+
+  // separate the two real spectra, fold sqrt(W), store planar re/im rows
+  const int64_t rs = a.chunk;
+  for (int idx = threadIdx.x; idx < a.nf * TP; idx += blockDim.x) {
+    const int f = idx / TP, p = idx - f * TP;
+    const int64_t lm = lm0 + p;
+    if (lm >= a.mcount) continue;
+    const int col = p >> 1;
+    const V zf = src[f * C + col];
+    const int fn = (f == 0) ? 0 : N - f;
+    const V zc = src[fn * C + col];
+    R re, im;
+    if ((p & 1) == 0) {          // (Z[f] + conj Z[N-f]) / 2
+      re = (R)0.5 * (zf.x + zc.x);
+      im = (R)0.5 * (zf.y - zc.y);
+    } else {                     // (Z[f] - conj Z[N-f]) / (2i)
+      re = (R)0.5 * (zf.y + zc.y);
+      im = (R)-0.5 * (zf.x - zc.x);
+    }
+    const R sw = sqrtW[gm0 + p];
+    R* q = qhat + ((int64_t)f * 2 * a.nb + l) * rs + lm;
+    q[0] = re * sw;
+    q[(int64_t)a.nb * rs] = im * sw;
+  }
+}
+
+template <typename Tin, typename R>
+cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
+  constexpr int TP = 16;
+  FftArgs a;
+  a.M = p.M; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
+  a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;
+  a.subtract_mean = p.desc.subtract_mean;
+  a.fp = p.fft;
+  const size_t smem = fft_smem_bytes(p);
+  auto kern = k_fft<Tin, R, TP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (mcount + TP - 1) / TP;
+  const int64_t grid = ntiles * p.nb;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  kern<<<(unsigned)grid, 256, smem, s>>>(
+      static_cast<const Tin*>(d_X), static_cast<const R*>(p.d_win),
+      static_cast<const typename C2<R>::T*>(p.d_tw), static_cast<const R*>(p.d_sqrtW), p.d_mu,
+      static_cast<R*>(p.d_qhat), a);
+  return cudaGetLastError();
+}
+
+template <typename Tin>
+cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, cudaStream_t s) {
+  const int64_t tper = (p.nt + p.mean_splits - 1) / p.mean_splits;
+  dim3 grid((unsigned)((p.M + 255) / 256), (unsigned)p.mean_splits);
+  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), p.M, p.nt, tper, p.d_mupart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_mean_finish<<<(unsigned)((p.M + 255) / 256), 256, 0, s>>>(p.d_mupart, p.mean_splits, p.M,
+                                                               1.0 / (double)p.nt, p.d_mu);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t fft_smem_bytes(const spod_plan_s& p) {
+  const size_t vb = p.f64 ? 16 : 8;
+  const size_t C = 16 / 2;
+  return vb * ((size_t)p.nfft * C * 2 + (size_t)p.nfft);
+}
+
+cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, cudaStream_t s) {
+  switch (p.desc.in_dtype) {
+    case SPOD_F64: return launch_mean_t<double>(p, d_X, s);
+    case SPOD_F32: return launch_mean_t<float>(p, d_X, s);
+    default: return launch_mean_t<__nv_bfloat16>(p, d_X, s);
+  }
+}
+
+cudaError_t launch_fft_chunk(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount,
+                             cudaStream_t s) {
+  if (p.f64) {
+    if (p.desc.in_dtype == SPOD_F64) return launch_fft_t<double, double>(p, d_X, m0, mcount, s);
+    if (p.desc.in_dtype == SPOD_F32) return launch_fft_t<float, double>(p, d_X, m0, mcount, s);
+    return launch_fft_t<__nv_bfloat16, double>(p, d_X, m0, mcount, s);
+  }
+  if (p.desc.in_dtype == SPOD_F64) return launch_fft_t<double, float>(p, d_X, m0, mcount, s);
+  if (p.desc.in_dtype == SPOD_F32) return launch_fft_t<float, float>(p, d_X, m0, mcount, s);
+  return launch_fft_t<__nv_bfloat16, float>(p, d_X, m0, mcount, s);
+}
+
+bool make_fft_plan(int n, FftPlan* fp) {
+  fp->n = n;
+  fp->npass = 0;
+  int r = n;
+  while (r % 8 == 0 && fp->npass < kMaxRadixPasses) { fp->radix[fp->npass++] = 8; r /= 8; }
+  while (r % 4 == 0 && fp->npass < kMaxRadixPasses) { fp->radix[fp->npass++] = 4; r /= 4; }
+  while (r % 2 == 0 && fp->npass < kMaxRadixPasses) { fp->radix[fp->npass++] = 2; r /= 2; }
+  while (r % 3 == 0 && fp->npass < kMaxRadixPasses) { fp->radix[fp->npass++] = 3; r /= 3; }
+  while (r % 5 == 0 && fp->npass < kMaxRadixPasses) { fp->radix[fp->npass++] = 5; r /= 5; }
+  return r == 1;
+}
+
+}  // namespace spod

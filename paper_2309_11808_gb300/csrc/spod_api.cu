@@ -1,0 +1,563 @@
+// C ABI of libspod.so: plan validation, workspace layout and the entry points
+// declared in include/spod.h.  Every step of the path runs in the kernels of
+// this library; this file only validates, allocates and enqueues.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "spod_internal.cuh"
+
+namespace spod {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+spod_status fail(spod_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+spod_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SPOD_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define SPOD_CUDA(call, where)                 \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::vector<double> make_window(const spod_plan_desc& d) {
+  const int N = d.nfft;
+  std::vector<double> w(N, 1.0);
+  const double pi = 3.14159265358979323846;
+  for (int n = 0; n < N; ++n) {
+    switch (d.window) {
+      case SPOD_WIN_HAMMING: w[n] = N > 1 ? 0.54 - 0.46 * std::cos(2.0 * pi * n / (N - 1)) : 1.0; break;
+      case SPOD_WIN_HAMMING_PERIODIC: w[n] = 0.54 - 0.46 * std::cos(2.0 * pi * n / N); break;
+      case SPOD_WIN_HANN: w[n] = N > 1 ? 0.5 - 0.5 * std::cos(2.0 * pi * n / (N - 1)) : 1.0; break;
+      case SPOD_WIN_RECT: w[n] = 1.0; break;
+      case SPOD_WIN_USER: w[n] = d.user_window[n]; break;
+    }
+  }
+  return w;
+}
+
+size_t elem_bytes(spod_dtype t) { return t == SPOD_F64 ? 8 : (t == SPOD_F32 ? 4 : 2); }
+
+spod_status check_plan(spod_plan_t p) {
+  if (!p) return fail(SPOD_EINVAL, "plan is NULL");
+  return SPOD_OK;
+}
+
+spod_status read_flags(spod_plan_t p) {
+  unsigned h[4] = {0, 0, 0, 0};
+  SPOD_CUDA(cudaMemcpy(h, p->d_flags, sizeof(h), cudaMemcpyDeviceToHost), "read device flags");
+  if (h[0] & FLAG_TIMEOUT) return fail(SPOD_ETIMEOUT, "a bounded device wait gave up");
+  if (h[0] & FLAG_NAN) return fail(SPOD_ENANINPUT, "non-finite values in X (Gram diagonal not finite)");
+  if (h[0] & FLAG_NOTCONV) return fail(SPOD_ENOTCONVERGED, "eigen-solver reached its sweep cap");
+  return SPOD_OK;
+}
+
+cudaEvent_t take_event(spod_plan_s* p) {
+  if (!p->ev_free.empty()) {
+    cudaEvent_t e = p->ev_free.back();
+    p->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Bracket one phase of a call with events on its stream (when profiling).
+struct Phase {
+  spod_plan_s* p;
+  int ph;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int n;
+  Phase(spod_plan_s* p_, int ph_, cudaStream_t s_, int nlaunch) : p(p_), ph(ph_), s(s_), n(nlaunch) {
+    if (p->prof) {
+      a = take_event(p);
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~Phase() {
+    p->launches[ph] += n;
+    if (a) {
+      cudaEvent_t b = take_event(p);
+      if (b) {
+        cudaEventRecord(b, s);
+        p->recs.push_back({ph, a, b});
+      } else {
+        p->ev_free.push_back(a);
+      }
+    }
+  }
+};
+
+}  // namespace
+}  // namespace spod
+
+using namespace spod;
+
+extern "C" {
+
+const char* spod_last_error(void) { return g_err.c_str(); }
+
+const char* spod_version(void) { return "spod-gb300 0.1 (sm_103a)"; }
+
+spod_status spod_desc_init(spod_plan_desc* d) {
+  if (!d) return fail(SPOD_EINVAL, "desc is NULL");
+  std::memset(d, 0, sizeof(*d));
+  d->ndim = 1;
+  d->dims[0] = 1;
+  d->dims[1] = 1;
+  d->dims[2] = 1;
+  d->nvars = 1;
+  d->window = SPOD_WIN_HAMMING;
+  d->dt = 1.0;
+  d->in_dtype = SPOD_F32;
+  d->precision = SPOD_PREC_FP32;
+  d->norm = SPOD_NORM_NB;
+  d->subtract_mean = 1;
+  d->chunk_points = 0;
+  return SPOD_OK;
+}
+
+spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
+  if (!out) return fail(SPOD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(SPOD_EINVAL, "desc is NULL");
+  if (d->ndim < 1 || d->ndim > 3) return fail(SPOD_EINVAL, "ndim must be 1..3");
+  int64_t npoints = 1;
+  for (int i = 0; i < d->ndim; ++i) {
+    if (d->dims[i] <= 0) return fail(SPOD_EINVAL, "dims must be positive");
+    if (npoints > (int64_t(1) << 40) / d->dims[i]) return fail(SPOD_EINVAL, "grid too large");
+    npoints *= d->dims[i];
+  }
+  if (d->nvars < 1) return fail(SPOD_EINVAL, "nvars must be >= 1");
+  const int64_t M = npoints * d->nvars;
+  if (d->nfft < 2) return fail(SPOD_EINVAL, "nfft must be >= 2");
+  if (d->noverlap < 0 || d->noverlap >= d->nfft) return fail(SPOD_EINVAL, "need 0 <= noverlap < nfft");
+  if (d->nt < d->nfft) return fail(SPOD_EINVAL, "need nfft <= nt");
+  if (d->in_dtype != SPOD_F64 && d->in_dtype != SPOD_F32 && d->in_dtype != SPOD_BF16)
+    return fail(SPOD_EINVAL, "unknown in_dtype");
+  if (d->precision < SPOD_PREC_FP64 || d->precision > SPOD_PREC_BF16X3) return fail(SPOD_EINVAL, "unknown precision");
+  if (d->norm != SPOD_NORM_NB && d->norm != SPOD_NORM_NB_MINUS_1) return fail(SPOD_EINVAL, "unknown norm");
+  if (d->window < SPOD_WIN_HAMMING || d->window > SPOD_WIN_USER) return fail(SPOD_EINVAL, "unknown window");
+  if (d->window == SPOD_WIN_USER && !d->user_window) return fail(SPOD_EINVAL, "user_window is NULL");
+  if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(SPOD_EINVAL, "dt must be positive and finite");
+  if (d->chunk_points < 0) return fail(SPOD_EINVAL, "chunk_points must be >= 0");
+  if (d->precision == SPOD_PREC_BF16 || d->precision == SPOD_PREC_BF16X3)
+    return fail(SPOD_EUNSUPPORTED, "tensor-core precisions are not built in this library version");
+
+  spod_plan_s* p = new (std::nothrow) spod_plan_s();
+  if (!p) return fail(SPOD_ENOMEM, "host allocation failed");
+  p->desc = *d;
+  p->desc.user_window = nullptr;
+  p->desc.weights = nullptr;
+  p->npoints = npoints;
+  p->M = M;
+  p->nvars = d->nvars;
+  p->nt = d->nt;
+  p->nfft = d->nfft;
+  p->noverlap = d->noverlap;
+  p->step = d->nfft - d->noverlap;
+  p->nb = (int)((d->nt - d->noverlap) / p->step);
+  p->nf = d->nfft / 2 + 1;
+  p->f64 = d->precision == SPOD_PREC_FP64;
+  auto bail = [&](spod_status st, const std::string& m) {
+    spod_plan_destroy(p);
+    return fail(st, m);
+  };
+  if (p->nb < 1) return bail(SPOD_EINVAL, "no complete block");
+  if (d->norm == SPOD_NORM_NB_MINUS_1 && p->nb < 2) return bail(SPOD_EINVAL, "nb-1 normalisation needs nb >= 2");
+  if (p->nb > 256) return bail(SPOD_EUNSUPPORTED, "nb > 256 blocks is not supported");
+  if (!make_fft_plan(d->nfft, &p->fft)) return bail(SPOD_EUNSUPPORTED, "nfft must factor into 2, 3 and 5");
+  p->kappa = 1.0 / (d->norm == SPOD_NORM_NB ? (double)p->nb : (double)(p->nb - 1));
+
+  p->w = make_window(*d);
+  double sw = 0.0;
+  for (double v : p->w) {
+    if (!std::isfinite(v)) return bail(SPOD_EINVAL, "window has non-finite entries");
+    sw += v;
+  }
+  if (!(std::fabs(sw) > 0.0)) return bail(SPOD_EINVAL, "window sums to zero");
+  p->c = 1.0 / sw;
+  p->W.assign(M, 1.0);
+  if (d->weights) {
+    for (int64_t m = 0; m < M; ++m) {
+      const double v = d->weights[m];
+      if (!(v > 0.0) || !std::isfinite(v)) return bail(SPOD_EINVAL, "weights must be positive and finite");
+      p->W[m] = v;
+    }
+  }
+
+  if (cudaGetDevice(&p->device) != cudaSuccess) return bail(SPOD_ECUDA, "no CUDA device");
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return bail(SPOD_ECUDA, "device query failed");
+  if (fft_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
+    return bail(SPOD_EUNSUPPORTED, "nfft too large for the shared-memory FFT");
+
+  // ---- sizes of the workspace
+  const size_t R = p->f64 ? 8 : 4;
+  const int64_t tile = 64;
+  const size_t per_point = (size_t)p->nf * 2 * p->nb * R;
+  int64_t chunk = d->chunk_points;
+  if (chunk == 0) {
+    const size_t budget = (size_t)40 << 30;   // whole-array Qhat up to 40 GiB, else spatial chunks
+    chunk = (int64_t)std::min<size_t>((size_t)M, std::max<size_t>(budget / per_point, tile));
+  }
+  chunk = std::min<int64_t>(chunk, M);
+  chunk = ((chunk + tile - 1) / tile) * tile;
+  p->chunk_points = chunk;
+  p->Mpad = ((M + tile - 1) / tile) * tile;
+  {
+    const int64_t ctas = (M + 255) / 256;
+    int64_t sp = (1216 + ctas - 1) / ctas;
+    sp = std::max<int64_t>(1, std::min<int64_t>(sp, p->nt / 16 > 0 ? p->nt / 16 : 1));
+    p->mean_splits = (int)std::min<int64_t>(sp, 4096);
+  }
+  {
+    int64_t s = (2048 + p->nf - 1) / p->nf;
+    s = std::max<int64_t>(1, std::min<int64_t>(s, (chunk + 255) / 256));
+    p->gram_splits = (int)s;
+  }
+  const int nb = p->nb, nf = p->nf;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_flags = carve(4 * sizeof(unsigned));
+  const size_t o_mu = carve(sizeof(double) * M);
+  const size_t o_mupart = carve(sizeof(double) * M * p->mean_splits);
+  const size_t o_win = carve(R * p->nfft);
+  const size_t o_tw = carve(2 * R * p->nfft);
+  const size_t o_sqrtW = carve(R * p->Mpad);
+  const size_t o_rsqrtW = carve(R * p->Mpad);
+  const size_t o_gpart = carve(sizeof(double) * 2 * (size_t)p->gram_splits * nf * nb * nb);
+  const size_t o_gram = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
+  const size_t o_lam = carve(sizeof(double) * (size_t)nf * nb);
+  const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
+  const size_t o_eigws = nb > kEigSmemMaxNb ? carve(sizeof(double) * 4 * (size_t)nf * nb * nb) : 0;
+  const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
+  const size_t o_qhat = carve(per_point * (size_t)chunk);
+  p->ws.bytes = off;
+  {
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaMalloc(&p->ws.base, p->ws.bytes);
+    if (e != cudaSuccess) {
+      p->ws.base = nullptr;
+      cudaGetLastError();
+      return bail(SPOD_ENOMEM, "device workspace allocation failed (" + std::to_string(p->ws.bytes) + " bytes)");
+    }
+  }
+  char* b = static_cast<char*>(p->ws.base);
+  p->d_flags = reinterpret_cast<unsigned*>(b + o_flags);
+  p->d_mu = reinterpret_cast<double*>(b + o_mu);
+  p->d_mupart = reinterpret_cast<double*>(b + o_mupart);
+  p->d_win = b + o_win;
+  p->d_tw = b + o_tw;
+  p->d_sqrtW = b + o_sqrtW;
+  p->d_rsqrtW = b + o_rsqrtW;
+  p->d_gpart = reinterpret_cast<double*>(b + o_gpart);
+  p->d_gram = reinterpret_cast<double*>(b + o_gram);
+  p->d_lam = reinterpret_cast<double*>(b + o_lam);
+  p->d_psi = reinterpret_cast<double*>(b + o_psi);
+  p->d_eigws = nb > kEigSmemMaxNb ? reinterpret_cast<double*>(b + o_eigws) : nullptr;
+  p->d_bmat = b + o_bmat;
+  p->d_qhat = b + o_qhat;
+
+  // ---- constant tables (host FP64, rounded once to the compute type)
+  {
+    const int N = p->nfft;
+    std::vector<double> win(N), tw(2 * N);
+    const double pi = 3.14159265358979323846;
+    for (int n = 0; n < N; ++n) {
+      win[n] = p->c * p->w[n];
+      const double ang = 2.0 * pi * (double)n / (double)N;   // n < N: already reduced
+      tw[2 * n] = std::cos(ang);
+      tw[2 * n + 1] = -std::sin(ang);
+    }
+    std::vector<double> sq(p->Mpad, 0.0), rsq(p->Mpad, 0.0);
+    for (int64_t m = 0; m < M; ++m) {
+      sq[m] = std::sqrt(p->W[m]);
+      rsq[m] = 1.0 / sq[m];
+    }
+    DeviceGuard g(p->device);
+    auto up = [&](void* dst, const std::vector<double>& v) -> cudaError_t {
+      if (p->f64) return cudaMemcpy(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice);
+      std::vector<float> f(v.begin(), v.end());
+      return cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = up(p->d_win, win);
+    if (e == cudaSuccess) e = up(p->d_tw, tw);
+    if (e == cudaSuccess) e = up(p->d_sqrtW, sq);
+    if (e == cudaSuccess) e = up(p->d_rsqrtW, rsq);
+    if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, 4 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+      spod_status st = cuda_fail(e, "upload tables");
+      spod_plan_destroy(p);
+      return st;
+    }
+  }
+  *out = p;
+  return SPOD_OK;
+}
+
+spod_status spod_plan_destroy(spod_plan_t p) {
+  if (!p) return SPOD_OK;
+  {
+    DeviceGuard g(p->device);
+    if (p->ws.base) {
+      cudaDeviceSynchronize();
+      cudaFree(p->ws.base);
+    }
+    if (p->d_xstage) cudaFree(p->d_xstage);
+    if (p->d_phistage) cudaFree(p->d_phistage);
+    if (p->d_gradlam) cudaFree(p->d_gradlam);
+    for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : p->ev_free) cudaEventDestroy(e);
+  }
+  delete p;
+  return SPOD_OK;
+}
+
+spod_status spod_plan_get_info(spod_plan_t p, spod_plan_info* info) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!info) return fail(SPOD_EINVAL, "info is NULL");
+  info->M = p->M;
+  info->nt = p->nt;
+  info->nfft = p->nfft;
+  info->noverlap = p->noverlap;
+  info->step = p->step;
+  info->nb = p->nb;
+  info->nf = p->nf;
+  info->device = p->device;
+  info->workspace_bytes = p->ws.bytes;
+  info->chunk_points = p->chunk_points;
+  return SPOD_OK;
+}
+
+static spod_status check_ptr(const void* ptr, const char* what) {
+  if (!ptr) return fail(SPOD_EINVAL, std::string(what) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(SPOD_EINVAL, std::string(what) + " must be 16-byte aligned");
+  return SPOD_OK;
+}
+
+spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plan's device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->fitted = false;
+  p->qhat_valid = false;
+  SPOD_CUDA(cudaMemsetAsync(p->d_flags, 0, 4 * sizeof(unsigned), s), "clear flags");
+  if (p->desc.subtract_mean) {
+    Phase ph(p, SPOD_PHASE_MEAN, s, 2);
+    SPOD_CUDA(launch_mean(*p, d_X, s), "mean kernel");
+  } else {
+    SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M, s), "zero mean");
+  }
+  int64_t nchunks = 0;
+  for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points, ++nchunks) {
+    const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
+    {
+      Phase ph(p, SPOD_PHASE_FFT, s, 1);
+      SPOD_CUDA(launch_fft_chunk(*p, d_X, m0, mc, s), "fft kernel");
+    }
+    Phase ph(p, SPOD_PHASE_GRAM, s, 1);
+    SPOD_CUDA(launch_gram_chunk(*p, mc, m0 == 0, s), "gram kernel");
+  }
+  {
+    Phase ph(p, SPOD_PHASE_REDUCE, s, 1);
+    SPOD_CUDA(launch_gram_reduce(*p, s), "gram reduce kernel");
+  }
+  {
+    Phase ph(p, SPOD_PHASE_EIG, s, 1);
+    SPOD_CUDA(launch_eig(*p, s), "eigen-solver kernel");
+  }
+  p->fitted = true;
+  p->qhat_valid = nchunks == 1;
+  p->last_stream = s;
+  return SPOD_OK;
+}
+
+spod_status spod_sync(spod_plan_t p, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  DeviceGuard g(p->device);
+  SPOD_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream synchronize");
+  return read_flags(p);
+}
+
+spod_status spod_get_eigs(spod_plan_t p, double* lambda, double* psi, int on_device) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!p->fitted) return fail(SPOD_ESTATE, "spod_get_eigs before spod_fit");
+  if (!lambda) return fail(SPOD_EINVAL, "lambda is NULL");
+  DeviceGuard g(p->device);
+  const size_t nl = sizeof(double) * (size_t)p->nf * p->nb;
+  const size_t npsi = 2 * sizeof(double) * (size_t)p->nf * p->nb * p->nb;
+  if (on_device) {
+    SPOD_CUDA(cudaMemcpyAsync(lambda, p->d_lam, nl, cudaMemcpyDeviceToDevice, p->last_stream), "copy lambda");
+    if (psi) SPOD_CUDA(cudaMemcpyAsync(psi, p->d_psi, npsi, cudaMemcpyDeviceToDevice, p->last_stream), "copy psi");
+    return SPOD_OK;
+  }
+  SPOD_CUDA(cudaStreamSynchronize(p->last_stream), "stream synchronize");
+  SPOD_CUDA(cudaMemcpy(lambda, p->d_lam, nl, cudaMemcpyDeviceToHost), "copy lambda");
+  if (psi) SPOD_CUDA(cudaMemcpy(psi, p->d_psi, npsi, cudaMemcpyDeviceToHost), "copy psi");
+  return read_flags(p);
+}
+
+spod_status spod_get_gram(spod_plan_t p, double* gram) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!p->fitted) return fail(SPOD_ESTATE, "spod_get_gram before spod_fit");
+  if (!gram) return fail(SPOD_EINVAL, "gram is NULL");
+  DeviceGuard g(p->device);
+  SPOD_CUDA(cudaStreamSynchronize(p->last_stream), "stream synchronize");
+  SPOD_CUDA(cudaMemcpy(gram, p->d_gram, 2 * sizeof(double) * (size_t)p->nf * p->nb * p->nb, cudaMemcpyDeviceToHost),
+            "copy gram");
+  return SPOD_OK;
+}
+
+spod_status spod_get_freqs(spod_plan_t p, double* freqs) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!freqs) return fail(SPOD_EINVAL, "freqs is NULL");
+  for (int f = 0; f < p->nf; ++f) freqs[f] = (double)f / ((double)p->nfft * p->desc.dt);
+  return SPOD_OK;
+}
+
+spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!p->fitted) return fail(SPOD_ESTATE, "spod_modes before spod_fit");
+  if (nmodes < 1 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 1 <= nmodes <= nb");
+  if (spod_status st = check_ptr(d_Phi, "d_Phi")) return st;
+  if (!p->qhat_valid) {
+    if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  }
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    Phase ph(p, SPOD_PHASE_MODES, s, 1);
+    SPOD_CUDA(launch_mode_coeffs(*p, nmodes, s), "mode coefficient kernel");
+  }
+  if (p->qhat_valid) {
+    Phase ph(p, SPOD_PHASE_MODES, s, 0);
+    SPOD_CUDA(launch_modes_chunk(*p, 0, p->M, nmodes, d_Phi, s, &ph.n), "modes kernel");
+  } else {
+    for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points) {
+      const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
+      {
+        Phase ph(p, SPOD_PHASE_FFT, s, 1);
+        SPOD_CUDA(launch_fft_chunk(*p, d_X, m0, mc, s), "fft kernel");
+      }
+      Phase ph(p, SPOD_PHASE_MODES, s, 0);
+      SPOD_CUDA(launch_modes_chunk(*p, m0, mc, nmodes, d_Phi, s, &ph.n), "modes kernel");
+    }
+  }
+  p->last_stream = s;
+  return SPOD_OK;
+}
+
+spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* d_X, void* d_dX, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!p->fitted) return fail(SPOD_ESTATE, "spod_backward before spod_fit");
+  (void)d_dLdlambda; (void)d_X; (void)d_dX; (void)stream;
+  return fail(SPOD_EUNSUPPORTED, "spod_backward is not built in this library version");
+}
+
+spod_status spod_run_host(spod_plan_t p, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
+                          void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!h_X) return fail(SPOD_EINVAL, "h_X is NULL");
+  if (nmodes < 0 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 0 <= nmodes <= nb");
+  if (nmodes > 0 && !h_Phi) return fail(SPOD_EINVAL, "h_Phi is NULL");
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t xb = (size_t)p->nt * p->M * elem_bytes(p->desc.in_dtype);
+  if (p->xstage_bytes < xb) {
+    if (p->d_xstage) cudaFree(p->d_xstage);
+    p->d_xstage = nullptr;
+    p->xstage_bytes = 0;
+    if (cudaMalloc(&p->d_xstage, xb) != cudaSuccess) { cudaGetLastError(); return fail(SPOD_ENOMEM, "X staging"); }
+    p->xstage_bytes = xb;
+  }
+  const size_t pb = (size_t)p->nf * nmodes * p->M * 2 * (p->f64 ? 8 : 4);
+  if (nmodes > 0 && p->phistage_bytes < pb) {
+    if (p->d_phistage) cudaFree(p->d_phistage);
+    p->d_phistage = nullptr;
+    p->phistage_bytes = 0;
+    if (cudaMalloc(&p->d_phistage, pb) != cudaSuccess) { cudaGetLastError(); return fail(SPOD_ENOMEM, "Phi staging"); }
+    p->phistage_bytes = pb;
+  }
+  SPOD_CUDA(cudaMemcpyAsync(p->d_xstage, h_X, xb, cudaMemcpyHostToDevice, s), "copy X to device");
+  if (spod_status st = spod_fit(p, p->d_xstage, stream)) return st;
+  if (nmodes > 0) {
+    if (spod_status st = spod_modes(p, p->d_xstage, nmodes, p->d_phistage, stream)) return st;
+    SPOD_CUDA(cudaMemcpyAsync(h_Phi, p->d_phistage, pb, cudaMemcpyDeviceToHost, s), "copy Phi to host");
+  }
+  if (h_lambda)
+    SPOD_CUDA(cudaMemcpyAsync(h_lambda, p->d_lam, sizeof(double) * (size_t)p->nf * p->nb, cudaMemcpyDeviceToHost, s),
+              "copy lambda to host");
+  SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  return read_flags(p);
+}
+
+spod_status spod_profile_enable(spod_plan_t p, int enable) {
+  if (spod_status st = check_plan(p)) return st;
+  p->prof = enable != 0;
+  return SPOD_OK;
+}
+
+spod_status spod_profile_read(spod_plan_t p, double* ms, int64_t* launches) {
+  if (spod_status st = check_plan(p)) return st;
+  DeviceGuard g(p->device);
+  double acc[SPOD_NPHASES] = {0};
+  spod_status st = SPOD_OK;
+  for (auto& r : p->recs) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && st == SPOD_OK) st = cuda_fail(e, "phase timing");
+    acc[r.phase] += t;
+    p->ev_free.push_back(r.a);
+    p->ev_free.push_back(r.b);
+  }
+  p->recs.clear();
+  for (int i = 0; i < SPOD_NPHASES; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (launches) launches[i] = p->launches[i];
+    p->launches[i] = 0;
+  }
+  return st;
+}
+
+spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream) {
+  if (!plans || !d_X || n < 0) return fail(SPOD_EINVAL, "bad batch arguments");
+  for (int i = 0; i < n; ++i)
+    if (spod_status st = spod_fit(plans[i], d_X[i], stream)) return st;
+  return SPOD_OK;
+}
+
+}  // extern "C"

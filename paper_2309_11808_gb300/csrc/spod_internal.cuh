@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of libspod.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spod.h"
+
+namespace spod {
+
+// Device-side condition bits (plan->d_flags[0]).
+enum : unsigned {
+  FLAG_NAN = 1u,            // non-finite Gram diagonal (non-finite input)
+  FLAG_NOTCONV = 2u,        // eigen-solver hit its sweep cap
+  FLAG_TIMEOUT = 4u,        // bounded device wait gave up
+};
+
+constexpr int kMaxRadixPasses = 32;
+constexpr int kMaxNb = 1024;           // largest supported block count
+constexpr int kEigSmemMaxNb = 48;      // eigen-solver keeps A and V in shared memory up to here
+
+struct FftPlan {
+  int n = 0;
+  int npass = 0;
+  int radix[kMaxRadixPasses] = {0};
+};
+
+// Factor n into passes of radix 8, 4, 2, 3, 5.  Returns false if n has another
+// prime factor.
+bool make_fft_plan(int n, FftPlan* fp);
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace spod
+
+struct spod_plan_s {
+  spod_plan_desc desc{};
+  int64_t npoints = 0, M = 0, Mpad = 0, nt = 0;
+  int nvars = 0, nfft = 0, noverlap = 0, step = 0, nb = 0, nf = 0;
+  double c = 0.0;        // 1 / sum(w)
+  double kappa = 0.0;    // 1/nb or 1/(nb-1)
+  std::vector<double> w; // window (FP64)
+  std::vector<double> W; // weights (FP64)
+  int device = 0;
+  bool f64 = false;      // FP64 arithmetic path
+  spod::FftPlan fft;
+
+  // spatial chunking of the FFT -> Gram / modes pipeline
+  int64_t chunk_points = 0;   // points per chunk (multiple of the FFT tile)
+  int gram_splits = 1;        // CTAs per frequency per chunk in the Gram kernel
+  int tile_points = 16;       // points per FFT CTA
+
+  // device workspace (one allocation, carved)
+  spod::Workspace ws;
+  double* d_mu = nullptr;          // [M] time mean
+  double* d_mupart = nullptr;      // [mean_splits][M]
+  int mean_splits = 1;
+  void* d_win = nullptr;           // [nfft] c * w_n, compute type
+  void* d_tw = nullptr;            // [nfft] complex twiddles exp(-2 pi i k / nfft), compute type
+  void* d_sqrtW = nullptr;         // [Mpad] sqrt(W) (0 in the padding), compute type
+  void* d_rsqrtW = nullptr;        // [Mpad] 1/sqrt(W), compute type
+  void* d_qhat = nullptr;          // [nf][2*nb][chunk_points] compute type (planar re | im)
+  double* d_gpart = nullptr;       // [gram_splits][nf][nb][nb][2] FP64 partial Grams
+  double* d_gram = nullptr;        // [nf][nb][nb][2] reduced Gram (kappa applied)
+  double* d_lam = nullptr;         // [nf][nb]
+  double* d_psi = nullptr;         // [nf][nb][nb][2]
+  double* d_eigws = nullptr;       // [nf][2][nbp][nbp][2] eigen-solver scratch (large nb)
+  void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa)
+  unsigned* d_flags = nullptr;     // [4]
+
+  bool fitted = false;
+  bool qhat_valid = false;         // d_qhat holds the fit's Qhat for all points (single chunk)
+  cudaStream_t last_stream = nullptr;
+
+  // staging for spod_run_host
+  void* d_xstage = nullptr;
+  size_t xstage_bytes = 0;
+  void* d_phistage = nullptr;
+  size_t phistage_bytes = 0;
+  double* d_gradlam = nullptr;
+
+  // per-phase timing and launch counts
+  bool prof = false;
+  struct Rec { int phase; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> ev_free;
+  int64_t launches[SPOD_NPHASES] = {0};
+};
+
+namespace spod {
+
+// Launchers (each returns the first CUDA error it meets).
+cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, cudaStream_t s);
+cudaError_t launch_fft_chunk(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount,
+                             cudaStream_t s);
+cudaError_t launch_gram_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
+cudaError_t launch_gram_reduce(const spod_plan_s& p, cudaStream_t s);
+cudaError_t launch_eig(const spod_plan_s& p, cudaStream_t s);
+cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s);
+cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes,
+                               void* d_Phi, cudaStream_t s, int* nlaunch);
+
+size_t fft_smem_bytes(const spod_plan_s& p);
+size_t eig_smem_bytes(int nb);
+
+void set_error(const std::string& msg);
+
+}  // namespace spod

@@ -1,0 +1,235 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Gates (stated for this method): FP64 path eigenvalues within 1e-10 relative;
+FP32 path the leading 5 eigenvalues per frequency within 1e-4 relative;
+modes 1 - |<phi, phi_ref>_W| <= 1e-4 where the relative eigen-gap is >= 1e-2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import jet_like, planted
+
+pytestmark = pytest.mark.gpu
+
+cuda = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+from paper_2309_11808_gb300 import SPOD, SpodError, _lib  # noqa: E402
+
+DEV = "cuda:0"
+WIN = {"hamming": O.WIN_HAMMING, "hamming_periodic": O.WIN_HAMMING_PERIODIC, "hann": O.WIN_HANN,
+       "rect": O.WIN_RECT}
+
+
+def run_both(X, npts, nvars, nfft, nov, prec, nmodes=None, W=None, window="hamming", norm="nb",
+             subtract_mean=True, chunk_points=0, dft="direct", user_window=None):
+    nt, M = X.shape
+    sp = SPOD(npts, nvars, nt, nfft, nov, dtype=X.dtype, precision=prec, weights=W, window=window,
+              norm=norm, subtract_mean=subtract_mean, chunk_points=chunk_points, user_window=user_window)
+    Xd = X.to(DEV).contiguous()
+    sp.fit(Xd)
+    lam, psi = sp.eigs(vectors=True)
+    gram = sp.gram()
+    Phi = sp.modes(Xd, nmodes or sp.nb).cpu().numpy() if nmodes != 0 else None
+    torch.cuda.synchronize()
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, window=WIN.get(window, "user"), user_window=user_window,
+               weights=None if W is None else np.asarray(W, dtype=np.float64),
+               norm=O.NORM_NB if norm == "nb" else O.NORM_NB_MINUS_1, subtract_mean=subtract_mean)
+    ref = O.spod_fit(X.double().cpu().numpy(), d, dft=dft)
+    sp.close()
+    return dict(lam=lam, psi=psi, gram=gram, Phi=Phi, ref=ref, desc=d)
+
+
+def lam_rel_err(lam, ref, k=None):
+    k = k or lam.shape[1]
+    l, r = lam[:, :k], ref[:, :k]
+    keep = r > 1e-13 * r[:, :1]
+    return float((np.abs(l - r) / np.where(keep, np.abs(r), 1.0))[keep].max())
+
+
+def mode_err(Phi, ref_fit, d, W, nmodes, gap=1e-2):
+    Pref = O.spod_modes(ref_fit, d, nmodes)
+    lam = ref_fit.lam
+    Wv = np.ones(d.M) if W is None else np.asarray(W, dtype=np.float64)
+    worst = 0.0
+    for f in range(lam.shape[0]):
+        for k in range(nmodes):
+            lk = lam[f, k]
+            if lk <= 1e-8 * lam[f, 0]:
+                continue
+            nb = []
+            if k > 0:
+                nb.append(abs(lam[f, k - 1] - lk))
+            if k + 1 < lam.shape[1]:
+                nb.append(abs(lam[f, k + 1] - lk))
+            if nb and min(nb) / lk < gap:
+                continue
+            ip = abs(np.vdot(Pref[f, k] * Wv, Phi[f, k]))
+            worst = max(worst, 1.0 - ip)
+    return worst
+
+
+# ------------------------------------------------------------------ configs
+@cuda
+def test_fp64_planted_small_config():
+    # 64 x 32 grid, 1 variable, nt = 2048 FP64, nfft = 256, 50 % overlap (nb = 15),
+    # symmetric Hamming, uniform weights, planted modes + N(0, 0.1^2)
+    wl = planted(64 * 32, 1, 2048, 256, 128, noise_std=0.1, seed=0, dtype=torch.float64)
+    r = run_both(wl.X, 64 * 32, 1, 256, 128, "fp64")
+    assert r["lam"].shape == (129, 15)
+    assert lam_rel_err(r["lam"], r["ref"].lam) <= 1e-10
+    g, gr = r["gram"], r["ref"].M
+    assert np.abs(g - gr).max() <= 1e-12 * np.abs(gr).max()
+    assert mode_err(r["Phi"], r["ref"], r["desc"], None, 15) <= 1e-8
+    # statistically the planted energy a^2/4 dominates at its bin
+    for k, a in zip((10, 25, 60), (3.0, 2.0, 1.0)):
+        assert abs(r["lam"][k, 0] - a * a / 4) < 0.05 * a * a / 4
+
+
+@cuda
+def test_fp32_jet_shaped_small():
+    wl = jet_like(nx=32, nr=16, nvars=3, nt=1500, nfft=64, seed=3, dtype=torch.float32)
+    r = run_both(wl.X, wl.npoints, 3, 64, 32, "fp32", W=wl.W.numpy())
+    assert lam_rel_err(r["lam"], r["ref"].lam, 5) <= 1e-4
+    assert mode_err(r["Phi"], r["ref"], r["desc"], wl.W.numpy(), r["lam"].shape[1]) <= 1e-4
+
+
+SHAPES = [
+    # npts, nvars, nt, nfft, nov
+    (1000, 1, 200, 30, 10),     # M not a multiple of any tile, nfft = 2*3*5
+    (333, 2, 97, 15, 5),        # odd nfft, odd M
+    (77, 1, 40, 6, 3),          # tiny
+    (50, 3, 800, 384, 192),     # radix 3 * 2^7, nb = 3
+    (20, 1, 720, 720, 0),       # nfft = 720 = 2^4 3^2 5, nb = 1 (1 x 1 Gram)
+    (64, 1, 260, 125, 0),       # 5^3, nb = 2, tail of 10 samples
+    (96, 1, 130, 2, 1),         # smallest nfft, nb = 129 (> the shared-memory eigen-solver size)
+]
+
+
+@cuda
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{s[0]}x{s[1]}_nt{s[2]}_n{s[3]}_ov{s[4]}" for s in SHAPES])
+def test_ragged_shapes(shape, prec):
+    npts, nvars, nt, nfft, nov = shape
+    g = torch.Generator().manual_seed(npts * 7 + nfft)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    X = (torch.randn(nt, npts * nvars, generator=g, dtype=torch.float64) * 0.7 + 3.0).to(dt)
+    W = (0.5 + torch.rand(npts * nvars, generator=g, dtype=torch.float64)).numpy()
+    r = run_both(X, npts, nvars, nfft, nov, prec, W=W, nmodes=min(4, O.n_blocks(nt, nfft, nov)))
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    k = None if prec == "fp64" else 5
+    assert lam_rel_err(r["lam"], r["ref"].lam, k) <= tol
+    merr = mode_err(r["Phi"], r["ref"], r["desc"], W, r["Phi"].shape[1])
+    assert merr <= (1e-8 if prec == "fp64" else 1e-4)
+
+
+@cuda
+def test_chunked_pipeline_matches_single_pass():
+    g = torch.Generator().manual_seed(5)
+    npts, nt, nfft = 1000, 300, 32
+    X = torch.randn(nt, npts, generator=g, dtype=torch.float32)
+    a = run_both(X, npts, 1, nfft, 16, "fp32", nmodes=3)
+    b = run_both(X, npts, 1, nfft, 16, "fp32", nmodes=3, chunk_points=128)   # 8 chunks, ragged last
+    # FP32 partial sums are promoted to FP64 at different point boundaries in the
+    # two layouts, so the two differ at FP32 rounding level, not bit for bit
+    np.testing.assert_allclose(a["lam"], b["lam"], rtol=1e-5, atol=1e-7 * a["lam"].max())
+    np.testing.assert_allclose(a["Phi"], b["Phi"], rtol=0, atol=1e-4 * np.abs(a["Phi"]).max())
+    assert lam_rel_err(b["lam"], b["ref"].lam, 5) <= 1e-4
+    assert lam_rel_err(a["lam"], a["ref"].lam, 5) <= 1e-4
+    # FP64: the same change of grouping stays at FP64 rounding level
+    X64 = X.double()
+    a = run_both(X64, npts, 1, nfft, 16, "fp64", nmodes=0)
+    b = run_both(X64, npts, 1, nfft, 16, "fp64", nmodes=0, chunk_points=128)
+    np.testing.assert_allclose(a["lam"], b["lam"], rtol=1e-12, atol=1e-14 * a["lam"].max())
+
+
+@cuda
+def test_bitwise_reproducible():
+    wl = jet_like(nx=16, nr=16, nvars=2, nt=700, nfft=64, seed=1)
+    sp = SPOD(wl.npoints, 2, 700, 64, 32, weights=wl.W)
+    Xd = wl.X.to(DEV)
+    sp.fit(Xd)
+    l1, p1 = sp.eigs(vectors=True)
+    sp.fit(Xd)
+    l2, p2 = sp.eigs(vectors=True)
+    assert np.array_equal(l1, l2) and np.array_equal(p1, p2)
+
+
+@cuda
+@pytest.mark.parametrize("window", ["hamming_periodic", "hann", "rect", "user"])
+def test_window_and_options(window):
+    g = torch.Generator().manual_seed(11)
+    npts, nt, nfft = 200, 400, 40
+    X = torch.randn(nt, npts, generator=g, dtype=torch.float64) + 1.0
+    uw = np.linspace(0.2, 1.0, nfft) if window == "user" else None
+    r = run_both(X, npts, 1, nfft, 20, "fp64", window=window, user_window=uw, nmodes=3)
+    assert lam_rel_err(r["lam"], r["ref"].lam) <= 1e-10
+    r = run_both(X, npts, 1, nfft, 20, "fp64", window=window, user_window=uw, nmodes=0, norm="nb-1",
+                 subtract_mean=False)
+    assert lam_rel_err(r["lam"], r["ref"].lam) <= 1e-10
+
+
+@cuda
+def test_bf16_storage_fp32_arithmetic():
+    wl = jet_like(nx=16, nr=16, nvars=3, nt=900, nfft=64, seed=2, dtype=torch.bfloat16)
+    r = run_both(wl.X, wl.npoints, 3, 64, 32, "fp32", W=wl.W.numpy(), nmodes=2)
+    assert lam_rel_err(r["lam"], r["ref"].lam, 5) <= 1e-4
+
+
+@cuda
+def test_run_host_matches_device_path():
+    wl = jet_like(nx=16, nr=8, nvars=2, nt=600, nfft=64, seed=4)
+    sp = SPOD(wl.npoints, 2, 600, 64, 32, weights=wl.W)
+    Xd = wl.X.to(DEV)
+    sp.fit(Xd)
+    lam = sp.eigs()
+    Phi = sp.modes(Xd, 3).cpu().numpy()
+    hX = wl.X.numpy().copy()
+    hlam = np.empty_like(lam)
+    hPhi = np.empty((sp.nf, 3, sp.M), dtype=np.complex64)
+    _lib.spod_run_host(sp.handle, hX, 3, hPhi, hlam)
+    assert np.array_equal(hlam, lam)
+    assert np.array_equal(hPhi, Phi)
+
+
+@cuda
+def test_error_statuses():
+    sp = SPOD(64, 1, 200, 32, 16)
+    X = torch.randn(200, 64, device=DEV)
+    out = torch.empty((sp.nf, 2, 64), dtype=torch.complex64, device=DEV)
+    with pytest.raises(SpodError) as e:
+        _lib.spod_modes(sp.handle, X, 2, out)
+    assert e.value.status == _lib.SPOD_ESTATE
+    with pytest.raises(SpodError) as e:
+        sp.eigs()
+    assert e.value.status == _lib.SPOD_ESTATE
+    sp.fit(X)
+    with pytest.raises(SpodError) as e:
+        _lib.spod_modes(sp.handle, X, sp.nb + 1, out)
+    assert e.value.status == _lib.SPOD_EINVAL
+    with pytest.raises(SpodError) as e:     # misaligned device pointer
+        _lib.spod_fit(sp.handle, X.data_ptr() + 4)
+    assert e.value.status == _lib.SPOD_EINVAL
+    Xn = X.clone()
+    Xn[17, 5] = float("nan")
+    sp.fit(Xn)
+    with pytest.raises(SpodError) as e:
+        sp.eigs()
+    assert e.value.status == _lib.SPOD_ENANINPUT
+    sp.fit(X)
+    sp.eigs()          # recovers
+    with pytest.raises(SpodError) as e:
+        SPOD(64, 1, 200, 28, 14)    # 7 is not a supported radix
+    assert e.value.status == _lib.SPOD_EUNSUPPORTED
+    with pytest.raises(SpodError) as e:
+        SPOD(64, 1, 200, 32, 16, weights=np.r_[np.ones(63), -1.0])
+    assert e.value.status == _lib.SPOD_EINVAL
+    sp.close()
