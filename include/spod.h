@@ -215,6 +215,31 @@ typedef enum {
 spod_status spod_profile_enable(spod_plan_t plan, int enable);
 spod_status spod_profile_read(spod_plan_t plan, double* ms, int64_t* launches);
 
+/* Allocation-free batched Hermitian eigen-decomposition (the eigen-solver step
+ * of spod_fit on caller-provided matrices).  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- code running under a
+ * host framework that owns all device memory, real-time loops that cannot
+ * take the allocator's latency or the device-wide synchronisation of
+ * cudaFree, programs that reserve all their memory up front.
+ *   d_gram   : device, [nf][nb][nb] interleaved complex FP64 Hermitian
+ *              matrices (16-byte aligned), read only.
+ *   d_lambda : device, [nf][nb] FP64 eigenvalues, descending (8-byte aligned).
+ *   d_psi    : device, [nf][nb][nb] interleaved complex FP64, column k of
+ *              psi[f] the k-th eigenvector, unit norm, largest-modulus entry
+ *              real positive (16-byte aligned).
+ * Scratch comes from one fixed 32 MiB device array inside the library (held
+ * by every GPU that loads it until the process exits): the call needs
+ * 256 + (nb > 48 ? nf * 32 * nb * nb : 0) bytes and returns SPOD_EINVAL when
+ * that exceeds 32 MiB, or when nf < 1 or nb is outside 1..1024.  No device
+ * memory is allocated.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), so make it before any stream capture.
+ * The call is enqueued on `stream` on the current device and then waits for
+ * that stream, returning SPOD_ENOTCONVERGED if the solver hit its sweep cap.
+ * All calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller. */
+spod_status spod_eigh_batched_noalloc(const double* d_gram, int nf, int nb, double* d_lambda, double* d_psi,
+                                      void* stream);
+
 /* Thread-local message describing the last non-OK status. */
 const char* spod_last_error(void);
 

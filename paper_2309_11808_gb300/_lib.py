@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "SPOD_OK", 1: "SPOD_EINVAL", 2: "SPOD_ENOMEM", 3: "SPOD_ECUDA
 EXPORTED = ["spod_desc_init", "spod_plan_create", "spod_plan_destroy", "spod_plan_get_info", "spod_fit",
             "spod_get_eigs", "spod_get_gram", "spod_get_freqs", "spod_modes", "spod_backward",
             "spod_run_host", "spod_sync", "spod_fit_batch", "spod_profile_enable", "spod_profile_read",
-            "spod_last_error", "spod_version"]
+            "spod_eigh_batched_noalloc", "spod_last_error", "spod_version"]
 
 PHASES = ["mean", "fft", "gram", "reduce", "eig", "modes", "backward"]
 
@@ -77,6 +77,7 @@ def lib() -> C.CDLL:
         L.spod_fit_batch.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, P]
         L.spod_profile_enable.argtypes = [P, C.c_int]
         L.spod_profile_read.argtypes = [P, P, P]
+        L.spod_eigh_batched_noalloc.argtypes = [P, C.c_int, C.c_int, P, P, P]
         L.spod_last_error.restype = C.c_char_p
         L.spod_version.restype = C.c_char_p
         for name in EXPORTED[:-2]:
@@ -185,6 +186,11 @@ def spod_profile_read(plan: int):
     ln = np.zeros(len(PHASES), dtype=np.int64)
     check(lib().spod_profile_read(plan, ms.ctypes.data, ln.ctypes.data), "spod_profile_read")
     return dict(zip(PHASES, ms.tolist())), dict(zip(PHASES, ln.tolist()))
+
+
+def spod_eigh_batched_noalloc(gram, nf: int, nb: int, lam, psi, stream=None) -> None:
+    check(lib().spod_eigh_batched_noalloc(_ptr(gram), int(nf), int(nb), _ptr(lam), _ptr(psi), _stream(stream)),
+          "spod_eigh_batched_noalloc")
 
 
 def spod_last_error() -> str:

@@ -275,6 +275,17 @@ cudaError_t launch_eig(const spod_plan_s& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The same eigen-solver launch on caller-chosen buffers (used by the
+// allocation-free entry point, which supplies its scratch from a static array).
+cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, double* psi, double* gws,
+                               unsigned* flags, cudaStream_t s) {
+  const size_t smem = eig_smem_bytes(nb);
+  cudaError_t e = cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_eig_jacobi<<<nf, 256, smem, s>>>(gram, nb, lam, psi, gws, flags, 50, 1e-14);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s) {
   if (p.f64)
     k_mode_coeffs<double><<<p.nf, 256, 0, s>>>(p.d_lam, p.d_psi, p.nb, nmodes, p.kappa,

@@ -107,6 +107,9 @@ cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s)
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes,
                                void* d_Phi, cudaStream_t s, int* nlaunch);
 
+cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, double* psi, double* gws,
+                               unsigned* flags, cudaStream_t s);
+
 size_t fft_smem_bytes(const spod_plan_s& p);
 size_t eig_smem_bytes(int nb);
 
