@@ -73,7 +73,10 @@ typedef enum { SPOD_F64 = 0, SPOD_F32 = 1, SPOD_BF16 = 2 } spod_dtype;
  *   BF16   : FFT in FP32; Gram and mode products on the tensor cores from
  *            BF16-rounded operands, FP32 accumulation.
  *   BF16X3 : as BF16 but every operand x is split x = hi + lo (hi = bf16(x),
- *            lo = bf16(x - hi)) and the product is hi*hi + hi*lo + lo*hi. */
+ *            lo = bf16(x - hi)), three tensor-core products per step.  Modes:
+ *            hi*hi + hi*lo + lo*hi.  Gram (symmetric): A1 = hi hi^T + lo lo^T
+ *            and A2 = hi lo^T in two accumulators, Y Y^T = A1 + A2 + A2^T, so
+ *            no product term is dropped. */
 typedef enum {
   SPOD_PREC_FP64 = 0,
   SPOD_PREC_FP32 = 1,
@@ -193,6 +196,20 @@ spod_status spod_sync(spod_plan_t plan, void* stream);
 /* Fit n plans on n inputs with one CUDA-graph launch (datasets of different
  * grid size, nt and nfft).  Equivalent to n spod_fit calls.  */
 spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream);
+
+/* Launch-shape knobs (the autotuner's interface).  They change how work is
+ * split across CTAs, never what is computed beyond floating-point grouping.
+ * In spod_plan_set_tuning a zero field keeps the plan's current value. */
+typedef struct {
+  int gram_splits;        /* CTAs per frequency over the points of a chunk, 1..gram_splits_max */
+  int gram_splits_max;    /* read-only: bound set by the plan's workspace */
+  int gram_flush_blocks;  /* tensor-core Gram: 64-point blocks per FP32 accumulation group (1..64) */
+  int modes_ctas;         /* tensor-core modes: CTAs per frequency (0 = automatic) */
+} spod_tuning;
+
+spod_status spod_plan_get_tuning(spod_plan_t plan, spod_tuning* tuning);
+/* SPOD_EINVAL for values outside the stated ranges; takes effect from the next fit/modes call. */
+spod_status spod_plan_set_tuning(spod_plan_t plan, const spod_tuning* tuning);
 
 /* Phases of the hot path, for per-phase timing. */
 typedef enum {

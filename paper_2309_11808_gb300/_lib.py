@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "SPOD_OK", 1: "SPOD_EINVAL", 2: "SPOD_ENOMEM", 3: "SPOD_ECUDA
 EXPORTED = ["spod_desc_init", "spod_plan_create", "spod_plan_destroy", "spod_plan_get_info", "spod_fit",
             "spod_get_eigs", "spod_get_gram", "spod_get_freqs", "spod_modes", "spod_backward",
             "spod_run_host", "spod_sync", "spod_fit_batch", "spod_profile_enable", "spod_profile_read",
-            "spod_eigh_batched_noalloc", "spod_last_error", "spod_version"]
+            "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning",
+            "spod_last_error", "spod_version"]
 
 PHASES = ["mean", "fft", "gram", "reduce", "eig", "modes", "backward"]
 
@@ -42,6 +43,11 @@ class spod_plan_info(C.Structure):
     _fields_ = [("M", C.c_int64), ("nt", C.c_int64), ("nfft", C.c_int), ("noverlap", C.c_int),
                 ("step", C.c_int), ("nb", C.c_int), ("nf", C.c_int), ("device", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("chunk_points", C.c_int64)]
+
+
+class spod_tuning(C.Structure):
+    _fields_ = [("gram_splits", C.c_int), ("gram_splits_max", C.c_int), ("gram_flush_blocks", C.c_int),
+                ("modes_ctas", C.c_int)]
 
 
 class SpodError(RuntimeError):
@@ -78,6 +84,8 @@ def lib() -> C.CDLL:
         L.spod_profile_enable.argtypes = [P, C.c_int]
         L.spod_profile_read.argtypes = [P, P, P]
         L.spod_eigh_batched_noalloc.argtypes = [P, C.c_int, C.c_int, P, P, P]
+        L.spod_plan_get_tuning.argtypes = [P, C.POINTER(spod_tuning)]
+        L.spod_plan_set_tuning.argtypes = [P, C.POINTER(spod_tuning)]
         L.spod_last_error.restype = C.c_char_p
         L.spod_version.restype = C.c_char_p
         for name in EXPORTED[:-2]:
@@ -191,6 +199,17 @@ def spod_profile_read(plan: int):
 def spod_eigh_batched_noalloc(gram, nf: int, nb: int, lam, psi, stream=None) -> None:
     check(lib().spod_eigh_batched_noalloc(_ptr(gram), int(nf), int(nb), _ptr(lam), _ptr(psi), _stream(stream)),
           "spod_eigh_batched_noalloc")
+
+
+def spod_plan_get_tuning(plan: int) -> spod_tuning:
+    t = spod_tuning()
+    check(lib().spod_plan_get_tuning(plan, C.byref(t)), "spod_plan_get_tuning")
+    return t
+
+
+def spod_plan_set_tuning(plan: int, gram_splits: int = 0, gram_flush_blocks: int = 0, modes_ctas: int = 0) -> None:
+    t = spod_tuning(int(gram_splits), 0, int(gram_flush_blocks), int(modes_ctas))
+    check(lib().spod_plan_set_tuning(plan, C.byref(t)), "spod_plan_set_tuning")
 
 
 def spod_last_error() -> str:

@@ -4,14 +4,17 @@
 // Mean: FP64 accumulation of FP32 runs of 16 samples (FP64 throughout for FP64
 // input), time axis split over grid.y, then a fixed-order FP64 sum.
 //
-// FFT: one CTA per (Welch block l, tile of TP spatial points).  Two real point
-// series are packed into one complex sequence (z = x_even + i x_odd), the
-// tile's TP/2 sequences are transformed together by a shared-memory Stockham
-// FFT of mixed radix 8/4/2/3/5, and the two real spectra are separated at the
-// end.  The mean is subtracted as a double-float pair, the window carries
+// FFT: one CTA of 256 threads per (Welch block l, tile of TP spatial points;
+// TP = 16 for FP32 arithmetic, 8 for FP64).  Two real point series are
+// packed into one complex sequence (z = x_even + i x_odd), the tile's TP/2
+// sequences are transformed together by a shared-memory Stockham FFT of mixed
+// radix 8/4/2/3/5 (ping-pong buffers, nfft <= 1024), and the two real spectra
+// are separated at the end.  The mean is subtracted as a double-float pair, the window carries
 // c = 1/sum(w), and sqrt(W_m) is folded into the output so that the Gram is a
 // plain Qhat^H Qhat.  Output: Qhat[f][row][m_local], row = l (real part) or
 // nb + l (imaginary part), f = 0 .. nfft/2.
+#include <algorithm>
+
 #include "spod_internal.cuh"
 
 namespace spod {
@@ -79,6 +82,7 @@ __global__ void k_mean_finish(const double* __restrict__ part, int splits, int64
 // ---------------------------------------------------------------- FFT
 struct FftArgs {
   int64_t M, m0, mcount, chunk;   // chunk = row stride of Qhat (points per chunk)
+  int64_t mpad;                   // points written: mcount rounded up to 64 (zeros past mcount)
   int nfft, step, nb, nf;
   int subtract_mean;
   FftPlan fp;
@@ -131,34 +135,43 @@ __device__ __forceinline__ void dft_small(V* v) {
   }
 }
 
-// One Stockham pass of radix RAD over `cols` interleaved sequences of length n.
-template <int RAD, typename V, typename R>
+// One Stockham pass of radix RAD over C interleaved sequences of length n
+// (layout [n][C]) from src to dst.  Butterfly b uses k = b mod Ns and group
+// b / Ns; the power-of-two passes run first, so Ns stays a power of two
+// (shift and mask) until the radix-3/5 passes.  C is a compile-time constant.
+template <int RAD, int C, typename V, typename R>
 __device__ __forceinline__ void stockham_pass(const V* __restrict__ src, V* __restrict__ dst,
-                                              const V* __restrict__ tw, int n, int cols, int Ns) {
+                                              const V* __restrict__ tw, int n, int Ns, int log2Ns) {
   const int nbut = n / RAD;
   const int stride_tw = n / (Ns * RAD);
-  for (int idx = threadIdx.x; idx < nbut * cols; idx += blockDim.x) {
-    const int b = idx / cols, col = idx - b * cols;
+  for (int idx = threadIdx.x; idx < nbut * C; idx += blockDim.x) {
+    const int b = idx / C, col = idx % C;
     V v[RAD];
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[r] = src[(b + r * nbut) * cols + col];
-    const int k = b % Ns;
+    for (int r = 0; r < RAD; ++r) v[r] = src[(b + r * nbut) * C + col];
+    int k, g;
+    if (log2Ns >= 0) { k = b & (Ns - 1); g = b >> log2Ns; }
+    else { g = b / Ns; k = b - g * Ns; }
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[r * k * stride_tw]);
     }
     dft_small<RAD, V, R>(v);
-    const int base = (b / Ns) * Ns * RAD + k;
+    const int base = g * Ns * RAD + k;
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) dst[(base + r * Ns) * cols + col] = v[r];
+    for (int r = 0; r < RAD; ++r) dst[(base + r * Ns) * C + col] = v[r];
   }
 }
 
-template <typename Tin, typename R, int TP>
+// Output element types of the FFT kernel.
+enum OutKind { OUT_NATIVE = 0, OUT_BF16X3 = 1, OUT_BF16 = 2 };
+
+// One CTA (256 threads) per (Welch block l, tile of TP points).
+template <typename Tin, typename R, int TP, int OUTK>
 __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R* __restrict__ win,
                                              const typename C2<R>::T* __restrict__ tw_g,
                                              const R* __restrict__ sqrtW, const double* __restrict__ mu,
-                                             R* __restrict__ qhat, FftArgs a) {
+                                             void* __restrict__ qout, void* __restrict__ qout_lo, FftArgs a) {
   using V = typename C2<R>::T;
   constexpr int C = TP / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -167,115 +180,125 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
   V* tw = bufB + (size_t)a.nfft * C;
   const int N = a.nfft;
 
-  const int64_t ntiles = (a.mcount + TP - 1) / TP;
   const int64_t item = blockIdx.x;
   const int l = (int)(item % a.nb);
   const int64_t tile = item / a.nb;
-  if (tile >= ntiles) return;
   const int64_t lm0 = tile * TP;          // local (chunk) point index
   const int64_t gm0 = a.m0 + lm0;         // global point index
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
 
-  // load block l, subtract the mean, apply c*w_n; columns pack points (2j, 2j+1)
-  const int64_t tbase = (int64_t)l * a.step;
-  for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-    const int n = idx / C, j = idx - n * C;
+  // ---- load block l: thread owns column pair j, rows n = n0, n0 + 256/C, ...
+  // (the mean is read once per column and kept as a rounded pair hi + lo)
+  {
+    const int j = threadIdx.x % C;
+    const int n0 = threadIdx.x / C;
     const int64_t m = gm0 + 2 * j;
-    const Tin* row = X + (tbase + n) * a.M;
-    R x0 = 0, x1 = 0;
-    if (m < a.m0 + a.mcount && m < a.M) {
-      if constexpr (sizeof(R) == 8) {
-        x0 = (R)to_f64<Tin>(row[m]);
-        if (a.subtract_mean) x0 -= (R)mu[m];
-      } else {
-        x0 = to_f32<Tin>(row[m]);
-        if (a.subtract_mean) {
-          const double mm = mu[m];
-          const float hi = (float)mm, lo = (float)(mm - (double)hi);
-          x0 = (x0 - hi) - lo;
-        }
-      }
+    const int64_t mend = a.m0 + a.mcount;
+    const bool ok0 = m < mend, ok1 = m + 1 < mend;
+    R mhi0 = 0, mlo0 = 0, mhi1 = 0, mlo1 = 0;
+    if (a.subtract_mean) {
+      if (ok0) { const double d = mu[m]; mhi0 = (R)d; mlo0 = (R)(d - (double)mhi0); }
+      if (ok1) { const double d = mu[m + 1]; mhi1 = (R)d; mlo1 = (R)(d - (double)mhi1); }
     }
-    if (m + 1 < a.m0 + a.mcount && m + 1 < a.M) {
-      if constexpr (sizeof(R) == 8) {
-        x1 = (R)to_f64<Tin>(row[m + 1]);
-        if (a.subtract_mean) x1 -= (R)mu[m + 1];
-      } else {
-        x1 = to_f32<Tin>(row[m + 1]);
-        if (a.subtract_mean) {
-          const double mm = mu[m + 1];
-          const float hi = (float)mm, lo = (float)(mm - (double)hi);
-          x1 = (x1 - hi) - lo;
-        }
-      }
+    const Tin* base = X + (int64_t)l * a.step * a.M + m;
+    constexpr int NSTEP = 256 / C;
+#pragma unroll 4
+    for (int n = n0; n < N; n += NSTEP) {
+      const Tin* row = base + (int64_t)n * a.M;
+      R x0 = ok0 ? (R)to_f64<Tin>(row[0]) : (R)0;
+      R x1 = ok1 ? (R)to_f64<Tin>(row[1]) : (R)0;
+      x0 = ok0 ? (x0 - mhi0) - mlo0 : (R)0;
+      x1 = ok1 ? (x1 - mhi1) - mlo1 : (R)0;
+      const R wn = win[n];
+      bufA[n * C + j] = mk<R>(x0 * wn, x1 * wn);
     }
-    const R wn = win[n];
-    bufA[idx] = mk<R>(x0 * wn, x1 * wn);
   }
   __syncthreads();
 
   V* src = bufA;
   V* dst = bufB;
-  int Ns = 1;
+  int Ns = 1, log2Ns = 0;
   for (int ps = 0; ps < a.fp.npass; ++ps) {
     const int rad = a.fp.radix[ps];
     switch (rad) {
-      case 8: stockham_pass<8, V, R>(src, dst, tw, N, C, Ns); break;
-      case 4: stockham_pass<4, V, R>(src, dst, tw, N, C, Ns); break;
-      case 2: stockham_pass<2, V, R>(src, dst, tw, N, C, Ns); break;
-      case 3: stockham_pass<3, V, R>(src, dst, tw, N, C, Ns); break;
-      default: stockham_pass<5, V, R>(src, dst, tw, N, C, Ns); break;
+      case 8: stockham_pass<8, C, V, R>(src, dst, tw, N, Ns, log2Ns); break;
+      case 4: stockham_pass<4, C, V, R>(src, dst, tw, N, Ns, log2Ns); break;
+      case 2: stockham_pass<2, C, V, R>(src, dst, tw, N, Ns, log2Ns); break;
+      case 3: stockham_pass<3, C, V, R>(src, dst, tw, N, Ns, log2Ns); break;
+      default: stockham_pass<5, C, V, R>(src, dst, tw, N, Ns, log2Ns); break;
     }
     Ns *= rad;
+    if (log2Ns >= 0) log2Ns = (rad == 2) ? log2Ns + 1 : (rad == 4) ? log2Ns + 2 : (rad == 8) ? log2Ns + 3 : -1;
     __syncthreads();
     V* t = src; src = dst; dst = t;
   }
+  V* buf = src;
 
-  // separate the two real spectra, fold sqrt(W), store planar re/im rows
+  // ---- separate the two real spectra, fold sqrt(W), store planar re/im rows;
+  // points past mcount (up to the 64-point padding) are written as zeros
   const int64_t rs = a.chunk;
   for (int idx = threadIdx.x; idx < a.nf * TP; idx += blockDim.x) {
     const int f = idx / TP, p = idx - f * TP;
     const int64_t lm = lm0 + p;
-    if (lm >= a.mcount) continue;
-    const int col = p >> 1;
-    const V zf = src[f * C + col];
-    const int fn = (f == 0) ? 0 : N - f;
-    const V zc = src[fn * C + col];
-    R re, im;
-    if ((p & 1) == 0) {          // (Z[f] + conj Z[N-f]) / 2
-      re = (R)0.5 * (zf.x + zc.x);
-      im = (R)0.5 * (zf.y - zc.y);
-    } else {                     // (Z[f] - conj Z[N-f]) / (2i)
-      re = (R)0.5 * (zf.y + zc.y);
-      im = (R)-0.5 * (zf.x - zc.x);
+    if (lm >= a.mpad) continue;
+    R re = 0, im = 0;
+    if (lm < a.mcount) {
+      const int col = p >> 1;
+      const V zf = buf[f * C + col];
+      const int fn = (f == 0) ? 0 : N - f;
+      const V zc = buf[fn * C + col];
+      if ((p & 1) == 0) {          // (Z[f] + conj Z[N-f]) / 2
+        re = (R)0.5 * (zf.x + zc.x);
+        im = (R)0.5 * (zf.y - zc.y);
+      } else {                     // (Z[f] - conj Z[N-f]) / (2i)
+        re = (R)0.5 * (zf.y + zc.y);
+        im = (R)-0.5 * (zf.x - zc.x);
+      }
+      const R sw = sqrtW[gm0 + p];
+      re *= sw;
+      im *= sw;
     }
-    const R sw = sqrtW[gm0 + p];
-    R* q = qhat + ((int64_t)f * 2 * a.nb + l) * rs + lm;
-    q[0] = re * sw;
-    q[(int64_t)a.nb * rs] = im * sw;
+    const int64_t o_re = ((int64_t)f * 2 * a.nb + l) * rs + lm;
+    const int64_t o_im = o_re + (int64_t)a.nb * rs;
+    if constexpr (OUTK == OUT_NATIVE) {
+      R* q = static_cast<R*>(qout);
+      q[o_re] = re;
+      q[o_im] = im;
+    } else {
+      __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
+      const __nv_bfloat16 hr = __float2bfloat16_rn((float)re), hi = __float2bfloat16_rn((float)im);
+      qh[o_re] = hr;
+      qh[o_im] = hi;
+      if constexpr (OUTK == OUT_BF16X3) {
+        __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qout_lo);
+        ql[o_re] = __float2bfloat16_rn((float)re - __bfloat162float(hr));
+        ql[o_im] = __float2bfloat16_rn((float)im - __bfloat162float(hi));
+      }
+    }
   }
 }
 
-template <typename Tin, typename R>
+template <typename Tin, typename R, int OUTK>
 cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
-  constexpr int TP = 16;
+  constexpr int TP = sizeof(R) == 8 ? 8 : 16;
   FftArgs a;
   a.M = p.M; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
+  a.mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
   a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;
   a.subtract_mean = p.desc.subtract_mean;
   a.fp = p.fft;
   const size_t smem = fft_smem_bytes(p);
-  auto kern = k_fft<Tin, R, TP>;
+  auto kern = k_fft<Tin, R, TP, OUTK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (mcount + TP - 1) / TP;
+  const int64_t ntiles = (a.mpad + TP - 1) / TP;
   const int64_t grid = ntiles * p.nb;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   kern<<<(unsigned)grid, 256, smem, s>>>(
       static_cast<const Tin*>(d_X), static_cast<const R*>(p.d_win),
       static_cast<const typename C2<R>::T*>(p.d_tw), static_cast<const R*>(p.d_sqrtW), p.d_mu,
-      static_cast<R*>(p.d_qhat), a);
+      p.d_qhat, p.d_qlo, a);
   return cudaGetLastError();
 }
 
@@ -295,7 +318,7 @@ cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, cudaStream_t s)
 
 size_t fft_smem_bytes(const spod_plan_s& p) {
   const size_t vb = p.f64 ? 16 : 8;
-  const size_t C = 16 / 2;
+  const size_t C = p.f64 ? 4 : 8;
   return vb * ((size_t)p.nfft * C * 2 + (size_t)p.nfft);
 }
 
@@ -307,16 +330,19 @@ cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, cudaStream_t s) {
   }
 }
 
+template <typename Tin>
+static cudaError_t launch_fft_in(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
+  if (p.f64) return launch_fft_t<Tin, double, OUT_NATIVE>(p, d_X, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_fft_t<Tin, float, OUT_BF16X3>(p, d_X, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16) return launch_fft_t<Tin, float, OUT_BF16>(p, d_X, m0, mcount, s);
+  return launch_fft_t<Tin, float, OUT_NATIVE>(p, d_X, m0, mcount, s);
+}
+
 cudaError_t launch_fft_chunk(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount,
                              cudaStream_t s) {
-  if (p.f64) {
-    if (p.desc.in_dtype == SPOD_F64) return launch_fft_t<double, double>(p, d_X, m0, mcount, s);
-    if (p.desc.in_dtype == SPOD_F32) return launch_fft_t<float, double>(p, d_X, m0, mcount, s);
-    return launch_fft_t<__nv_bfloat16, double>(p, d_X, m0, mcount, s);
-  }
-  if (p.desc.in_dtype == SPOD_F64) return launch_fft_t<double, float>(p, d_X, m0, mcount, s);
-  if (p.desc.in_dtype == SPOD_F32) return launch_fft_t<float, float>(p, d_X, m0, mcount, s);
-  return launch_fft_t<__nv_bfloat16, float>(p, d_X, m0, mcount, s);
+  if (p.desc.in_dtype == SPOD_F64) return launch_fft_in<double>(p, d_X, m0, mcount, s);
+  if (p.desc.in_dtype == SPOD_F32) return launch_fft_in<float>(p, d_X, m0, mcount, s);
+  return launch_fft_in<__nv_bfloat16>(p, d_X, m0, mcount, s);
 }
 
 bool make_fft_plan(int n, FftPlan* fp) {

@@ -8,6 +8,8 @@
 #include <new>
 #include <string>
 
+#include <cudaTypedefs.h>
+
 #include "spod_internal.cuh"
 
 namespace spod {
@@ -118,6 +120,30 @@ struct Phase {
   }
 };
 
+// TMA maps of the BF16 Qhat planes: dims {chunk points, 2 nb rows, nf}, box
+// {64 points, 2 nb rounded up to 16 rows, 1}; rows past 2 nb read as zeros.
+spod_status make_qhat_maps(spod_plan_s* p) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[3] = {(cuuint64_t)p->chunk_points, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)p->chunk_points * 2, (cuuint64_t)(2 * p->nb) * p->chunk_points * 2};
+  const cuuint32_t box[3] = {64, (cuuint32_t)((2 * p->nb + 15) / 16 * 16), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* bases[2] = {p->d_qhat, p->d_qlo ? p->d_qlo : p->d_qhat};
+  CUtensorMap* maps[2] = {&p->tmap_hi, &p->tmap_lo};
+  for (int i = 0; i < 2; ++i) {
+    CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, bases[i], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  }
+  return SPOD_OK;
+}
+
 }  // namespace
 }  // namespace spod
 
@@ -171,8 +197,6 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   if (d->window == SPOD_WIN_USER && !d->user_window) return fail(SPOD_EINVAL, "user_window is NULL");
   if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(SPOD_EINVAL, "dt must be positive and finite");
   if (d->chunk_points < 0) return fail(SPOD_EINVAL, "chunk_points must be >= 0");
-  if (d->precision == SPOD_PREC_BF16 || d->precision == SPOD_PREC_BF16X3)
-    return fail(SPOD_EUNSUPPORTED, "tensor-core precisions are not built in this library version");
 
   spod_plan_s* p = new (std::nothrow) spod_plan_s();
   if (!p) return fail(SPOD_ENOMEM, "host allocation failed");
@@ -189,6 +213,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->nb = (int)((d->nt - d->noverlap) / p->step);
   p->nf = d->nfft / 2 + 1;
   p->f64 = d->precision == SPOD_PREC_FP64;
+  p->tensor = d->precision == SPOD_PREC_BF16 || d->precision == SPOD_PREC_BF16X3;
   auto bail = [&](spod_status st, const std::string& m) {
     spod_plan_destroy(p);
     return fail(st, m);
@@ -197,6 +222,9 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   if (d->norm == SPOD_NORM_NB_MINUS_1 && p->nb < 2) return bail(SPOD_EINVAL, "nb-1 normalisation needs nb >= 2");
   if (p->nb > 256) return bail(SPOD_EUNSUPPORTED, "nb > 256 blocks is not supported");
   if (!make_fft_plan(d->nfft, &p->fft)) return bail(SPOD_EUNSUPPORTED, "nfft must factor into 2, 3 and 5");
+  if (d->nfft > 1024) return bail(SPOD_EUNSUPPORTED, "nfft > 1024 is not supported by the block FFT kernel");
+  if (p->tensor && p->nb > 64)
+    return bail(SPOD_EUNSUPPORTED, "BF16 / BF16X3 precisions support nb <= 64 (2 nb rows per MMA tile)");
   p->kappa = 1.0 / (d->norm == SPOD_NORM_NB ? (double)p->nb : (double)(p->nb - 1));
 
   p->w = make_window(*d);
@@ -219,13 +247,21 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   if (cudaGetDevice(&p->device) != cudaSuccess) return bail(SPOD_ECUDA, "no CUDA device");
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return bail(SPOD_ECUDA, "device query failed");
+  p->num_sms = prop.multiProcessorCount;
   if (fft_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
     return bail(SPOD_EUNSUPPORTED, "nfft too large for the shared-memory FFT");
+  if (p->tensor && (gram_tc_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin ||
+                    modes_tc_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin))
+    return bail(SPOD_EUNSUPPORTED, "tensor-core kernels do not fit in shared memory for this nb");
+  if (p->tensor && prop.major < 10) return bail(SPOD_EUNSUPPORTED, "tensor-core path needs an sm_100-class GPU");
 
   // ---- sizes of the workspace
   const size_t R = p->f64 ? 8 : 4;
   const int64_t tile = 64;
-  const size_t per_point = (size_t)p->nf * 2 * p->nb * R;
+  // Qhat bytes per point: FP64/FP32 planar, or BF16 hi (+ lo for BF16X3)
+  const size_t qelem = p->tensor ? 2 : R;
+  const size_t nq = d->precision == SPOD_PREC_BF16X3 ? 2 : 1;
+  const size_t per_point = (size_t)p->nf * 2 * p->nb * qelem * nq;
   int64_t chunk = d->chunk_points;
   if (chunk == 0) {
     const size_t budget = (size_t)40 << 30;   // whole-array Qhat up to 40 GiB, else spatial chunks
@@ -241,10 +277,14 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     sp = std::max<int64_t>(1, std::min<int64_t>(sp, p->nt / 16 > 0 ? p->nt / 16 : 1));
     p->mean_splits = (int)std::min<int64_t>(sp, 4096);
   }
-  {
+  if (p->tensor) {
+    p->gram_splits = gram_tc_splits(*p, (chunk + 63) / 64);
+    p->gram_splits_max = (int)std::max<int64_t>(p->gram_splits, std::min<int64_t>(32, (chunk + 63) / 64));
+  } else {
     int64_t s = (2048 + p->nf - 1) / p->nf;
     s = std::max<int64_t>(1, std::min<int64_t>(s, (chunk + 255) / 256));
     p->gram_splits = (int)s;
+    p->gram_splits_max = (int)std::max<int64_t>(s, std::min<int64_t>(32, (chunk + 255) / 256));
   }
   const int nb = p->nb, nf = p->nf;
   size_t off = 0;
@@ -256,7 +296,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_tw = carve(2 * R * p->nfft);
   const size_t o_sqrtW = carve(R * p->Mpad);
   const size_t o_rsqrtW = carve(R * p->Mpad);
-  const size_t o_gpart = carve(sizeof(double) * 2 * (size_t)p->gram_splits * nf * nb * nb);
+  const size_t o_gpart = carve(sizeof(double) * 2 * (size_t)p->gram_splits_max * nf * nb * nb);
   const size_t o_gram = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
   const size_t o_lam = carve(sizeof(double) * (size_t)nf * nb);
   const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
@@ -288,6 +328,15 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_eigws = nb > kEigSmemMaxNb ? reinterpret_cast<double*>(b + o_eigws) : nullptr;
   p->d_bmat = b + o_bmat;
   p->d_qhat = b + o_qhat;
+  if (d->precision == SPOD_PREC_BF16X3)
+    p->d_qlo = b + o_qhat + (size_t)p->nf * 2 * p->nb * 2 * (size_t)chunk;
+  if (p->tensor) {
+    if (spod_status st = make_qhat_maps(p)) {
+      std::string msg = spod_last_error();
+      spod_plan_destroy(p);
+      return fail(st, msg);
+    }
+  }
 
   // ---- constant tables (host FP64, rounded once to the compute type)
   {
@@ -389,7 +438,8 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
       SPOD_CUDA(launch_fft_chunk(*p, d_X, m0, mc, s), "fft kernel");
     }
     Phase ph(p, SPOD_PHASE_GRAM, s, 1);
-    SPOD_CUDA(launch_gram_chunk(*p, mc, m0 == 0, s), "gram kernel");
+    if (p->tensor) SPOD_CUDA(launch_gram_tc_chunk(*p, mc, m0 == 0, s), "tensor-core gram kernel");
+    else SPOD_CUDA(launch_gram_chunk(*p, mc, m0 == 0, s), "gram kernel");
   }
   {
     Phase ph(p, SPOD_PHASE_REDUCE, s, 1);
@@ -464,7 +514,12 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
   }
   if (p->qhat_valid) {
     Phase ph(p, SPOD_PHASE_MODES, s, 0);
-    SPOD_CUDA(launch_modes_chunk(*p, 0, p->M, nmodes, d_Phi, s, &ph.n), "modes kernel");
+    if (p->tensor) {
+      SPOD_CUDA(launch_modes_tc_chunk(*p, 0, p->M, nmodes, d_Phi, s), "tensor-core modes kernel");
+      ph.n = 1;
+    } else {
+      SPOD_CUDA(launch_modes_chunk(*p, 0, p->M, nmodes, d_Phi, s, &ph.n), "modes kernel");
+    }
   } else {
     for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points) {
       const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
@@ -473,7 +528,12 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
         SPOD_CUDA(launch_fft_chunk(*p, d_X, m0, mc, s), "fft kernel");
       }
       Phase ph(p, SPOD_PHASE_MODES, s, 0);
-      SPOD_CUDA(launch_modes_chunk(*p, m0, mc, nmodes, d_Phi, s, &ph.n), "modes kernel");
+      if (p->tensor) {
+        SPOD_CUDA(launch_modes_tc_chunk(*p, m0, mc, nmodes, d_Phi, s), "tensor-core modes kernel");
+        ph.n = 1;
+      } else {
+        SPOD_CUDA(launch_modes_chunk(*p, m0, mc, nmodes, d_Phi, s, &ph.n), "modes kernel");
+      }
     }
   }
   p->last_stream = s;
@@ -522,6 +582,29 @@ spod_status spod_run_host(spod_plan_t p, const void* h_X, int nmodes, void* h_Ph
               "copy lambda to host");
   SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
   return read_flags(p);
+}
+
+spod_status spod_plan_get_tuning(spod_plan_t p, spod_tuning* t) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!t) return fail(SPOD_EINVAL, "tuning is NULL");
+  t->gram_splits = p->gram_splits;
+  t->gram_splits_max = p->gram_splits_max;
+  t->gram_flush_blocks = p->gram_flush;
+  t->modes_ctas = p->modes_ctas;
+  return SPOD_OK;
+}
+
+spod_status spod_plan_set_tuning(spod_plan_t p, const spod_tuning* t) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!t) return fail(SPOD_EINVAL, "tuning is NULL");
+  if (t->gram_splits < 0 || t->gram_splits > p->gram_splits_max)
+    return fail(SPOD_EINVAL, "gram_splits must be in 1..gram_splits_max");
+  if (t->gram_flush_blocks < 0 || t->gram_flush_blocks > 64) return fail(SPOD_EINVAL, "gram_flush_blocks must be in 1..64");
+  if (t->modes_ctas < 0 || t->modes_ctas > 4096) return fail(SPOD_EINVAL, "modes_ctas must be in 0..4096");
+  if (t->gram_splits) p->gram_splits = t->gram_splits;
+  if (t->gram_flush_blocks) p->gram_flush = t->gram_flush_blocks;
+  p->modes_ctas = t->modes_ctas;
+  return SPOD_OK;
 }
 
 spod_status spod_profile_enable(spod_plan_t p, int enable) {

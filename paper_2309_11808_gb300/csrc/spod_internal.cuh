@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libspod.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -55,7 +56,10 @@ struct spod_plan_s {
   // spatial chunking of the FFT -> Gram / modes pipeline
   int64_t chunk_points = 0;   // points per chunk (multiple of the FFT tile)
   int gram_splits = 1;        // CTAs per frequency per chunk in the Gram kernel
-  int tile_points = 16;       // points per FFT CTA
+  int gram_splits_max = 1;    // partial-Gram slots allocated
+  int gram_flush = 4;         // tensor-core Gram: blocks per FP32 accumulation group
+  int modes_ctas = 0;         // tensor-core modes: CTAs per frequency (0 = automatic)
+  int num_sms = 0;
 
   // device workspace (one allocation, carved)
   spod::Workspace ws;
@@ -66,7 +70,11 @@ struct spod_plan_s {
   void* d_tw = nullptr;            // [nfft] complex twiddles exp(-2 pi i k / nfft), compute type
   void* d_sqrtW = nullptr;         // [Mpad] sqrt(W) (0 in the padding), compute type
   void* d_rsqrtW = nullptr;        // [Mpad] 1/sqrt(W), compute type
-  void* d_qhat = nullptr;          // [nf][2*nb][chunk_points] compute type (planar re | im)
+  void* d_qhat = nullptr;          // [nf][2*nb][chunk_points] compute type (planar re | im); BF16 hi for tensor precisions
+  void* d_qlo = nullptr;           // BF16X3: the lo part, same layout
+  bool tensor = false;             // BF16 / BF16X3: Gram and modes on the tensor cores
+  CUtensorMap tmap_hi;            // TMA maps of d_qhat / d_qlo: dims {chunk, 2nb, nf}, box {64, round16(2nb), 1}
+  CUtensorMap tmap_lo;
   double* d_gpart = nullptr;       // [gram_splits][nf][nb][nb][2] FP64 partial Grams
   double* d_gram = nullptr;        // [nf][nb][nb][2] reduced Gram (kappa applied)
   double* d_lam = nullptr;         // [nf][nb]
@@ -106,6 +114,13 @@ cudaError_t launch_eig(const spod_plan_s& p, cudaStream_t s);
 cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s);
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes,
                                void* d_Phi, cudaStream_t s, int* nlaunch);
+
+cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
+cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
+                                  cudaStream_t s);
+size_t gram_tc_smem_bytes(const spod_plan_s& p);
+size_t modes_tc_smem_bytes(const spod_plan_s& p);
+int gram_tc_splits(const spod_plan_s& p, int64_t nkb);
 
 cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, double* psi, double* gws,
                                unsigned* flags, cudaStream_t s);
