@@ -1,0 +1,336 @@
+// Persistent block DFT (Eqs. blocks, blocks-ft, blocks-k) with a TMA ring.
+//
+// Persistent CTAs of 512 threads (two per SM for the compiled nfft values
+// 256/384/512/720, one otherwise) walk tiles of 16 spatial points; for each tile
+// it transforms the Welch blocks l = 0 .. nb-1 in order.  The tile's time rows
+// arrive by TMA into a ring of nfft + step rows: block 0 loads nfft rows, each
+// later block only its step new rows (the overlap is already resident), and
+// the next block's rows are requested while the current block is transformed,
+// so every sample of X is read from HBM once.  Per block: mean subtraction
+// (double-float pair), window c w_n, two real point series packed into one
+// complex sequence, an in-place shared-memory Stockham FFT (radix 8/4/2/3/5,
+// butterfly inputs held in registers across each pass), the two
+// real spectra separated, sqrt(W) folded in, and planar rows stored two points
+// per store (FP32, or BF16 hi [+ lo]).
+//
+// Requires M * sizeof(element) to be a multiple of 16 bytes (TMA row stride);
+// other shapes use the per-block kernel of k_fft.cu.
+#include "fft_common.cuh"
+#include "tc_common.cuh"
+
+namespace spod {
+namespace {
+
+using namespace fft;
+
+constexpr int RTP = 16;          // points per tile
+constexpr int RC = RTP / 2;      // complex columns (point pairs)
+constexpr int RTHREADS = 512;
+
+struct RingArgs {
+  int64_t M, m0, mcount, chunk, mpad, ntiles;
+  int nfft, step, nb, nf, boxr, ring;
+  int subtract_mean;
+  FftPlan fp;
+};
+
+struct RingHdr {
+  uint64_t full;
+  int abort;
+};
+
+// In-place Stockham pass over RC interleaved sequences: every thread loads the
+// inputs of its (at most MAXB) butterflies, the block synchronises, then every
+// thread writes its outputs.  MAXB = ceil(NMAX * RC / (RAD * RTHREADS)).
+template <int RAD, int MAXB>
+__device__ __forceinline__ void pass_inplace(float2* __restrict__ buf, const float2* __restrict__ tw, int n, int Ns,
+                                             int log2Ns) {
+  const int nbut = n / RAD;
+  const int stride_tw = n / (Ns * RAD);
+  constexpr int BSTEP = RTHREADS / RC;
+  const int col = threadIdx.x % RC;
+  const int b0 = threadIdx.x / RC;
+  float2 v[MAXB][RAD];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = b0 + i * BSTEP;
+    if (b < nbut) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) v[i][r] = buf[(b + r * nbut) * RC + col];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = b0 + i * BSTEP;
+    if (b < nbut) {
+      int k, g;
+      if (log2Ns >= 0) { k = b & (Ns - 1); g = b >> log2Ns; }
+      else { g = b / Ns; k = b - g * Ns; }
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) v[i][r] = cmul(v[i][r], tw[r * k * stride_tw]);
+      }
+      dft_small<RAD, float2, float>(v[i]);
+      const int base = g * Ns * RAD + k;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) buf[(base + r * Ns) * RC + col] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int NMAX, int RAD>
+struct MaxB {
+  static constexpr int value = (NMAX * RC + RAD * RTHREADS - 1) / (RAD * RTHREADS);
+};
+
+__host__ __device__ constexpr int ilog2_or_neg(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return (1 << l) == v ? l : -1;
+}
+
+// Compile-time radix sequence for a fixed nfft: strides and masks are constants.
+template <int N, int NS, int R0, int... RS>
+__device__ __forceinline__ void run_passes(float2* buf, const float2* tw) {
+  pass_inplace<R0, MaxB<N, R0>::value>(buf, tw, N, NS, ilog2_or_neg(NS));
+  if constexpr (sizeof...(RS) > 0) run_passes<N, NS * R0, RS...>(buf, tw);
+}
+
+// nfft values with a compiled pass sequence (0: runtime plan)
+template <int N> struct Seq;
+template <> struct Seq<256> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<256, 1, 8, 8, 4>(b, t); } };
+template <> struct Seq<384> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<384, 1, 8, 8, 2, 3>(b, t); } };
+template <> struct Seq<512> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<512, 1, 8, 8, 8>(b, t); } };
+template <> struct Seq<720> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<720, 1, 8, 2, 3, 3, 5>(b, t); } };
+
+template <typename Tin, int OUTK, int NMAX, int FIXN>
+__global__ void __launch_bounds__(RTHREADS, (FIXN > 0 && FIXN <= 512) ? 2 : 1) k_fft_ring(const __grid_constant__ CUtensorMap xmap,
+                                                          const float* __restrict__ win,
+                                                          const float2* __restrict__ tw_g,
+                                                          const float* __restrict__ sqrtW,
+                                                          const double* __restrict__ mu, void* __restrict__ qout,
+                                                          void* __restrict__ qout_lo, RingArgs a,
+                                                          unsigned* __restrict__ gflags) {
+  using namespace tc;
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  RingHdr* hdr = reinterpret_cast<RingHdr*>(sm);
+  Tin* ring = reinterpret_cast<Tin*>(sm + 1024);                        // [ring rows][RTP]
+  float2* buf = reinterpret_cast<float2*>(sm + 1024 + (size_t)a.ring * RTP * sizeof(Tin));
+  float2* tw = buf + (size_t)a.nfft * RC;
+  float* wsm = reinterpret_cast<float*>(tw + a.nfft);                   // c w_n
+  float* swt = wsm + a.nfft;                                            // sqrt(W) of the tile
+  const int N = a.nfft, S = a.step;
+  const int tid = threadIdx.x;
+  const uint32_t bar = smem_u32(&hdr->full);
+  volatile int* abort_flag = &hdr->abort;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    hdr->abort = 0;
+    fence_mbar_init();
+  }
+  for (int i = tid; i < N; i += RTHREADS) {
+    tw[i] = tw_g[i];
+    wsm[i] = win[i];
+  }
+  __syncthreads();
+
+  const int64_t t_first = blockIdx.x;
+  const int64_t t_step = gridDim.x;
+  if (t_first >= a.ntiles) return;
+  const uint32_t row_bytes = RTP * sizeof(Tin);
+
+  // issue the TMA boxes for time rows [r0, r0 + nrows) of tile t into the ring
+  auto issue = [&](int64_t t, int r0, int nrows) {
+    mbar_arrive_expect_tx(bar, (uint32_t)nrows * row_bytes);
+    const int x = (int)(a.m0 + t * RTP);
+    for (int r = r0; r < r0 + nrows; r += a.boxr) {
+      const int slot = r % a.ring;
+      tma_load_2d(smem_u32(ring + (size_t)slot * RTP), &xmap, x, r, bar);
+    }
+  };
+  if (tid == 0) {
+    prefetch_tmap(&xmap);
+    issue(t_first, 0, N);
+  }
+
+  const int j = tid % RC;            // copy phase: this thread's column (point pair)
+  const int n0 = tid / RC;
+  uint32_t phase = 0;
+  for (int64_t t = t_first; t < a.ntiles; t += t_step) {
+    const int64_t lm0 = t * RTP;
+    const int64_t gm0 = a.m0 + lm0;
+    float mhi0 = 0.f, mlo0 = 0.f, mhi1 = 0.f, mlo1 = 0.f;
+    {
+      const int64_t m = gm0 + 2 * j;
+      const int64_t mend = a.m0 + a.mcount;
+      if (a.subtract_mean && m < mend) { const double d = mu[m]; mhi0 = (float)d; mlo0 = (float)(d - (double)mhi0); }
+      if (a.subtract_mean && m + 1 < mend) {
+        const double d = mu[m + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
+      }
+      if (tid < RTP) swt[tid] = (lm0 + tid < a.mcount) ? sqrtW[gm0 + tid] : 0.f;
+    }
+    for (int l = 0; l < a.nb; ++l) {
+      mbar_wait(bar, phase & 1, abort_flag, gflags);
+      ++phase;
+      __syncthreads();
+      if (hdr->abort) break;
+      // ---- ring rows -> FFT buffer (mean, window, pack two points)
+      const int rbase = l * S;
+      const int rb = rbase % a.ring;
+      for (int n = n0; n < N; n += RTHREADS / RC) {
+        int slot = rb + n;
+        if (slot >= a.ring) slot -= a.ring;
+        const Tin* rp = ring + slot * RTP + 2 * j;
+        const float x0 = (to_f32<Tin>(rp[0]) - mhi0) - mlo0;
+        const float x1 = (to_f32<Tin>(rp[1]) - mhi1) - mlo1;
+        const float wn = wsm[n];
+        buf[n * RC + j] = make_float2(x0 * wn, x1 * wn);
+      }
+      __syncthreads();
+      // ---- request the next rows (ring slots of rows no longer needed)
+      if (tid == 0) {
+        if (l + 1 < a.nb) {
+          issue(t, rbase + N, S);
+        } else if (t + t_step < a.ntiles) {
+          issue(t + t_step, 0, N);
+        }
+      }
+      // ---- FFT (in place)
+      if constexpr (FIXN > 0) {
+        Seq<FIXN>::run(buf, tw);
+      } else {
+        int Ns = 1, log2Ns = 0;
+        for (int ps = 0; ps < a.fp.npass; ++ps) {
+          const int rad = a.fp.radix[ps];
+          switch (rad) {
+            case 8: pass_inplace<8, MaxB<NMAX, 8>::value>(buf, tw, N, Ns, log2Ns); break;
+            case 4: pass_inplace<4, MaxB<NMAX, 4>::value>(buf, tw, N, Ns, log2Ns); break;
+            case 2: pass_inplace<2, MaxB<NMAX, 2>::value>(buf, tw, N, Ns, log2Ns); break;
+            case 3: pass_inplace<3, MaxB<NMAX, 3>::value>(buf, tw, N, Ns, log2Ns); break;
+            default: pass_inplace<5, MaxB<NMAX, 5>::value>(buf, tw, N, Ns, log2Ns); break;
+          }
+          Ns *= rad;
+          if (log2Ns >= 0) log2Ns = (rad == 2) ? log2Ns + 1 : (rad == 4) ? log2Ns + 2 : (rad == 8) ? log2Ns + 3 : -1;
+        }
+      }
+      const float2* src = buf;
+      // ---- separate the two real spectra of each column, fold sqrt(W), store pairs
+      const int64_t rs = a.chunk;
+      // this thread's items: pair pp, frequencies f0, f0 + RTHREADS/RC, ...
+      const int pp = tid % RC;
+      const int f0 = tid / RC;
+      constexpr int FSTEP = RTHREADS / RC;
+      const int64_t fstride = (int64_t)FSTEP * 2 * a.nb * rs;
+      int64_t o_re = ((int64_t)f0 * 2 * a.nb + l) * rs + lm0 + 2 * pp;
+      const int64_t im_off = (int64_t)a.nb * rs;
+      const float sa = swt[2 * pp], sb = swt[2 * pp + 1];
+      for (int f = f0; f < a.nf; f += FSTEP, o_re += fstride) {
+        const float2 zf = src[f * RC + pp];
+        const float2 zc = src[((f == 0) ? 0 : N - f) * RC + pp];
+        // even point: (Z[f] + conj Z[N-f]) / 2 ; odd point: (Z[f] - conj Z[N-f]) / (2i)
+        const float ra = 0.5f * (zf.x + zc.x) * sa, ia = 0.5f * (zf.y - zc.y) * sa;
+        const float rb = 0.5f * (zf.y + zc.y) * sb, ib = -0.5f * (zf.x - zc.x) * sb;
+        const int64_t o_im = o_re + im_off;
+        if constexpr (OUTK == OUT_NATIVE) {
+          float* q = static_cast<float*>(qout);
+          *reinterpret_cast<float2*>(q + o_re) = make_float2(ra, rb);
+          *reinterpret_cast<float2*>(q + o_im) = make_float2(ia, ib);
+        } else {
+          __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
+          const __nv_bfloat162 hr = __floats2bfloat162_rn(ra, rb);
+          const __nv_bfloat162 hi = __floats2bfloat162_rn(ia, ib);
+          *reinterpret_cast<__nv_bfloat162*>(qh + o_re) = hr;
+          *reinterpret_cast<__nv_bfloat162*>(qh + o_im) = hi;
+          if constexpr (OUTK == OUT_BF16X3) {
+            __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qout_lo);
+            const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi);
+            *reinterpret_cast<__nv_bfloat162*>(ql + o_re) = __floats2bfloat162_rn(ra - fr.x, rb - fr.y);
+            *reinterpret_cast<__nv_bfloat162*>(ql + o_im) = __floats2bfloat162_rn(ia - fi.x, ib - fi.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (hdr->abort) break;
+  }
+  // a request issued before an abort must land before the CTA exits
+  if (tid == 0 && hdr->abort) mbar_wait(bar, phase & 1, abort_flag, gflags);
+}
+
+template <typename Tin, int OUTK, int NMAX, int FIXN>
+cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                          cudaStream_t s) {
+  RingArgs a;
+  a.M = p.M; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
+  a.mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
+  a.ntiles = a.mpad / RTP;
+  a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;
+  a.boxr = p.ring_boxr;
+  a.ring = p.nfft + p.step;
+  a.subtract_mean = p.desc.subtract_mean;
+  a.fp = p.fft;
+  const size_t smem = fft_ring_smem_bytes(p);
+  auto kern = k_fft_ring<Tin, OUTK, NMAX, FIXN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RTHREADS, smem);
+  per_sm = std::max(1, per_sm);
+  const int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)(p.num_sms > 0 ? p.num_sms : 148) * per_sm);
+  kern<<<grid, RTHREADS, smem, s>>>(xmap, static_cast<const float*>(p.d_win), static_cast<const float2*>(p.d_tw),
+                                    static_cast<const float*>(p.d_sqrtW), p.d_mu, p.d_qhat, p.d_qlo, a, p.d_flags);
+  return cudaGetLastError();
+}
+
+template <typename Tin, int OUTK>
+cudaError_t launch_ring_t(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                          cudaStream_t s) {
+  if constexpr (sizeof(Tin) != 8) {
+    switch (p.nfft) {
+      case 256: return launch_ring_n<Tin, OUTK, 256, 256>(p, xmap, m0, mcount, s);
+      case 384: return launch_ring_n<Tin, OUTK, 384, 384>(p, xmap, m0, mcount, s);
+      case 512: return launch_ring_n<Tin, OUTK, 512, 512>(p, xmap, m0, mcount, s);
+      case 720: return launch_ring_n<Tin, OUTK, 720, 720>(p, xmap, m0, mcount, s);
+      default: break;
+    }
+  }
+  if (p.nfft <= 512) return launch_ring_n<Tin, OUTK, 512, 0>(p, xmap, m0, mcount, s);
+  return launch_ring_n<Tin, OUTK, 1024, 0>(p, xmap, m0, mcount, s);
+}
+
+template <typename Tin>
+cudaError_t launch_ring_in(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                           cudaStream_t s) {
+  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_ring_t<Tin, OUT_BF16X3>(p, xmap, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16) return launch_ring_t<Tin, OUT_BF16>(p, xmap, m0, mcount, s);
+  return launch_ring_t<Tin, OUT_NATIVE>(p, xmap, m0, mcount, s);
+}
+
+}  // namespace
+
+size_t fft_ring_smem_bytes(const spod_plan_s& p) {
+  const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
+  return 1024 + 1024 + (size_t)(p.nfft + p.step) * RTP * el + sizeof(float2) * ((size_t)p.nfft * RC + p.nfft) +
+         sizeof(float) * (p.nfft + RTP);
+}
+
+bool fft_ring_usable(const spod_plan_s& p, int smem_optin) {
+  if (p.f64) return false;
+  const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
+  if ((p.M * (int64_t)el) % 16 != 0) return false;        // TMA row stride
+  if (p.ring_boxr <= 0 || p.nfft > 1024) return false;
+  return fft_ring_smem_bytes(p) <= (size_t)smem_optin;
+}
+
+cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                                  cudaStream_t s) {
+  if (p.desc.in_dtype == SPOD_F64) return launch_ring_in<double>(p, xmap, m0, mcount, s);
+  if (p.desc.in_dtype == SPOD_F32) return launch_ring_in<float>(p, xmap, m0, mcount, s);
+  return launch_ring_in<__nv_bfloat16>(p, xmap, m0, mcount, s);
+}
+
+}  // namespace spod

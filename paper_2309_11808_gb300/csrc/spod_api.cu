@@ -120,15 +120,45 @@ struct Phase {
   }
 };
 
-// TMA maps of the BF16 Qhat planes: dims {chunk points, 2 nb rows, nf}, box
-// {64 points, 2 nb rounded up to 16 rows, 1}; rows past 2 nb read as zeros.
-spod_status make_qhat_maps(spod_plan_s* p) {
+void* driver_encode_fn() {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-    return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
-  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) return nullptr;
+  return fn;
+}
+
+// TMA map of X for the ring FFT: dims {M, nt}, box {16 points, ring_boxr rows}.
+spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) {
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
+  if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available");
+  const size_t el = elem_bytes(p->desc.in_dtype);
+  const CUtensorMapDataType dt = p->desc.in_dtype == SPOD_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : p->desc.in_dtype == SPOD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[2] = {(cuuint64_t)p->M, (cuuint64_t)p->nt};
+  const cuuint64_t strides[1] = {(cuuint64_t)p->M * el};
+  const cuuint32_t box[2] = {16, (cuuint32_t)p->ring_boxr};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, dt, 2, const_cast<void*>(d_X), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled (X) failed (" + std::to_string((int)r) + ")");
+  return SPOD_OK;
+}
+
+// FFT of one spatial chunk: the TMA-ring kernel when the shape allows it.
+spod_status run_fft_chunk(spod_plan_s* p, const void* d_X, const CUtensorMap* xmap, int64_t m0, int64_t mc,
+                          cudaStream_t s) {
+  cudaError_t e = xmap ? launch_fft_ring_chunk(*p, *xmap, m0, mc, s) : launch_fft_chunk(*p, d_X, m0, mc, s);
+  if (e != cudaSuccess) return cuda_fail(e, "fft kernel");
+  return SPOD_OK;
+}
+
+// TMA maps of the BF16 Qhat planes: dims {chunk points, 2 nb rows, nf}, box
+// {64 points, 2 nb rounded up to 16 rows, 1}; rows past 2 nb read as zeros.
+spod_status make_qhat_maps(spod_plan_s* p) {
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
+  if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
   const cuuint64_t dims[3] = {(cuuint64_t)p->chunk_points, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf};
   const cuuint64_t strides[2] = {(cuuint64_t)p->chunk_points * 2, (cuuint64_t)(2 * p->nb) * p->chunk_points * 2};
   const cuuint32_t box[3] = {64, (cuuint32_t)((2 * p->nb + 15) / 16 * 16), 1};
@@ -248,6 +278,18 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return bail(SPOD_ECUDA, "device query failed");
   p->num_sms = prop.multiProcessorCount;
+  p->encode_fn = driver_encode_fn();
+  {
+    // ring FFT: TMA boxes of ring_boxr rows must tile both nfft and step (largest such <= 256)
+    int g = p->nfft, b = p->step;
+    while (b) { const int t = g % b; g = b; b = t; }
+    int boxr = 0;
+    for (int d = std::min(g, 256); d >= 1; --d)
+      if (g % d == 0) { boxr = d; break; }
+    const size_t rowb = 16 * elem_bytes(d->in_dtype);
+    p->ring_boxr = ((size_t)boxr * rowb) % 128 == 0 ? boxr : 0;
+    p->ring_ok = p->encode_fn && fft_ring_usable(*p, (int)prop.sharedMemPerBlockOptin);
+  }
   if (fft_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
     return bail(SPOD_EUNSUPPORTED, "nfft too large for the shared-memory FFT");
   if (p->tensor && (gram_tc_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin ||
@@ -430,12 +472,18 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
   } else {
     SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M, s), "zero mean");
   }
+  alignas(64) CUtensorMap xmap;
+  const CUtensorMap* xm = nullptr;
+  if (p->ring_ok) {
+    if (spod_status st = make_x_map(p, d_X, &xmap)) return st;
+    xm = &xmap;
+  }
   int64_t nchunks = 0;
   for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points, ++nchunks) {
     const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
     {
       Phase ph(p, SPOD_PHASE_FFT, s, 1);
-      SPOD_CUDA(launch_fft_chunk(*p, d_X, m0, mc, s), "fft kernel");
+      if (spod_status st = run_fft_chunk(p, d_X, xm, m0, mc, s)) return st;
     }
     Phase ph(p, SPOD_PHASE_GRAM, s, 1);
     if (p->tensor) SPOD_CUDA(launch_gram_tc_chunk(*p, mc, m0 == 0, s), "tensor-core gram kernel");
@@ -521,11 +569,17 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
       SPOD_CUDA(launch_modes_chunk(*p, 0, p->M, nmodes, d_Phi, s, &ph.n), "modes kernel");
     }
   } else {
+    alignas(64) CUtensorMap xmap;
+    const CUtensorMap* xm = nullptr;
+    if (p->ring_ok) {
+      if (spod_status st = make_x_map(p, d_X, &xmap)) return st;
+      xm = &xmap;
+    }
     for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points) {
       const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
       {
         Phase ph(p, SPOD_PHASE_FFT, s, 1);
-        SPOD_CUDA(launch_fft_chunk(*p, d_X, m0, mc, s), "fft kernel");
+        if (spod_status st = run_fft_chunk(p, d_X, xm, m0, mc, s)) return st;
       }
       Phase ph(p, SPOD_PHASE_MODES, s, 0);
       if (p->tensor) {

@@ -59,6 +59,9 @@ struct spod_plan_s {
   int gram_splits_max = 1;    // partial-Gram slots allocated
   int gram_flush = 4;         // tensor-core Gram: blocks per FP32 accumulation group
   int modes_ctas = 0;         // tensor-core modes: CTAs per frequency (0 = automatic)
+  int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
+  bool ring_ok = false;
+  void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   int num_sms = 0;
 
   // device workspace (one allocation, carved)
@@ -126,6 +129,10 @@ cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, 
                                unsigned* flags, cudaStream_t s);
 
 size_t fft_smem_bytes(const spod_plan_s& p);
+size_t fft_ring_smem_bytes(const spod_plan_s& p);
+bool fft_ring_usable(const spod_plan_s& p, int smem_optin);
+cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                                  cudaStream_t s);
 size_t eig_smem_bytes(int nb);
 
 void set_error(const std::string& msg);
