@@ -117,3 +117,40 @@ class SPOD:
 
     def sync(self, stream=None) -> None:
         _lib.spod_sync(self.handle, stream or torch.cuda.current_stream())
+
+
+class SpodEigs(torch.autograd.Function):
+    """lambda = SPOD eigenvalues of X ([nf][nb], FP64) with a hand-written adjoint.
+
+    Forward: spod_fit.  Backward: spod_backward (the adjoint kernels carry
+    dL/dlambda back through the Gram, the inverse DFT, the window, the
+    overlap-add and the mean subtraction; Qhat is reused or recomputed, never
+    stored per step).  Valid for simple eigenvalues.  The plan keeps the state
+    of its last fit: run backward before fitting other data with the same plan.
+    """
+
+    @staticmethod
+    def forward(ctx, X: torch.Tensor, plan: "SPOD"):
+        plan.fit(X)
+        lam = torch.empty((plan.nf, plan.nb), dtype=torch.float64, device=X.device)
+        _lib.spod_get_eigs(plan.handle, lam, None, on_device=True)
+        ctx.plan = plan
+        ctx.save_for_backward(X)
+        return lam
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        (X,) = ctx.saved_tensors
+        plan = ctx.plan
+        dX = torch.empty(X.shape, dtype=torch.float64 if plan.f64 else torch.float32, device=X.device)
+        _lib.spod_backward(plan.handle, g.detach().contiguous().to(torch.float64), X, dX,
+                           torch.cuda.current_stream(X.device))
+        return dX.to(X.dtype), None
+
+
+def spod_eigs(X: torch.Tensor, plan: "SPOD") -> torch.Tensor:
+    """Differentiable SPOD eigenvalues (see SpodEigs)."""
+    return SpodEigs.apply(X, plan)
+
+
+__all__ += ["SpodEigs", "spod_eigs"]

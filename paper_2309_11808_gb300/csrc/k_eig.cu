@@ -298,7 +298,7 @@ cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s)
 
 template <typename R>
 static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, int* nlaunch) {
+                                  cudaStream_t s, int* nlaunch, bool adjoint) {
   // point tile and mode group sized to stay within 160 KB of shared memory
   const size_t cap = 160 * 1024;
   int tpm = 128;
@@ -314,7 +314,8 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
     const int kc = std::min(kg, nmodes - k0);
     const size_t smem = sizeof(R) * 2 * (size_t)p.nb * (tpm + kc);
     kern<<<grid, tpm, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, nmodes, k0, kc, mcount, m0,
-                                 p.M, static_cast<const R*>(p.d_bmat), static_cast<const R*>(p.d_rsqrtW),
+                                 p.M, static_cast<const R*>(p.d_bmat),
+                                 static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW),
                                  static_cast<R*>(d_Phi));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -324,9 +325,9 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
 }
 
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                               cudaStream_t s, int* nlaunch) {
-  return p.f64 ? launch_modes_t<double>(p, m0, mcount, nmodes, d_Phi, s, nlaunch)
-               : launch_modes_t<float>(p, m0, mcount, nmodes, d_Phi, s, nlaunch);
+                               cudaStream_t s, int* nlaunch, bool adjoint) {
+  return p.f64 ? launch_modes_t<double>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint)
+               : launch_modes_t<float>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint);
 }
 
 }  // namespace spod

@@ -223,7 +223,8 @@ size_t modes_tc_smem_bytes(const spod_plan_s& p) {
 }
 
 cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, bool adjoint) {
+  const float* scale = static_cast<const float*>(adjoint ? p.d_sqrtW : p.d_rsqrtW);
   ModesTcArgs a;
   a.nb = p.nb;
   a.nmodes = nmodes;
@@ -251,14 +252,12 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
     cudaError_t e = cudaFuncSetAttribute(k_modes_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_modes_tc<true><<<grid, 192, smem, s>>>(p.tmap_hi, p.tmap_lo, a, static_cast<const float*>(p.d_bmat),
-                                             static_cast<const float*>(p.d_rsqrtW), static_cast<float2*>(d_Phi),
-                                             p.d_flags);
+                                             scale, static_cast<float2*>(d_Phi), p.d_flags);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_modes_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_modes_tc<false><<<grid, 192, smem, s>>>(p.tmap_hi, p.tmap_hi, a, static_cast<const float*>(p.d_bmat),
-                                              static_cast<const float*>(p.d_rsqrtW), static_cast<float2*>(d_Phi),
-                                              p.d_flags);
+                                              scale, static_cast<float2*>(d_Phi), p.d_flags);
   }
   return cudaGetLastError();
 }

@@ -344,6 +344,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
   const size_t o_eigws = nb > kEigSmemMaxNb ? carve(sizeof(double) * 4 * (size_t)nf * nb * nb) : 0;
   const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
+  const size_t o_wc = carve(2 * R * (size_t)nf);
   const size_t o_qhat = carve(per_point * (size_t)chunk);
   p->ws.bytes = off;
   {
@@ -369,6 +370,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_psi = reinterpret_cast<double*>(b + o_psi);
   p->d_eigws = nb > kEigSmemMaxNb ? reinterpret_cast<double*>(b + o_eigws) : nullptr;
   p->d_bmat = b + o_bmat;
+  p->d_wc = b + o_wc;
   p->d_qhat = b + o_qhat;
   if (d->precision == SPOD_PREC_BF16X3)
     p->d_qlo = b + o_qhat + (size_t)p->nf * 2 * p->nb * 2 * (size_t)chunk;
@@ -383,7 +385,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   // ---- constant tables (host FP64, rounded once to the compute type)
   {
     const int N = p->nfft;
-    std::vector<double> win(N), tw(2 * N);
+    std::vector<double> win(N), tw(2 * N), wc(2 * (size_t)p->nf, 0.0);
     const double pi = 3.14159265358979323846;
     for (int n = 0; n < N; ++n) {
       win[n] = p->c * p->w[n];
@@ -406,6 +408,20 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     if (e == cudaSuccess) e = up(p->d_tw, tw);
     if (e == cudaSuccess) e = up(p->d_sqrtW, sq);
     if (e == cudaSuccess) e = up(p->d_rsqrtW, rsq);
+    if (e == cudaSuccess) {
+      // Wc_f = c sum_n w_n exp(+2 pi i f n / N), angle reduced exactly in integers
+      for (int f = 0; f < p->nf; ++f) {
+        double re = 0.0, im = 0.0;
+        for (int n = 0; n < N; ++n) {
+          const double ang = 2.0 * pi * (double)(((int64_t)f * n) % N) / (double)N;
+          re += p->w[n] * std::cos(ang);
+          im += p->w[n] * std::sin(ang);
+        }
+        wc[2 * f] = p->c * re;
+        wc[2 * f + 1] = p->c * im;
+      }
+      e = up(p->d_wc, wc);
+    }
     if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, 4 * sizeof(unsigned));
     if (e != cudaSuccess) {
       spod_status st = cuda_fail(e, "upload tables");
@@ -428,6 +444,7 @@ spod_status spod_plan_destroy(spod_plan_t p) {
     if (p->d_xstage) cudaFree(p->d_xstage);
     if (p->d_phistage) cudaFree(p->d_phistage);
     if (p->d_gradlam) cudaFree(p->d_gradlam);
+    if (p->d_radj) cudaFree(p->d_radj);
     for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : p->ev_free) cudaEventDestroy(e);
   }
@@ -597,8 +614,52 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
 spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* d_X, void* d_dX, void* stream) {
   if (spod_status st = check_plan(p)) return st;
   if (!p->fitted) return fail(SPOD_ESTATE, "spod_backward before spod_fit");
-  (void)d_dLdlambda; (void)d_X; (void)d_dX; (void)stream;
-  return fail(SPOD_EUNSUPPORTED, "spod_backward is not built in this library version");
+  if (!d_dLdlambda || reinterpret_cast<uintptr_t>(d_dLdlambda) % 8) return fail(SPOD_EINVAL, "d_dLdlambda NULL or misaligned");
+  if (spod_status st = check_ptr(d_dX, "d_dX")) return st;
+  if (!p->qhat_valid) {
+    if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  }
+  if (adjoint_smem_bytes(*p) > 227 * 1024) return fail(SPOD_EUNSUPPORTED, "nfft too large for the adjoint kernel");
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t rb = (size_t)p->nf * p->nb * p->M * 2 * (p->f64 ? 8 : 4);
+  if (p->radj_bytes < rb) {
+    // R_f of the adjoint, kept for later calls (allocated on first use)
+    SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    if (p->d_radj) cudaFree(p->d_radj);
+    p->d_radj = nullptr;
+    p->radj_bytes = 0;
+    if (cudaMalloc(&p->d_radj, rb) != cudaSuccess) { cudaGetLastError(); return fail(SPOD_ENOMEM, "adjoint buffer"); }
+    p->radj_bytes = rb;
+  }
+  Phase ph(p, SPOD_PHASE_BACKWARD, s, 0);
+  SPOD_CUDA(launch_adj_gmat(*p, d_dLdlambda, s), "adjoint G kernel");
+  ph.n += 1;
+  alignas(64) CUtensorMap xmap;
+  const CUtensorMap* xm = nullptr;
+  if (!p->qhat_valid && p->ring_ok) {
+    if (spod_status st = make_x_map(p, d_X, &xmap)) return st;
+    xm = &xmap;
+  }
+  for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points) {
+    const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
+    if (!p->qhat_valid) {
+      if (spod_status st = run_fft_chunk(p, d_X, xm, m0, mc, s)) return st;
+      ph.n += 1;
+    }
+    if (p->tensor) {
+      SPOD_CUDA(launch_modes_tc_chunk(*p, m0, mc, p->nb, p->d_radj, s, true), "adjoint R kernel (tensor cores)");
+      ph.n += 1;
+    } else {
+      int nl = 0;
+      SPOD_CUDA(launch_modes_chunk(*p, m0, mc, p->nb, p->d_radj, s, &nl, true), "adjoint R kernel");
+      ph.n += nl;
+    }
+    SPOD_CUDA(launch_adjoint_chunk(*p, p->d_radj, p->M, m0, mc, d_dX, s), "adjoint kernel");
+    ph.n += 1;
+  }
+  p->last_stream = s;
+  return SPOD_OK;
 }
 
 spod_status spod_run_host(spod_plan_t p, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,

@@ -83,7 +83,10 @@ struct spod_plan_s {
   double* d_lam = nullptr;         // [nf][nb]
   double* d_psi = nullptr;         // [nf][nb][nb][2]
   double* d_eigws = nullptr;       // [nf][2][nbp][nbp][2] eigen-solver scratch (large nb)
-  void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa)
+  void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa), or G_f
+  void* d_wc = nullptr;            // [nf] complex compute type: c sum_n w_n e^{+2 pi i f n / nfft}
+  void* d_radj = nullptr;          // [nf][nb][M] complex compute type: R_f of the adjoint (allocated on first use)
+  size_t radj_bytes = 0;
   unsigned* d_flags = nullptr;     // [4]
 
   bool fitted = false;
@@ -116,11 +119,15 @@ cudaError_t launch_gram_reduce(const spod_plan_s& p, cudaStream_t s);
 cudaError_t launch_eig(const spod_plan_s& p, cudaStream_t s);
 cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s);
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes,
-                               void* d_Phi, cudaStream_t s, int* nlaunch);
+                               void* d_Phi, cudaStream_t s, int* nlaunch, bool adjoint = false);
+cudaError_t launch_adj_gmat(const spod_plan_s& p, const double* d_g, cudaStream_t s);
+cudaError_t launch_adjoint_chunk(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t m0, int64_t mcount,
+                                 void* d_dX, cudaStream_t s);
+size_t adjoint_smem_bytes(const spod_plan_s& p);
 
 cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
 cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s);
+                                  cudaStream_t s, bool adjoint = false);
 size_t gram_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_tc_smem_bytes(const spod_plan_s& p);
 int gram_tc_splits(const spod_plan_s& p, int64_t nkb);
