@@ -284,8 +284,8 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     int g = p->nfft, b = p->step;
     while (b) { const int t = g % b; g = b; b = t; }
     int boxr = 0;
-    for (int d = std::min(g, 256); d >= 1; --d)
-      if (g % d == 0) { boxr = d; break; }
+    for (int dv = std::min(g, 256); dv >= 1; --dv)
+      if (g % dv == 0) { boxr = dv; break; }
     const size_t rowb = 16 * elem_bytes(d->in_dtype);
     p->ring_boxr = ((size_t)boxr * rowb) % 128 == 0 ? boxr : 0;
     p->ring_ok = p->encode_fn && fft_ring_usable(*p, (int)prop.sharedMemPerBlockOptin);
@@ -342,7 +342,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_gram = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
   const size_t o_lam = carve(sizeof(double) * (size_t)nf * nb);
   const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
-  const size_t o_eigws = nb > kEigSmemMaxNb ? carve(sizeof(double) * 4 * (size_t)nf * nb * nb) : 0;
+  const size_t o_eigws = nb > kEigSmemMaxNb ? carve(sizeof(double) * eig_tridiag_gws_doubles(nb, nf)) : 0;
   const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
   const size_t o_wc = carve(2 * R * (size_t)nf);
   const size_t o_qhat = carve(per_point * (size_t)chunk);
@@ -512,7 +512,7 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
   }
   {
     Phase ph(p, SPOD_PHASE_EIG, s, 1);
-    SPOD_CUDA(launch_eig(*p, s), "eigen-solver kernel");
+    SPOD_CUDA(launch_eig_tridiag(*p, s), "eigen-solver kernel");
   }
   p->fitted = true;
   p->qhat_valid = nchunks == 1;

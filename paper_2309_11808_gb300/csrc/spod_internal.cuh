@@ -141,6 +141,9 @@ bool fft_ring_usable(const spod_plan_s& p, int smem_optin);
 cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                                   cudaStream_t s);
 size_t eig_smem_bytes(int nb);
+size_t eig_tridiag_smem_bytes(int nb);
+size_t eig_tridiag_gws_doubles(int nb, int nf);
+cudaError_t launch_eig_tridiag(const spod_plan_s& p, cudaStream_t s);
 
 void set_error(const std::string& msg);
 
