@@ -16,12 +16,13 @@
 // B operand (N = NP) of tcgen05.mma.cta_group::1.kind::f16, K = 16 per
 // instruction, 4 instructions per 64-point block (x3 for BF16X3).
 //
-// Warp roles (192 threads): warp 4 lane 0 issues TMA into a 4-stage ring,
-// warp 5 lane 0 issues the MMAs, warps 0-3 (one per TMEM lane quadrant) drain
+// Warp roles (320 threads): warp 8 lane 0 issues TMA into a 4-stage ring,
+// warp 9 lane 0 issues the MMAs, warps 0-7 (two per TMEM lane quadrant) drain
 // the accumulators every `flush` blocks of 64 points (short FP32 runs in the
 // tensor core) and add them into compensated FP32 (sum, carry) registers.
 // The accumulators are double-buffered in TMEM so draining overlaps the next
-// group's MMAs.  Partials per (split, frequency) go to the same FP64 buffer as
+// group's MMAs; the drain stages S1 = A1 + A2 and S2 = A2 in shared memory
+// (Y Y^T = S1 + S2^T) with one TMEM wait per 32 columns.  Partials per (split, frequency) go to the same FP64 buffer as
 // the SIMT kernel and are reduced in fixed order by k_gram_reduce.
 #include "tc_common.cuh"
 
@@ -30,7 +31,11 @@ namespace {
 
 constexpr int kStages = 4;
 constexpr int kTileBytes = 128 * 128;     // 128 rows x 64 BF16
-constexpr int kMaxPerThread = 17;         // nb <= 64: nb (nb+1) / 2 <= 17 * 128
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kThreadsGram = (kEpiWarps + 2) * 32;
+constexpr int kMaxPerThread = 9;          // nb <= 64: nb (nb+1) / 2 <= 9 * 256
 constexpr uint32_t kTmemCols = 512;       // buffer b: A1 at 256 b, A2 at 256 b + 128
 
 struct GramTcArgs {
@@ -55,7 +60,7 @@ struct GramHdr {
 };
 
 template <bool X3>
-__global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUtensorMap map_hi,
+__global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_constant__ CUtensorMap map_hi,
                                                    const __grid_constant__ CUtensorMap map_lo, GramTcArgs a,
                                                    double* __restrict__ gpart, unsigned* __restrict__ gflags) {
   using namespace tc;
@@ -65,8 +70,9 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUte
   GramHdr* hdr = reinterpret_cast<GramHdr*>(sm);
   uint8_t* stages = sm + 1024;
   const int RS = a.rows2 | 1;               // odd staging stride: conflict-free rows and columns
-  float* Ds = reinterpret_cast<float*>(stages + kStages * NOPS * kTileBytes);
-  uint32_t* pairs = reinterpret_cast<uint32_t*>(Ds + a.rows2 * RS);
+  float* Ds = reinterpret_cast<float*>(stages + kStages * NOPS * kTileBytes);   // S1 = A1 + A2
+  float* Qs = Ds + a.rows2 * RS;                                                  // S2 = A2 (BF16X3)
+  uint32_t* pairs = reinterpret_cast<uint32_t*>(Qs + (X3 ? a.rows2 * RS : 0));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s_idx = blockIdx.x, f = blockIdx.y;
@@ -83,13 +89,13 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUte
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&hdr->accfull[i]), 1);
-      mbar_init(smem_u32(&hdr->accempty[i]), 128);
+      mbar_init(smem_u32(&hdr->accempty[i]), kEpiThreads);
     }
     mbar_init(smem_u32(&hdr->drain), 1);
     hdr->abort = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == kMmaWarp) {
     tmem_alloc(smem_u32(&hdr->tmem_base), kTmemCols);
     tmem_relinquish();
   }
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUte
   const uint32_t tmem = hdr->tmem_base;
   volatile int* abort_flag = &hdr->abort;
 
-  if (warp == 4 && lane == 0 && nkbl > 0) {
+  if (warp == kTmaWarp && lane == 0 && nkbl > 0) {
     // ---------------- TMA producer
     prefetch_tmap(&map_hi);
     if (X3) prefetch_tmap(&map_lo);
@@ -133,7 +139,7 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUte
     // copies still in flight must land before the CTA can exit
     for (int kb = max(0, issued - kStages); kb < issued; ++kb)
       mbar_wait(smem_u32(&hdr->full[kb % kStages]), (kb / kStages) & 1, abort_flag, gflags);
-  } else if (warp == 5 && lane == 0 && nkbl > 0) {
+  } else if (warp == kMmaWarp && lane == 0 && nkbl > 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(128, a.np, 0, 0);
     for (int kb = 0; kb < nkbl; ++kb) {
@@ -164,70 +170,70 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUte
     }
     mma_commit(smem_u32(&hdr->drain));
     mbar_wait(smem_u32(&hdr->drain), 0, abort_flag, gflags);
-  } else if (warp < 4) {
+  } else if (warp < kEpiWarps) {
     // ---------------- epilogue: TMEM -> FP32 staging -> compensated FP32 sums
     float sr[kMaxPerThread], cr[kMaxPerThread], si[kMaxPerThread], ci[kMaxPerThread];
 #pragma unroll
     for (int j = 0; j < kMaxPerThread; ++j) { sr[j] = 0.f; cr[j] = 0.f; si[j] = 0.f; ci[j] = 0.f; }
-    const int row = warp * 32 + lane;
+    const int row = (warp & 3) * 32 + lane;
+    const int half = warp >> 2;               // takes the 32-column chunks c0 = 32 (2 k + half)
     const int nb = a.nb, r2 = a.rows2;
     for (int g = 0; g < ngroups; ++g) {
       const int acc = g & 1;
       // every epilogue thread takes the same stop/continue decision, so none
       // can be left behind in a named barrier
       mbar_wait(smem_u32(&hdr->accfull[acc]), (g >> 1) & 1, abort_flag, gflags);
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
       if (tid == 0) hdr->decision = *abort_flag;
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
       if (hdr->decision) break;
       tc_fence_after();
-      const uint32_t t1 = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)acc * 256u;
-      // D = A1 + A2 (rows), then D += A2^T (columns)
-      for (int c0 = 0; c0 < a.np; c0 += 16) {
-        float v[16], w[16];
-        tmem_ld16(t1 + c0, v);
+      const uint32_t t1 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)acc * 256u;
+      // stage S1 = A1 + A2 and S2 = A2 row by row (D = S1 + S2^T); 32 columns of
+      // each accumulator per load batch, one wait per batch
+      for (int c0 = 32 * half; c0 < a.np; c0 += 64) {
+        float v[32], w[32];
         if (X3) {
-          tmem_ld16(t1 + 128 + c0, w);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += w[i];
+          tmem_ld32x2(t1 + c0, t1 + 128 + c0, v, w);
+        } else {
+          tmem_ld32x2(t1 + c0, t1 + c0, v, w);
         }
         if (row < r2) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c0 + i < r2) Ds[row * RS + c0 + i] = v[i];
-        }
-      }
-      if (X3) {
-        named_sync(1, 128);
-        for (int c0 = 0; c0 < a.np; c0 += 16) {
-          float w[16];
-          tmem_ld16(t1 + 128 + c0, w);
-          if (row < r2) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (c0 + i < r2) Ds[(c0 + i) * RS + row] += w[i];
+          for (int i = 0; i < 32; ++i) {
+            if (c0 + i < r2) {
+              Ds[row * RS + c0 + i] = X3 ? v[i] + w[i] : v[i];
+              if (X3) Qs[row * RS + c0 + i] = w[i];
+            }
           }
         }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&hdr->accempty[acc]));
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
 #pragma unroll
       for (int j = 0; j < kMaxPerThread; ++j) {
-        const int e = tid + 128 * j;
+        const int e = tid + kEpiThreads * j;
         if (e < a.ne) {
           const uint32_t pr = pairs[e];
           const int l = pr & 0xFFFF, lp = pr >> 16;
-          comp_add(sr[j], cr[j], Ds[l * RS + lp] + Ds[(nb + l) * RS + nb + lp]);
-          comp_add(si[j], ci[j], Ds[l * RS + nb + lp] - Ds[(nb + l) * RS + lp]);
+          // D[i][k] = S1[i][k] + S2[k][i]
+          float d1 = Ds[l * RS + lp] + Ds[(nb + l) * RS + nb + lp];
+          float d2 = Ds[l * RS + nb + lp] - Ds[(nb + l) * RS + lp];
+          if (X3) {
+            d1 += Qs[lp * RS + l] + Qs[(nb + lp) * RS + nb + l];
+            d2 += Qs[(nb + lp) * RS + l] - Qs[lp * RS + nb + l];
+          }
+          comp_add(sr[j], cr[j], d1);
+          comp_add(si[j], ci[j], d2);
         }
       }
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
     }
     double* gp = gpart + (((int64_t)s_idx * a.nf + f) * nb) * nb * 2;
 #pragma unroll
     for (int j = 0; j < kMaxPerThread; ++j) {
-      const int e = tid + 128 * j;
+      const int e = tid + kEpiThreads * j;
       if (e < a.ne) {
         const uint32_t pr = pairs[e];
         const int l = pr & 0xFFFF, lp = pr >> 16;
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUte
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
@@ -252,7 +258,8 @@ size_t gram_tc_smem_bytes(const spod_plan_s& p) {
   const int nops = p.desc.precision == SPOD_PREC_BF16X3 ? 2 : 1;
   const int r2 = 2 * p.nb;
   const int ne = p.nb * (p.nb + 1) / 2;
-  return 1024 + 1024 + (size_t)kStages * nops * kTileBytes + sizeof(float) * r2 * (r2 | 1) + sizeof(uint32_t) * ne;
+  return 1024 + 1024 + (size_t)kStages * nops * kTileBytes + sizeof(float) * r2 * (r2 | 1) * nops +
+         sizeof(uint32_t) * ne;
 }
 
 int gram_tc_splits(const spod_plan_s& p, int64_t nkb) {
@@ -287,11 +294,11 @@ cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool firs
   if (p.desc.precision == SPOD_PREC_BF16X3) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<true><<<grid, 192, smem, s>>>(p.tmap_hi, p.tmap_lo, a, p.d_gpart, p.d_flags);
+    k_gram_tc<true><<<grid, kThreadsGram, smem, s>>>(p.tmap_hi, p.tmap_lo, a, p.d_gpart, p.d_flags);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<false><<<grid, 192, smem, s>>>(p.tmap_hi, p.tmap_hi, a, p.d_gpart, p.d_flags);
+    k_gram_tc<false><<<grid, kThreadsGram, smem, s>>>(p.tmap_hi, p.tmap_hi, a, p.d_gpart, p.d_flags);
   }
   return cudaGetLastError();
 }

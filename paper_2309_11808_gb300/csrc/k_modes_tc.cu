@@ -11,9 +11,10 @@
 // the same box the Gram kernel uses.  Then D[k][p] = Re Phi[p][k] and
 // D[nmodes + k][p] = Im Phi[p][k].  BF16X3 adds A_hi B_lo + A_lo B_hi.
 //
-// Warp roles as in the Gram kernel: warp 4 TMA, warp 5 MMA, warps 0-3 drain
-// TMEM (double-buffered accumulators) through shared memory into coalesced
-// complex stores of Phi[f][k][m].
+// Warp roles (320 threads): warp 8 issues TMA, warp 9 the MMAs; warps 0-7 drain
+// TMEM (double-buffered accumulators; warps w and w+4 share a lane quadrant and
+// take one 32-column half each) through shared memory into coalesced complex
+// stores of Phi[f][k][m].
 #include <algorithm>
 
 #include "tc_common.cuh"
@@ -24,6 +25,10 @@ namespace {
 constexpr int kStages = 4;
 constexpr uint32_t kTmemCols = 128;       // two 64-column accumulators
 constexpr int kPsStride = 65;             // staging row stride (floats): conflict-free rows and columns
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kThreadsModes = (kEpiWarps + 2) * 32;
 
 struct ModesTcArgs {
   int nb, nmodes, np, nf;
@@ -43,7 +48,7 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int kk) {
 }
 
 template <bool X3>
-__global__ void __launch_bounds__(192, 1) k_modes_tc(const __grid_constant__ CUtensorMap map_hi,
+__global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_constant__ CUtensorMap map_hi,
                                                     const __grid_constant__ CUtensorMap map_lo, ModesTcArgs a,
                                                     const float* __restrict__ bmat, const float* __restrict__ rsqrtW,
                                                     float2* __restrict__ phi, unsigned* __restrict__ gflags) {
@@ -73,13 +78,13 @@ __global__ void __launch_bounds__(192, 1) k_modes_tc(const __grid_constant__ CUt
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&hdr->accfull[i]), 1);
-      mbar_init(smem_u32(&hdr->accempty[i]), 128);
+      mbar_init(smem_u32(&hdr->accempty[i]), kEpiThreads);
     }
     mbar_init(smem_u32(&hdr->drain), 1);
     hdr->abort = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == kMmaWarp) {
     tmem_alloc(smem_u32(&hdr->tmem_base), kTmemCols);
     tmem_relinquish();
   }
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(192, 1) k_modes_tc(const __grid_constant__ CUt
   const uint32_t tmem = hdr->tmem_base;
   volatile int* abort_flag = &hdr->abort;
 
-  if (warp == 4 && lane == 0 && ntl > 0) {
+  if (warp == kTmaWarp && lane == 0 && ntl > 0) {
     // ---------------- TMA producer
     prefetch_tmap(&map_hi);
     if (X3) prefetch_tmap(&map_lo);
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(192, 1) k_modes_tc(const __grid_constant__ CUt
     }
     for (int i = max(0, issued - kStages); i < issued; ++i)
       mbar_wait(smem_u32(&hdr->full[i % kStages]), (i / kStages) & 1, abort_flag, gflags);
-  } else if (warp == 5 && lane == 0 && ntl > 0) {
+  } else if (warp == kMmaWarp && lane == 0 && ntl > 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(128, 64, 0, 1);
     const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
@@ -160,52 +165,51 @@ __global__ void __launch_bounds__(192, 1) k_modes_tc(const __grid_constant__ CUt
     }
     mma_commit(smem_u32(&hdr->drain));
     mbar_wait(smem_u32(&hdr->drain), 0, abort_flag, gflags);
-  } else if (warp < 4) {
+  } else if (warp < kEpiWarps) {
     // ---------------- epilogue
-    const int row = warp * 32 + lane;
+    const int row = (warp & 3) * 32 + lane;
+    const int half = warp >> 2;               // columns [32 half, 32 half + 32)
     const int nm = a.nmodes;
-    const int jpt = tid & 63, k0 = tid >> 6;
+    const int jpt = tid & 63, k0 = tid >> 6;  // output: point jpt, modes k0, k0 + 4, ...
     for (int i = 0; i < ntl; ++i) {
       const int acc = i & 1;
       // every epilogue thread takes the same stop/continue decision, so none
       // can be left behind in a named barrier
       mbar_wait(smem_u32(&hdr->accfull[acc]), (i >> 1) & 1, abort_flag, gflags);
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
       if (tid == 0) hdr->decision = *abort_flag;
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
       if (hdr->decision) break;
       tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)acc * 64u;
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + c0, v);
-        tmem_wait_ld();
+      const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)acc * 64u + 32u * half;
+      {
+        float v[32], w[32];
+        tmem_ld32x2(taddr, taddr, v, w);           // this warp's 32 columns, one wait
         if (row < 2 * nm) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) Ps[row * kPsStride + c0 + q] = v[q];
+          for (int q = 0; q < 32; ++q) Ps[row * kPsStride + 32 * half + q] = v[q];
         }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&hdr->accempty[acc]));
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
       const int64_t lm = (t0 + i) * 64 + jpt;
       if (lm < a.mcount) {
         const int64_t m = a.m0 + lm;
         const float rw = rsqrtW[m];
-        for (int k = k0; k < nm; k += 2) {
+        for (int k = k0; k < nm; k += kEpiThreads / 64) {
           float2 o;
           o.x = Ps[k * kPsStride + jpt] * rw;
           o.y = Ps[(nm + k) * kPsStride + jpt] * rw;
           phi[((int64_t)f * nm + k) * a.M + m] = o;
         }
       }
-      named_sync(1, 128);
+      named_sync(1, kEpiThreads);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
@@ -251,12 +255,12 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
   if (p.desc.precision == SPOD_PREC_BF16X3) {
     cudaError_t e = cudaFuncSetAttribute(k_modes_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_modes_tc<true><<<grid, 192, smem, s>>>(p.tmap_hi, p.tmap_lo, a, static_cast<const float*>(p.d_bmat),
+    k_modes_tc<true><<<grid, kThreadsModes, smem, s>>>(p.tmap_hi, p.tmap_lo, a, static_cast<const float*>(p.d_bmat),
                                              scale, static_cast<float2*>(d_Phi), p.d_flags);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_modes_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_modes_tc<false><<<grid, 192, smem, s>>>(p.tmap_hi, p.tmap_hi, a, static_cast<const float*>(p.d_bmat),
+    k_modes_tc<false><<<grid, kThreadsModes, smem, s>>>(p.tmap_hi, p.tmap_hi, a, static_cast<const float*>(p.d_bmat),
                                               scale, static_cast<float2*>(d_Phi), p.d_flags);
   }
   return cudaGetLastError();
