@@ -15,6 +15,8 @@
 //
 // Requires M * sizeof(element) to be a multiple of 16 bytes (TMA row stride);
 // other shapes use the per-block kernel of k_fft.cu.
+#include <type_traits>
+
 #include "fft_common.cuh"
 #include "tc_common.cuh"
 
@@ -30,6 +32,9 @@ constexpr int RTHREADS = 512;
 struct RingArgs {
   int64_t M, m0, mcount, chunk, mpad, ntiles;
   int nfft, step, nb, nf, boxr, ring;
+  int stg_off;                      // byte offset of the output staging (from the ring start)
+  int fbox, nfbox;                  // frequency rows per TMA store box, boxes per plane
+  int pst;                          // staging plane stride in elements (nfbox * fbox * 16, 128-byte padded)
   int subtract_mean;
   FftPlan fp;
 };
@@ -106,7 +111,9 @@ template <> struct Seq<512> { static __device__ __forceinline__ void run(float2*
 template <> struct Seq<720> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<720, 1, 8, 2, 3, 3, 5>(b, t); } };
 
 template <typename Tin, int OUTK, int NMAX, int FIXN>
-__global__ void __launch_bounds__(RTHREADS, (FIXN > 0 && FIXN <= 512) ? 2 : 1) k_fft_ring(const __grid_constant__ CUtensorMap xmap,
+__global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant__ CUtensorMap xmap,
+                                                          const __grid_constant__ CUtensorMap smap_hi,
+                                                          const __grid_constant__ CUtensorMap smap_lo,
                                                           const float* __restrict__ win,
                                                           const float2* __restrict__ tw_g,
                                                           const float* __restrict__ sqrtW,
@@ -122,6 +129,11 @@ __global__ void __launch_bounds__(RTHREADS, (FIXN > 0 && FIXN <= 512) ? 2 : 1) k
   float2* tw = buf + (size_t)a.nfft * RC;
   float* wsm = reinterpret_cast<float*>(tw + a.nfft);                   // c w_n
   float* swt = wsm + a.nfft;                                            // sqrt(W) of the tile
+  // output staging, two buffers: [plane][nf][RTP] (planes: re, im [, re lo, im lo])
+  constexpr int NPL = (OUTK == OUT_BF16X3) ? 4 : 2;
+  using Tout = typename std::conditional<OUTK == OUT_NATIVE, float, __nv_bfloat16>::type;
+  Tout* stg0 = reinterpret_cast<Tout*>(sm + 1024 + a.stg_off);
+  const int stg_elems = NPL * a.pst;
   const int N = a.nfft, S = a.step;
   const int tid = threadIdx.x;
   const uint32_t bar = smem_u32(&hdr->full);
@@ -160,6 +172,7 @@ __global__ void __launch_bounds__(RTHREADS, (FIXN > 0 && FIXN <= 512) ? 2 : 1) k
   const int j = tid % RC;            // copy phase: this thread's column (point pair)
   const int n0 = tid / RC;
   uint32_t phase = 0;
+  uint32_t blk = 0;                  // blocks transformed by this CTA (staging buffer parity)
   for (int64_t t = t_first; t < a.ntiles; t += t_step) {
     const int64_t lm0 = t * RTP;
     const int64_t gm0 = a.m0 + lm0;
@@ -218,47 +231,61 @@ __global__ void __launch_bounds__(RTHREADS, (FIXN > 0 && FIXN <= 512) ? 2 : 1) k
         }
       }
       const float2* src = buf;
-      // ---- separate the two real spectra of each column, fold sqrt(W), store pairs
-      const int64_t rs = a.chunk;
-      // this thread's items: pair pp, frequencies f0, f0 + RTHREADS/RC, ...
+      // ---- separate the two real spectra of each column, fold sqrt(W), stage the
+      // output planes [plane][f][16 points] in shared memory, store them by TMA
+      Tout* stg = stg0 + (size_t)(blk & 1) * stg_elems;
+      if (tid == 0) tma_store_wait_read<1>();      // the stores that last read this buffer are done
+      __syncthreads();
       const int pp = tid % RC;
       const int f0 = tid / RC;
       constexpr int FSTEP = RTHREADS / RC;
-      const int64_t fstride = (int64_t)FSTEP * 2 * a.nb * rs;
-      int64_t o_re = ((int64_t)f0 * 2 * a.nb + l) * rs + lm0 + 2 * pp;
-      const int64_t im_off = (int64_t)a.nb * rs;
       const float sa = swt[2 * pp], sb = swt[2 * pp + 1];
-      for (int f = f0; f < a.nf; f += FSTEP, o_re += fstride) {
+      for (int f = f0; f < a.nf; f += FSTEP) {
         const float2 zf = src[f * RC + pp];
         const float2 zc = src[((f == 0) ? 0 : N - f) * RC + pp];
         // even point: (Z[f] + conj Z[N-f]) / 2 ; odd point: (Z[f] - conj Z[N-f]) / (2i)
         const float ra = 0.5f * (zf.x + zc.x) * sa, ia = 0.5f * (zf.y - zc.y) * sa;
         const float rb = 0.5f * (zf.y + zc.y) * sb, ib = -0.5f * (zf.x - zc.x) * sb;
-        const int64_t o_im = o_re + im_off;
+        const int e = f * RTP + 2 * pp;
         if constexpr (OUTK == OUT_NATIVE) {
-          float* q = static_cast<float*>(qout);
-          *reinterpret_cast<float2*>(q + o_re) = make_float2(ra, rb);
-          *reinterpret_cast<float2*>(q + o_im) = make_float2(ia, ib);
+          *reinterpret_cast<float2*>(stg + e) = make_float2(ra, rb);
+          *reinterpret_cast<float2*>(stg + a.pst + e) = make_float2(ia, ib);
         } else {
-          __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
           const __nv_bfloat162 hr = __floats2bfloat162_rn(ra, rb);
           const __nv_bfloat162 hi = __floats2bfloat162_rn(ia, ib);
-          *reinterpret_cast<__nv_bfloat162*>(qh + o_re) = hr;
-          *reinterpret_cast<__nv_bfloat162*>(qh + o_im) = hi;
+          *reinterpret_cast<__nv_bfloat162*>(stg + e) = hr;
+          *reinterpret_cast<__nv_bfloat162*>(stg + a.pst + e) = hi;
           if constexpr (OUTK == OUT_BF16X3) {
-            __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qout_lo);
             const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi);
-            *reinterpret_cast<__nv_bfloat162*>(ql + o_re) = __floats2bfloat162_rn(ra - fr.x, rb - fr.y);
-            *reinterpret_cast<__nv_bfloat162*>(ql + o_im) = __floats2bfloat162_rn(ia - fi.x, ib - fi.y);
+            *reinterpret_cast<__nv_bfloat162*>(stg + 2 * a.pst + e) = __floats2bfloat162_rn(ra - fr.x, rb - fr.y);
+            *reinterpret_cast<__nv_bfloat162*>(stg + 3 * a.pst + e) = __floats2bfloat162_rn(ia - fi.x, ib - fi.y);
           }
         }
       }
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        // rows: re = l, im = nb + l of every frequency; boxes of fbox frequencies
+        // (the staged planes cover nfbox * fbox rows, so every box read stays inside them;
+        // frequencies past nf are clipped by the store)
+        const int x = (int)lm0;
+        for (int pl = 0; pl < NPL; ++pl) {
+          const CUtensorMap* mp = (pl < 2) ? &smap_hi : &smap_lo;
+          const int row = (pl & 1) ? a.nb + l : l;
+          for (int b = 0; b < a.nfbox; ++b)
+            tma_store_3d(mp, x, row, b * a.fbox, smem_u32(stg + (size_t)pl * a.pst + (size_t)b * a.fbox * RTP));
+        }
+        tma_store_commit();
+      }
+      ++blk;
       __syncthreads();
     }
     if (hdr->abort) break;
   }
-  // a request issued before an abort must land before the CTA exits
+  // a request issued before an abort must land before the CTA exits, and the
+  // output stores must have finished reading shared memory
   if (tid == 0 && hdr->abort) mbar_wait(bar, phase & 1, abort_flag, gflags);
+  if (tid == 0) tma_store_wait_all<0>();
 }
 
 template <typename Tin, int OUTK, int NMAX, int FIXN>
@@ -273,6 +300,10 @@ cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
   a.ring = p.nfft + p.step;
   a.subtract_mean = p.desc.subtract_mean;
   a.fp = p.fft;
+  a.stg_off = (int)fft_ring_stage_offset(p);
+  a.fbox = p.fst_fbox;
+  a.nfbox = (p.nf + p.fst_fbox - 1) / p.fst_fbox;
+  a.pst = (int)fft_ring_plane_elems(p);
   const size_t smem = fft_ring_smem_bytes(p);
   auto kern = k_fft_ring<Tin, OUTK, NMAX, FIXN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -281,7 +312,8 @@ cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RTHREADS, smem);
   per_sm = std::max(1, per_sm);
   const int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)(p.num_sms > 0 ? p.num_sms : 148) * per_sm);
-  kern<<<grid, RTHREADS, smem, s>>>(xmap, static_cast<const float*>(p.d_win), static_cast<const float2*>(p.d_tw),
+  kern<<<grid, RTHREADS, smem, s>>>(xmap, p.tmap_fst_hi, p.tmap_fst_lo, static_cast<const float*>(p.d_win),
+                                    static_cast<const float2*>(p.d_tw),
                                     static_cast<const float*>(p.d_sqrtW), p.d_mu, p.d_qhat, p.d_qlo, a, p.d_flags);
   return cudaGetLastError();
 }
@@ -312,17 +344,34 @@ cudaError_t launch_ring_in(const spod_plan_s& p, const CUtensorMap& xmap, int64_
 
 }  // namespace
 
-size_t fft_ring_smem_bytes(const spod_plan_s& p) {
+// Byte offset (from the ring start) of the output staging area, 128-byte aligned.
+size_t fft_ring_stage_offset(const spod_plan_s& p) {
   const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
-  return 1024 + 1024 + (size_t)(p.nfft + p.step) * RTP * el + sizeof(float2) * ((size_t)p.nfft * RC + p.nfft) +
-         sizeof(float) * (p.nfft + RTP);
+  const size_t pre = (size_t)(p.nfft + p.step) * RTP * el + sizeof(float2) * ((size_t)p.nfft * RC + p.nfft) +
+                     sizeof(float) * (p.nfft + RTP);
+  return (pre + 127) & ~size_t(127);
+}
+
+// Staging plane stride (elements): whole store boxes of fst_fbox frequency rows x 16
+// points, padded to 128 bytes.
+size_t fft_ring_plane_elems(const spod_plan_s& p) {
+  const size_t oel = p.tensor ? 2 : 4;
+  const size_t nbox = (p.nf + p.fst_fbox - 1) / p.fst_fbox;
+  const size_t bytes = nbox * p.fst_fbox * RTP * oel;
+  return ((bytes + 127) & ~size_t(127)) / oel;
+}
+
+size_t fft_ring_smem_bytes(const spod_plan_s& p) {
+  const size_t npl = p.desc.precision == SPOD_PREC_BF16X3 ? 4 : 2;
+  const size_t oel = p.tensor ? 2 : 4;
+  return 1024 + 1024 + fft_ring_stage_offset(p) + 2 * npl * fft_ring_plane_elems(p) * oel;
 }
 
 bool fft_ring_usable(const spod_plan_s& p, int smem_optin) {
   if (p.f64) return false;
   const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
   if ((p.M * (int64_t)el) % 16 != 0) return false;        // TMA row stride
-  if (p.ring_boxr <= 0 || p.nfft > 1024) return false;
+  if (p.ring_boxr <= 0 || p.nfft > 1024 || !p.fst_maps) return false;
   return fft_ring_smem_bytes(p) <= (size_t)smem_optin;
 }
 

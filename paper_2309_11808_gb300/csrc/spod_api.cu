@@ -154,6 +154,29 @@ spod_status run_fft_chunk(spod_plan_s* p, const void* d_X, const CUtensorMap* xm
   return SPOD_OK;
 }
 
+// TMA store maps for the FFT output planes: dims {chunk, 2 nb, nf}, box {16, 1, 256}.
+void make_fft_store_maps(spod_plan_s* p) {
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
+  if (!encode || p->f64) return;
+  const size_t el = p->tensor ? 2 : 4;
+  const CUtensorMapDataType dt = p->tensor ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t dims[3] = {(cuuint64_t)p->chunk_points, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)p->chunk_points * el, (cuuint64_t)(2 * p->nb) * p->chunk_points * el};
+  const int nbox = (p->nf + 255) / 256;
+  // <= 256 rows per box, a multiple of 4 so every box starts 128-byte aligned in shared memory
+  p->fst_fbox = ((p->nf + nbox - 1) / nbox + 3) / 4 * 4;
+  const cuuint32_t box[3] = {16, 1, (cuuint32_t)p->fst_fbox};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* bases[2] = {p->d_qhat, p->d_qlo ? p->d_qlo : p->d_qhat};
+  CUtensorMap* maps[2] = {&p->tmap_fst_hi, &p->tmap_fst_lo};
+  for (int i = 0; i < 2; ++i) {
+    CUresult r = encode(maps[i], dt, 3, bases[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;   // the ring FFT is then not used
+  }
+  p->fst_maps = true;
+}
+
 // TMA maps of the BF16 Qhat planes: dims {chunk points, 2 nb rows, nf}, box
 // {64 points, 2 nb rounded up to 16 rows, 1}; rows past 2 nb read as zeros.
 spod_status make_qhat_maps(spod_plan_s* p) {
@@ -288,7 +311,6 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
       if (g % dv == 0) { boxr = dv; break; }
     const size_t rowb = 16 * elem_bytes(d->in_dtype);
     p->ring_boxr = ((size_t)boxr * rowb) % 128 == 0 ? boxr : 0;
-    p->ring_ok = p->encode_fn && fft_ring_usable(*p, (int)prop.sharedMemPerBlockOptin);
   }
   if (fft_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
     return bail(SPOD_EUNSUPPORTED, "nfft too large for the shared-memory FFT");
@@ -374,6 +396,12 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_qhat = b + o_qhat;
   if (d->precision == SPOD_PREC_BF16X3)
     p->d_qlo = b + o_qhat + (size_t)p->nf * 2 * p->nb * 2 * (size_t)chunk;
+  make_fft_store_maps(p);
+  {
+    cudaDeviceProp prop2;
+    p->ring_ok = p->encode_fn && cudaGetDeviceProperties(&prop2, p->device) == cudaSuccess &&
+                 fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin);
+  }
   if (p->tensor) {
     if (spod_status st = make_qhat_maps(p)) {
       std::string msg = spod_last_error();

@@ -78,6 +78,10 @@ struct spod_plan_s {
   bool tensor = false;             // BF16 / BF16X3: Gram and modes on the tensor cores
   CUtensorMap tmap_hi;            // TMA maps of d_qhat / d_qlo: dims {chunk, 2nb, nf}, box {64, round16(2nb), 1}
   CUtensorMap tmap_lo;
+  CUtensorMap tmap_fst_hi;         // FFT output store maps: dims {chunk, 2nb, nf}, box {16, 1, 256}
+  CUtensorMap tmap_fst_lo;         //   (FP32 planes, or BF16 hi / lo)
+  bool fst_maps = false;
+  int fst_fbox = 0;                // frequency rows per FFT output store box
   double* d_gpart = nullptr;       // [gram_splits][nf][nb][nb][2] FP64 partial Grams
   double* d_gram = nullptr;        // [nf][nb][nb][2] reduced Gram (kappa applied)
   double* d_lam = nullptr;         // [nf][nb]
@@ -137,6 +141,8 @@ cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, 
 
 size_t fft_smem_bytes(const spod_plan_s& p);
 size_t fft_ring_smem_bytes(const spod_plan_s& p);
+size_t fft_ring_stage_offset(const spod_plan_s& p);
+size_t fft_ring_plane_elems(const spod_plan_s& p);
 bool fft_ring_usable(const spod_plan_s& p, int smem_optin);
 cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                                   cudaStream_t s);
