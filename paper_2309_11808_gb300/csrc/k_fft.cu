@@ -150,8 +150,10 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
       re *= sw;
       im *= sw;
     }
-    const int64_t o_re = ((int64_t)f * 2 * a.nb + l) * rs + lm;
-    const int64_t o_im = o_re + (int64_t)a.nb * rs;
+    // planar FP32/FP64 rows, or 64-point blocked BF16 rows (qhat_blocked_offset)
+    const int64_t o_re = (OUTK == OUT_NATIVE) ? ((int64_t)f * 2 * a.nb + l) * rs + lm
+                                              : qhat_blocked_offset(a.nf, a.nb, f, l, lm);
+    const int64_t o_im = o_re + (int64_t)a.nb * ((OUTK == OUT_NATIVE) ? rs : (int64_t)kQBlock);
     if constexpr (OUTK == OUT_NATIVE) {
       R* q = static_cast<R*>(qout);
       q[o_re] = re;

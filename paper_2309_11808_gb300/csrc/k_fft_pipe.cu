@@ -1,0 +1,413 @@
+// Persistent block DFT (Eqs. blocks, blocks-ft, blocks-k) for the nfft values
+// with a compiled radix sequence (256, 384, 512, 720).
+//
+// Two CTAs of 256 threads per SM walk tiles of 16 spatial points; each CTA
+// transforms the Welch blocks l = 0 .. nb-1 of its tile in order.  The tile's
+// time rows arrive by TMA into a ring of exactly nfft rows: block 0 loads
+// nfft rows, each later block only its step new rows, written over the rows
+// the previous block no longer needs, so every sample of X is read from HBM
+// once and the request for block l+1 is in flight while block l is
+// transformed.
+//
+// Per block the Stockham passes run out of place between two shared-memory
+// buffers, so a pass needs one barrier (after its stores) instead of two:
+//   pass 0   reads the ring directly and applies the mean (double-float pair)
+//            and the window c w_n while loading its butterfly inputs;
+//   pass i   buffer -> other buffer, twiddled radix-R butterflies;
+//   output   the two real spectra packed in each complex column are
+//            separated, sqrt(W) is folded in, and the planar rows
+//            Q[f][l][m] (re) and Q[f][nb+l][m] (im) are stored directly.
+// The buffer roles alternate between blocks when the pass count is odd, so
+// the next block's pass 0 never writes the buffer the output phase reads and
+// no barrier is needed between them.
+#include <type_traits>
+
+#include "fft_common.cuh"
+#include "tc_common.cuh"
+
+namespace spod {
+namespace {
+
+using namespace fft;
+
+constexpr int PTP = 16;               // points per tile
+constexpr int PC = PTP / 2;           // complex columns (point pairs)
+constexpr int PTHREADS = 256;
+constexpr int PBSTEP = PTHREADS / PC; // butterflies between a thread's consecutive ones
+
+struct PipeArgs {
+  int64_t m0, mcount, chunk, ntiles;
+  int step, nb, nf, boxr;
+  int subtract_mean;
+};
+
+struct PipeHdr {
+  uint64_t full;
+  int abort;
+};
+
+template <typename Tin> struct PairLoad;
+template <> struct PairLoad<float> {
+  static __device__ __forceinline__ float2 get(const float* p) { return *reinterpret_cast<const float2*>(p); }
+};
+template <> struct PairLoad<__nv_bfloat16> {
+  static __device__ __forceinline__ float2 get(const __nv_bfloat16* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
+};
+template <> struct PairLoad<double> {
+  static __device__ __forceinline__ float2 get(const double* p) {
+    const double2 d = *reinterpret_cast<const double2*>(p);
+    return make_float2((float)d.x, (float)d.y);
+  }
+};
+
+// Pass 0 (Ns = 1, no twiddles): butterfly inputs come from the ring rows of
+// the current block with the mean removed and the window applied.
+template <typename Tin, int N, int RAD>
+__device__ __forceinline__ void pass_first(const Tin* __restrict__ ring, int rb, float2* __restrict__ dst,
+                                           const float* __restrict__ wsm, float mhi0, float mlo0, float mhi1,
+                                           float mlo1) {
+  constexpr int nbut = N / RAD;
+  constexpr int MAXB = (nbut + PBSTEP - 1) / PBSTEP;
+  const int col = threadIdx.x % PC;
+  const int b0 = threadIdx.x / PC;
+  float2 v[MAXB][RAD];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = b0 + i * PBSTEP;
+    if (nbut % PBSTEP == 0 || b < nbut) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        const int n = b + r * nbut;
+        int slot = rb + n;
+        if (slot >= N) slot -= N;
+        const float2 x = PairLoad<Tin>::get(ring + slot * PTP + 2 * col);
+        const float wn = wsm[n];
+        v[i][r] = make_float2(((x.x - mhi0) - mlo0) * wn, ((x.y - mhi1) - mlo1) * wn);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = b0 + i * PBSTEP;
+    if (nbut % PBSTEP == 0 || b < nbut) {
+      dft_small<RAD, float2, float>(v[i]);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) dst[(b * RAD + r) * PC + col] = v[i][r];
+    }
+  }
+}
+
+// Out-of-place Stockham pass with compile-time radix and stride.
+template <int N, int RAD, int NS>
+__device__ __forceinline__ void pass_oop(const float2* __restrict__ src, float2* __restrict__ dst,
+                                         const float2* __restrict__ tw) {
+  constexpr int nbut = N / RAD;
+  constexpr int MAXB = (nbut + PBSTEP - 1) / PBSTEP;
+  constexpr int stw = N / (NS * RAD);
+  const int col = threadIdx.x % PC;
+  const int b0 = threadIdx.x / PC;
+  float2 v[MAXB][RAD];
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = b0 + i * PBSTEP;
+    if (nbut % PBSTEP == 0 || b < nbut) {
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) v[i][r] = src[(b + r * nbut) * PC + col];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MAXB; ++i) {
+    const int b = b0 + i * PBSTEP;
+    if (nbut % PBSTEP == 0 || b < nbut) {
+      const int k = b % NS, g = b / NS;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[i][r] = cmul(v[i][r], tw[r * k * stw]);
+      dft_small<RAD, float2, float>(v[i]);
+      const int base = g * NS * RAD + k;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) dst[(base + r * NS) * PC + col] = v[i][r];
+    }
+  }
+}
+
+// Passes 1 .. P-1, each followed by a barrier; returns the buffer holding
+// the spectrum.
+template <int N, int NS, int R0, int... RS>
+__device__ __forceinline__ const float2* run_rest(float2* src, float2* dst, const float2* tw) {
+  pass_oop<N, R0, NS>(src, dst, tw);
+  __syncthreads();
+  if constexpr (sizeof...(RS) > 0) {
+    return run_rest<N, NS * R0, RS...>(dst, src, tw);
+  } else {
+    return dst;
+  }
+}
+
+// Radix sequences (first radix, then the rest).
+template <int N> struct PSeq;
+template <> struct PSeq<256> {
+  static constexpr int R0 = 8, P = 3;
+  static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
+    return run_rest<256, 8, 8, 4>(a, b, t);
+  }
+};
+template <> struct PSeq<384> {
+  static constexpr int R0 = 8, P = 4;
+  static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
+    return run_rest<384, 8, 8, 2, 3>(a, b, t);
+  }
+};
+template <> struct PSeq<512> {
+  static constexpr int R0 = 8, P = 3;
+  static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
+    return run_rest<512, 8, 8, 8>(a, b, t);
+  }
+};
+template <> struct PSeq<720> {
+  static constexpr int R0 = 8, P = 5;
+  static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
+    return run_rest<720, 8, 2, 3, 3, 5>(a, b, t);
+  }
+};
+
+// Separate the two real spectra of each column (even point: (Z[f] + conj
+// Z[N-f]) / 2, odd point: (Z[f] - conj Z[N-f]) / 2i), fold sqrt(W) (sa, sb
+// carry the 1/2) and store rows re = l and im = nb + l of every frequency.
+template <int OUTK, int N>
+__device__ __forceinline__ void output_phase(const float2* __restrict__ src, const PipeArgs& a, int l,
+                                             int64_t lm0, float sa, float sb, void* __restrict__ qout,
+                                             void* __restrict__ qlo) {
+  const int col = threadIdx.x % PC;
+  const int f0 = threadIdx.x / PC;
+  // FP32 planes are planar [nf][2 nb][chunk]; BF16 planes are blocked by 64
+  // points, [chunk / 64][nf][2 nb][64] (see qhat_blocked_offset)
+  constexpr bool BLK = OUTK != OUT_NATIVE;
+  const int64_t rs = BLK ? (int64_t)kQBlock : a.chunk;           // row stride
+  const int64_t rowstride = (int64_t)2 * a.nb * rs;              // one frequency
+  const int64_t imoff = (int64_t)a.nb * rs;
+  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lm0 + 2 * col)
+                  : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lm0 + 2 * col;
+  for (int f = f0; f < a.nf; f += PBSTEP, o += PBSTEP * rowstride) {
+    const float2 zf = src[f * PC + col];
+    const float2 zc = src[((f == 0) ? 0 : N - f) * PC + col];
+    const float ra = (zf.x + zc.x) * sa, ia = (zf.y - zc.y) * sa;
+    const float rb = (zf.y + zc.y) * sb, ib = (zc.x - zf.x) * sb;
+    if constexpr (OUTK == OUT_NATIVE) {
+      float* q = static_cast<float*>(qout);
+      *reinterpret_cast<float2*>(q + o) = make_float2(ra, rb);
+      *reinterpret_cast<float2*>(q + o + imoff) = make_float2(ia, ib);
+    } else {
+      __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
+      const __nv_bfloat162 hr = __floats2bfloat162_rn(ra, rb);
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(ia, ib);
+      *reinterpret_cast<__nv_bfloat162*>(qh + o) = hr;
+      *reinterpret_cast<__nv_bfloat162*>(qh + o + imoff) = hi;
+      if constexpr (OUTK == OUT_BF16X3) {
+        __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qlo);
+        const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi);
+        *reinterpret_cast<__nv_bfloat162*>(ql + o) = __floats2bfloat162_rn(ra - fr.x, rb - fr.y);
+        *reinterpret_cast<__nv_bfloat162*>(ql + o + imoff) = __floats2bfloat162_rn(ia - fi.x, ib - fi.y);
+      }
+    }
+  }
+}
+
+// Shared-memory layout (bytes from the 1024-aligned base).
+template <typename Tin, int N>
+struct PipeLayout {
+  static constexpr size_t hdr = 0;
+  static constexpr size_t ring = 128;
+  static constexpr size_t buf0 = ring + (size_t)N * PTP * sizeof(Tin);
+  static constexpr size_t buf1 = buf0 + (size_t)N * PC * sizeof(float2);
+  static constexpr size_t tw = buf1 + (size_t)N * PC * sizeof(float2);
+  static constexpr size_t win = tw + (size_t)N * sizeof(float2);
+  static constexpr size_t end = win + (size_t)N * sizeof(float);
+  static constexpr size_t dyn = end + 1024;                    // alignment slack
+};
+
+// two CTAs per SM up to nfft = 512 (shared memory allows it); larger
+// transforms get the whole register file
+template <int N> constexpr int pipe_min_blocks() { return N <= 512 ? 2 : 1; }
+
+template <typename Tin, int OUTK, int N>
+__global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(const __grid_constant__ CUtensorMap xmap,
+                                                          const float* __restrict__ win,
+                                                          const float2* __restrict__ tw_g,
+                                                          const float* __restrict__ sqrtW,
+                                                          const double* __restrict__ mu, void* __restrict__ qout,
+                                                          void* __restrict__ qlo, PipeArgs a,
+                                                          unsigned* __restrict__ gflags) {
+  using namespace tc;
+  using L = PipeLayout<Tin, N>;
+  using S = PSeq<N>;
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  PipeHdr* hdr = reinterpret_cast<PipeHdr*>(sm + L::hdr);
+  Tin* ring = reinterpret_cast<Tin*>(sm + L::ring);
+  float2* buf0 = reinterpret_cast<float2*>(sm + L::buf0);
+  float2* buf1 = reinterpret_cast<float2*>(sm + L::buf1);
+  float2* tw = reinterpret_cast<float2*>(sm + L::tw);
+  float* wsm = reinterpret_cast<float*>(sm + L::win);
+  const int tid = threadIdx.x;
+  const uint32_t bar = smem_u32(&hdr->full);
+  volatile int* abort_flag = &hdr->abort;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    hdr->abort = 0;
+    fence_mbar_init();
+  }
+  for (int i = tid; i < N; i += PTHREADS) {
+    tw[i] = tw_g[i];
+    wsm[i] = win[i];
+  }
+  __syncthreads();
+
+  const int64_t t_first = blockIdx.x;
+  const int64_t t_step = gridDim.x;
+  if (t_first >= a.ntiles) return;
+  constexpr uint32_t row_bytes = PTP * sizeof(Tin);
+
+  // TMA boxes for time rows [r0, r0 + nrows) of tile t; row r lands in ring slot r mod N
+  auto issue = [&](int64_t t, int r0, int nrows) {
+    mbar_arrive_expect_tx(bar, (uint32_t)nrows * row_bytes);
+    const int x = (int)(a.m0 + t * PTP);
+    for (int r = r0; r < r0 + nrows; r += a.boxr) tma_load_2d(smem_u32(ring + (size_t)(r % N) * PTP), &xmap, x, r, bar);
+  };
+  if (tid == 0) {
+    prefetch_tmap(&xmap);
+    issue(t_first, 0, N);
+  }
+
+  const int col = tid % PC;
+  uint32_t phase = 0;
+  bool last_ok = true;               // thread 0: its last wait saw the copy land
+  int par = 0;                       // buffer roles of the current block
+  for (int64_t t = t_first; t < a.ntiles; t += t_step) {
+    const int64_t lm0 = t * PTP;
+    const int64_t gm0 = a.m0 + lm0;
+    float mhi0 = 0.f, mlo0 = 0.f, mhi1 = 0.f, mlo1 = 0.f, sa = 0.f, sb = 0.f;
+    {
+      const int64_t lm = lm0 + 2 * col;
+      if (lm < a.mcount) {
+        sa = 0.5f * sqrtW[gm0 + 2 * col];
+        if (a.subtract_mean) { const double d = mu[gm0 + 2 * col]; mhi0 = (float)d; mlo0 = (float)(d - (double)mhi0); }
+      }
+      if (lm + 1 < a.mcount) {
+        sb = 0.5f * sqrtW[gm0 + 2 * col + 1];
+        if (a.subtract_mean) {
+          const double d = mu[gm0 + 2 * col + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
+        }
+      }
+    }
+    int rb = 0;                      // ring slot of the block's first row
+    for (int l = 0; l < a.nb; ++l) {
+      last_ok = mbar_wait(bar, phase & 1, abort_flag, gflags);
+      ++phase;
+      float2* bA = par ? buf1 : buf0;
+      float2* bB = par ? buf0 : buf1;
+      pass_first<Tin, N, S::R0>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1);
+      __syncthreads();
+      if (hdr->abort) break;
+      // the ring rows of this block are consumed: request the next rows
+      if (tid == 0) {
+        if (l + 1 < a.nb) {
+          issue(t, l * a.step + N, a.step);
+        } else if (t + t_step < a.ntiles) {
+          issue(t + t_step, 0, N);
+        }
+      }
+      const float2* spec = S::rest(bA, bB, tw);
+      output_phase<OUTK, N>(spec, a, l, lm0, sa, sb, qout, qlo);
+      rb += a.step;
+      if (rb >= N) rb -= N;
+      par ^= (S::P & 1);
+    }
+    if (hdr->abort) break;
+  }
+  // a request issued before an abort must land before the CTA exits
+  if (tid == 0 && !last_ok) mbar_drain(bar, (phase - 1) & 1, gflags);
+}
+
+template <typename Tin, int OUTK, int N>
+cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                          cudaStream_t s) {
+  PipeArgs a;
+  a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
+  const int64_t mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
+  a.ntiles = mpad / PTP;
+  a.step = p.step; a.nb = p.nb; a.nf = p.nf;
+  a.boxr = p.ring_boxr;
+  a.subtract_mean = p.desc.subtract_mean;
+  const size_t smem = PipeLayout<Tin, N>::dyn;
+  auto kern = k_fft_pipe<Tin, OUTK, N>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PTHREADS, smem);
+  per_sm = std::max(1, per_sm);
+  const int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)(p.num_sms > 0 ? p.num_sms : 148) * per_sm);
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, PTHREADS, smem, s>>>(xmap, static_cast<const float*>(p.d_win), static_cast<const float2*>(p.d_tw),
+                                    static_cast<const float*>(p.d_sqrtW), p.d_mu, p.d_qhat, p.d_qlo, a, p.d_flags);
+  return cudaGetLastError();
+}
+
+template <typename Tin, int OUTK>
+cudaError_t launch_pipe_t(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                          cudaStream_t s) {
+  switch (p.nfft) {
+    case 256: return launch_pipe_n<Tin, OUTK, 256>(p, xmap, m0, mcount, s);
+    case 384: return launch_pipe_n<Tin, OUTK, 384>(p, xmap, m0, mcount, s);
+    case 512: return launch_pipe_n<Tin, OUTK, 512>(p, xmap, m0, mcount, s);
+    default: return launch_pipe_n<Tin, OUTK, 720>(p, xmap, m0, mcount, s);
+  }
+}
+
+template <typename Tin>
+cudaError_t launch_pipe_in(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                           cudaStream_t s) {
+  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_pipe_t<Tin, OUT_BF16X3>(p, xmap, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16) return launch_pipe_t<Tin, OUT_BF16>(p, xmap, m0, mcount, s);
+  return launch_pipe_t<Tin, OUT_NATIVE>(p, xmap, m0, mcount, s);
+}
+
+template <typename Tin>
+size_t pipe_smem_t(int nfft) {
+  switch (nfft) {
+    case 256: return PipeLayout<Tin, 256>::dyn;
+    case 384: return PipeLayout<Tin, 384>::dyn;
+    case 512: return PipeLayout<Tin, 512>::dyn;
+    case 720: return PipeLayout<Tin, 720>::dyn;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+// Dynamic shared memory of the pipelined kernel, 0 when nfft has no compiled sequence.
+size_t fft_pipe_smem_bytes(const spod_plan_s& p) {
+  if (p.desc.in_dtype == SPOD_F64) return pipe_smem_t<double>(p.nfft);
+  if (p.desc.in_dtype == SPOD_F32) return pipe_smem_t<float>(p.nfft);
+  return pipe_smem_t<__nv_bfloat16>(p.nfft);
+}
+
+bool fft_pipe_usable(const spod_plan_s& p, int smem_optin) {
+  if (p.f64 || p.ring_boxr <= 0) return false;
+  const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
+  if ((p.M * (int64_t)el) % 16 != 0) return false;          // TMA row stride
+  if (p.nfft % p.ring_boxr != 0 || p.step % p.ring_boxr != 0) return false;
+  const size_t smem = fft_pipe_smem_bytes(p);
+  return smem > 0 && smem <= (size_t)smem_optin;
+}
+
+cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                                  cudaStream_t s) {
+  if (p.desc.in_dtype == SPOD_F64) return launch_pipe_in<double>(p, xmap, m0, mcount, s);
+  if (p.desc.in_dtype == SPOD_F32) return launch_pipe_in<float>(p, xmap, m0, mcount, s);
+  return launch_pipe_in<__nv_bfloat16>(p, xmap, m0, mcount, s);
+}
+
+}  // namespace spod

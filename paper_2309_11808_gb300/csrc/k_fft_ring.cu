@@ -1,17 +1,18 @@
-// Persistent block DFT (Eqs. blocks, blocks-ft, blocks-k) with a TMA ring.
+// Persistent block DFT (Eqs. blocks, blocks-ft, blocks-k) with a TMA ring, for
+// nfft values without a compiled radix sequence (those use k_fft_pipe.cu).
 //
-// Persistent CTAs of 512 threads (two per SM for the compiled nfft values
-// 256/384/512/720, one otherwise) walk tiles of 16 spatial points; for each tile
-// it transforms the Welch blocks l = 0 .. nb-1 in order.  The tile's time rows
-// arrive by TMA into a ring of nfft + step rows: block 0 loads nfft rows, each
-// later block only its step new rows (the overlap is already resident), and
-// the next block's rows are requested while the current block is transformed,
-// so every sample of X is read from HBM once.  Per block: mean subtraction
-// (double-float pair), window c w_n, two real point series packed into one
-// complex sequence, an in-place shared-memory Stockham FFT (radix 8/4/2/3/5,
-// butterfly inputs held in registers across each pass), the two
-// real spectra separated, sqrt(W) folded in, and planar rows stored two points
-// per store (FP32, or BF16 hi [+ lo]).
+// Persistent CTAs of 512 threads walk tiles of 16 spatial points; for each tile
+// a CTA transforms the Welch blocks l = 0 .. nb-1 in order.  The tile's time
+// rows arrive by TMA into a ring of nfft + step rows: block 0 loads nfft rows,
+// each later block only its step new rows (the overlap is already resident),
+// and the next block's rows are requested while the current block is
+// transformed, so every sample of X is read from HBM once.  Per block: mean
+// subtraction (double-float pair), window c w_n, two real point series packed
+// into one complex sequence, an in-place shared-memory Stockham FFT following
+// the plan's runtime radix list (8/4/2/3/5), the two real spectra separated,
+// sqrt(W) folded in, and the output planes staged in shared memory and
+// written by TMA bulk tensor stores (planar FP32 rows, or the 64-point blocked
+// BF16 layout of the tensor-core path).
 //
 // Requires M * sizeof(element) to be a multiple of 16 bytes (TMA row stride);
 // other shapes use the per-block kernel of k_fft.cu.
@@ -90,27 +91,8 @@ struct MaxB {
   static constexpr int value = (NMAX * RC + RAD * RTHREADS - 1) / (RAD * RTHREADS);
 };
 
-__host__ __device__ constexpr int ilog2_or_neg(int v) {
-  int l = 0;
-  while ((1 << l) < v) ++l;
-  return (1 << l) == v ? l : -1;
-}
 
-// Compile-time radix sequence for a fixed nfft: strides and masks are constants.
-template <int N, int NS, int R0, int... RS>
-__device__ __forceinline__ void run_passes(float2* buf, const float2* tw) {
-  pass_inplace<R0, MaxB<N, R0>::value>(buf, tw, N, NS, ilog2_or_neg(NS));
-  if constexpr (sizeof...(RS) > 0) run_passes<N, NS * R0, RS...>(buf, tw);
-}
-
-// nfft values with a compiled pass sequence (0: runtime plan)
-template <int N> struct Seq;
-template <> struct Seq<256> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<256, 1, 8, 8, 4>(b, t); } };
-template <> struct Seq<384> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<384, 1, 8, 8, 2, 3>(b, t); } };
-template <> struct Seq<512> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<512, 1, 8, 8, 8>(b, t); } };
-template <> struct Seq<720> { static __device__ __forceinline__ void run(float2* b, const float2* t) { run_passes<720, 1, 8, 2, 3, 3, 5>(b, t); } };
-
-template <typename Tin, int OUTK, int NMAX, int FIXN>
+template <typename Tin, int OUTK, int NMAX>
 __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant__ CUtensorMap xmap,
                                                           const __grid_constant__ CUtensorMap smap_hi,
                                                           const __grid_constant__ CUtensorMap smap_lo,
@@ -172,6 +154,7 @@ __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant_
   const int j = tid % RC;            // copy phase: this thread's column (point pair)
   const int n0 = tid / RC;
   uint32_t phase = 0;
+  bool last_ok = true;               // thread 0: its last wait saw the copy land
   uint32_t blk = 0;                  // blocks transformed by this CTA (staging buffer parity)
   for (int64_t t = t_first; t < a.ntiles; t += t_step) {
     const int64_t lm0 = t * RTP;
@@ -187,7 +170,7 @@ __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant_
       if (tid < RTP) swt[tid] = (lm0 + tid < a.mcount) ? sqrtW[gm0 + tid] : 0.f;
     }
     for (int l = 0; l < a.nb; ++l) {
-      mbar_wait(bar, phase & 1, abort_flag, gflags);
+      last_ok = mbar_wait(bar, phase & 1, abort_flag, gflags);
       ++phase;
       __syncthreads();
       if (hdr->abort) break;
@@ -213,9 +196,7 @@ __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant_
         }
       }
       // ---- FFT (in place)
-      if constexpr (FIXN > 0) {
-        Seq<FIXN>::run(buf, tw);
-      } else {
+      {
         int Ns = 1, log2Ns = 0;
         for (int ps = 0; ps < a.fp.npass; ++ps) {
           const int rad = a.fp.radix[ps];
@@ -268,12 +249,17 @@ __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant_
         // rows: re = l, im = nb + l of every frequency; boxes of fbox frequencies
         // (the staged planes cover nfbox * fbox rows, so every box read stays inside them;
         // frequencies past nf are clipped by the store)
-        const int x = (int)lm0;
         for (int pl = 0; pl < NPL; ++pl) {
           const CUtensorMap* mp = (pl < 2) ? &smap_hi : &smap_lo;
           const int row = (pl & 1) ? a.nb + l : l;
-          for (int b = 0; b < a.nfbox; ++b)
-            tma_store_3d(mp, x, row, b * a.fbox, smem_u32(stg + (size_t)pl * a.pst + (size_t)b * a.fbox * RTP));
+          for (int b = 0; b < a.nfbox; ++b) {
+            const uint32_t src = smem_u32(stg + (size_t)pl * a.pst + (size_t)b * a.fbox * RTP);
+            if constexpr (OUTK == OUT_NATIVE) {
+              tma_store_3d(mp, (int)lm0, row, b * a.fbox, src);
+            } else {   // blocked BF16 layout: point within the 64-point block, block index last
+              tma_store_4d(mp, (int)(lm0 % kQBlock), row, b * a.fbox, (int)(lm0 / kQBlock), src);
+            }
+          }
         }
         tma_store_commit();
       }
@@ -284,11 +270,11 @@ __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant_
   }
   // a request issued before an abort must land before the CTA exits, and the
   // output stores must have finished reading shared memory
-  if (tid == 0 && hdr->abort) mbar_wait(bar, phase & 1, abort_flag, gflags);
+  if (tid == 0 && !last_ok) mbar_drain(bar, (phase - 1) & 1, gflags);
   if (tid == 0) tma_store_wait_all<0>();
 }
 
-template <typename Tin, int OUTK, int NMAX, int FIXN>
+template <typename Tin, int OUTK, int NMAX>
 cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
   RingArgs a;
@@ -305,7 +291,7 @@ cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
   a.nfbox = (p.nf + p.fst_fbox - 1) / p.fst_fbox;
   a.pst = (int)fft_ring_plane_elems(p);
   const size_t smem = fft_ring_smem_bytes(p);
-  auto kern = k_fft_ring<Tin, OUTK, NMAX, FIXN>;
+  auto kern = k_fft_ring<Tin, OUTK, NMAX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
@@ -321,17 +307,8 @@ cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
 template <typename Tin, int OUTK>
 cudaError_t launch_ring_t(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
-  if constexpr (sizeof(Tin) != 8) {
-    switch (p.nfft) {
-      case 256: return launch_ring_n<Tin, OUTK, 256, 256>(p, xmap, m0, mcount, s);
-      case 384: return launch_ring_n<Tin, OUTK, 384, 384>(p, xmap, m0, mcount, s);
-      case 512: return launch_ring_n<Tin, OUTK, 512, 512>(p, xmap, m0, mcount, s);
-      case 720: return launch_ring_n<Tin, OUTK, 720, 720>(p, xmap, m0, mcount, s);
-      default: break;
-    }
-  }
-  if (p.nfft <= 512) return launch_ring_n<Tin, OUTK, 512, 0>(p, xmap, m0, mcount, s);
-  return launch_ring_n<Tin, OUTK, 1024, 0>(p, xmap, m0, mcount, s);
+  if (p.nfft <= 512) return launch_ring_n<Tin, OUTK, 512>(p, xmap, m0, mcount, s);
+  return launch_ring_n<Tin, OUTK, 1024>(p, xmap, m0, mcount, s);
 }
 
 template <typename Tin>

@@ -131,14 +131,14 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
       if (u >= 1 && !mbar_wait(smem_u32(&hdr->empty[s]), (u - 1) & 1, abort_flag, gflags)) break;
       const uint32_t fb = smem_u32(&hdr->full[s]);
       mbar_arrive_expect_tx(fb, bytes);
-      const int x = (int)((kb0 + kb) * 64);
-      tma_load_3d(smem_u32(stages + (s * NOPS) * kTileBytes), &map_hi, x, 0, f, fb);
-      if (X3) tma_load_3d(smem_u32(stages + (s * NOPS + 1) * kTileBytes), &map_lo, x, 0, f, fb);
+      const int kblk = (int)(kb0 + kb);        // 64-point block of the blocked Qhat layout
+      tma_load_4d(smem_u32(stages + (s * NOPS) * kTileBytes), &map_hi, 0, 0, f, kblk, fb);
+      if (X3) tma_load_4d(smem_u32(stages + (s * NOPS + 1) * kTileBytes), &map_lo, 0, 0, f, kblk, fb);
       issued = kb + 1;
     }
     // copies still in flight must land before the CTA can exit
     for (int kb = max(0, issued - kStages); kb < issued; ++kb)
-      mbar_wait(smem_u32(&hdr->full[kb % kStages]), (kb / kStages) & 1, abort_flag, gflags);
+      mbar_drain(smem_u32(&hdr->full[kb % kStages]), (kb / kStages) & 1, gflags);
   } else if (warp == kMmaWarp && lane == 0 && nkbl > 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(128, a.np, 0, 0);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
       if ((kb % FB) == FB - 1 || kb == nkbl - 1) mma_commit(smem_u32(&hdr->accfull[acc]));
     }
     mma_commit(smem_u32(&hdr->drain));
-    mbar_wait(smem_u32(&hdr->drain), 0, abort_flag, gflags);
+    mbar_drain(smem_u32(&hdr->drain), 0, gflags);
   } else if (warp < kEpiWarps) {
     // ---------------- epilogue: TMEM -> FP32 staging -> compensated FP32 sums
     float sr[kMaxPerThread], cr[kMaxPerThread], si[kMaxPerThread], ci[kMaxPerThread];

@@ -127,13 +127,14 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
       if (u >= 1 && !mbar_wait(smem_u32(&hdr->empty[s]), (u - 1) & 1, abort_flag, gflags)) break;
       const uint32_t fb = smem_u32(&hdr->full[s]);
       mbar_arrive_expect_tx(fb, bytes);
-      const int x = (int)((t0 + i) * 64);
-      tma_load_3d(smem_u32(stages + (s * NOPS) * tile_bytes), &map_hi, x, 0, f, fb);
-      if (X3) tma_load_3d(smem_u32(stages + (s * NOPS + 1) * tile_bytes), &map_lo, x, 0, f, fb);
+      const int kblk = (int)(t0 + i);          // 64-point block of the blocked Qhat layout
+      tma_load_4d(smem_u32(stages + (s * NOPS) * tile_bytes), &map_hi, 0, 0, f, kblk, fb);
+      if (X3) tma_load_4d(smem_u32(stages + (s * NOPS + 1) * tile_bytes), &map_lo, 0, 0, f, kblk, fb);
       issued = i + 1;
     }
+    // copies still in flight must land before the CTA can exit
     for (int i = max(0, issued - kStages); i < issued; ++i)
-      mbar_wait(smem_u32(&hdr->full[i % kStages]), (i / kStages) & 1, abort_flag, gflags);
+      mbar_drain(smem_u32(&hdr->full[i % kStages]), (i / kStages) & 1, gflags);
   } else if (warp == kMmaWarp && lane == 0 && ntl > 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(128, 64, 0, 1);
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
       mma_commit(smem_u32(&hdr->accfull[acc]));
     }
     mma_commit(smem_u32(&hdr->drain));
-    mbar_wait(smem_u32(&hdr->drain), 0, abort_flag, gflags);
+    mbar_drain(smem_u32(&hdr->drain), 0, gflags);
   } else if (warp < kEpiWarps) {
     // ---------------- epilogue
     const int row = (warp & 3) * 32 + lane;

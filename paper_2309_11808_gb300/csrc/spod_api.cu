@@ -149,47 +149,64 @@ spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) 
 // FFT of one spatial chunk: the TMA-ring kernel when the shape allows it.
 spod_status run_fft_chunk(spod_plan_s* p, const void* d_X, const CUtensorMap* xmap, int64_t m0, int64_t mc,
                           cudaStream_t s) {
-  cudaError_t e = xmap ? launch_fft_ring_chunk(*p, *xmap, m0, mc, s) : launch_fft_chunk(*p, d_X, m0, mc, s);
+  cudaError_t e = !xmap        ? launch_fft_chunk(*p, d_X, m0, mc, s)
+                  : p->pipe_ok ? launch_fft_pipe_chunk(*p, *xmap, m0, mc, s)
+                               : launch_fft_ring_chunk(*p, *xmap, m0, mc, s);
   if (e != cudaSuccess) return cuda_fail(e, "fft kernel");
   return SPOD_OK;
 }
 
-// TMA store maps for the FFT output planes: dims {chunk, 2 nb, nf}, box {16, 1, 256}.
+// TMA store maps for the FFT output planes: boxes of 16 points x 1 row x fst_fbox frequencies.
 void make_fft_store_maps(spod_plan_s* p) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
   if (!encode || p->f64) return;
   const size_t el = p->tensor ? 2 : 4;
   const CUtensorMapDataType dt = p->tensor ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const cuuint64_t dims[3] = {(cuuint64_t)p->chunk_points, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf};
-  const cuuint64_t strides[2] = {(cuuint64_t)p->chunk_points * el, (cuuint64_t)(2 * p->nb) * p->chunk_points * el};
   const int nbox = (p->nf + 255) / 256;
   // <= 256 rows per box, a multiple of 4 so every box starts 128-byte aligned in shared memory
   p->fst_fbox = ((p->nf + nbox - 1) / nbox + 3) / 4 * 4;
-  const cuuint32_t box[3] = {16, 1, (cuuint32_t)p->fst_fbox};
-  const cuuint32_t estr[3] = {1, 1, 1};
+  // FP32: planar {chunk, 2 nb, nf}; BF16: blocked {64, 2 nb, nf, chunk / 64} (qhat_blocked_offset)
+  const int rank = p->tensor ? 4 : 3;
+  cuuint64_t dims[4], strides[3];
+  if (p->tensor) {
+    dims[0] = kQBlock; dims[1] = 2 * p->nb; dims[2] = p->nf; dims[3] = p->chunk_points / kQBlock;
+    strides[0] = (cuuint64_t)kQBlock * el;
+    strides[1] = strides[0] * 2 * p->nb;
+    strides[2] = strides[1] * p->nf;
+  } else {
+    dims[0] = p->chunk_points; dims[1] = 2 * p->nb; dims[2] = p->nf;
+    strides[0] = (cuuint64_t)p->chunk_points * el;
+    strides[1] = strides[0] * 2 * p->nb;
+  }
+  const cuuint32_t box[4] = {16, 1, (cuuint32_t)p->fst_fbox, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
   void* bases[2] = {p->d_qhat, p->d_qlo ? p->d_qlo : p->d_qhat};
   CUtensorMap* maps[2] = {&p->tmap_fst_hi, &p->tmap_fst_lo};
   for (int i = 0; i < 2; ++i) {
-    CUresult r = encode(maps[i], dt, 3, bases[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult r = encode(maps[i], dt, rank, bases[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return;   // the ring FFT is then not used
   }
   p->fst_maps = true;
 }
 
-// TMA maps of the BF16 Qhat planes: dims {chunk points, 2 nb rows, nf}, box
-// {64 points, 2 nb rounded up to 16 rows, 1}; rows past 2 nb read as zeros.
+// TMA maps of the BF16 Qhat planes: dims {64 points, 2 nb rows, nf, chunk / 64},
+// box {64 points, 2 nb rounded up to 16 rows, 1, 1}; 128-byte swizzle.
 spod_status make_qhat_maps(spod_plan_s* p) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
   if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
-  const cuuint64_t dims[3] = {(cuuint64_t)p->chunk_points, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf};
-  const cuuint64_t strides[2] = {(cuuint64_t)p->chunk_points * 2, (cuuint64_t)(2 * p->nb) * p->chunk_points * 2};
-  const cuuint32_t box[3] = {64, (cuuint32_t)((2 * p->nb + 15) / 16 * 16), 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
+  // blocked layout [chunk / 64][nf][2 nb][64] (qhat_blocked_offset): one box =
+  // one frequency's rows over one 64-point K step; rows past 2 nb read as zero
+  const cuuint64_t dims[4] = {(cuuint64_t)kQBlock, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf,
+                              (cuuint64_t)(p->chunk_points / kQBlock)};
+  const cuuint64_t row = (cuuint64_t)kQBlock * 2;
+  const cuuint64_t strides[3] = {row, row * 2 * p->nb, row * 2 * p->nb * p->nf};
+  const cuuint32_t box[4] = {(cuuint32_t)kQBlock, (cuuint32_t)((2 * p->nb + 15) / 16 * 16), 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
   void* bases[2] = {p->d_qhat, p->d_qlo ? p->d_qlo : p->d_qhat};
   CUtensorMap* maps[2] = {&p->tmap_hi, &p->tmap_lo};
   for (int i = 0; i < 2; ++i) {
-    CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, bases[i], dims, strides, box, estr,
+    CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, bases[i], dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -399,8 +416,9 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   make_fft_store_maps(p);
   {
     cudaDeviceProp prop2;
-    p->ring_ok = p->encode_fn && cudaGetDeviceProperties(&prop2, p->device) == cudaSuccess &&
-                 fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin);
+    const bool q = p->encode_fn && cudaGetDeviceProperties(&prop2, p->device) == cudaSuccess;
+    p->pipe_ok = q && fft_pipe_usable(*p, (int)prop2.sharedMemPerBlockOptin);
+    p->ring_ok = p->pipe_ok || (q && fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin));
   }
   if (p->tensor) {
     if (spod_status st = make_qhat_maps(p)) {

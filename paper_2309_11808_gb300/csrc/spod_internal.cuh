@@ -24,6 +24,18 @@ constexpr int kMaxRadixPasses = 32;
 constexpr int kMaxNb = 1024;           // largest supported block count
 constexpr int kEigSmemMaxNb = 48;      // eigen-solver keeps A and V in shared memory up to here
 
+// Qhat layout of one spatial chunk.  FP32/FP64 planes are planar, element
+// (f, row, m) at (f * 2 nb + row) * chunk + m.  The BF16 planes of the
+// tensor-core path are blocked by kQBlock points, [chunk / kQBlock][nf][2 nb]
+// [kQBlock]: the rows that one spatial tile contributes to every frequency lie
+// within a few MB (a handful of pages, whatever the chunk size), and the
+// K step of one frequency is a single contiguous 2 nb x 128-byte box for the
+// tensor-core kernels.  Rows are re = l, im = nb + l for Welch block l.
+constexpr int kQBlock = 64;
+__host__ __device__ inline int64_t qhat_blocked_offset(int nf, int nb, int f, int row, int64_t m) {
+  return (((m / kQBlock) * nf + f) * 2 * nb + row) * kQBlock + (m % kQBlock);
+}
+
 struct FftPlan {
   int n = 0;
   int npass = 0;
@@ -60,7 +72,8 @@ struct spod_plan_s {
   int gram_flush = 4;         // tensor-core Gram: blocks per FP32 accumulation group
   int modes_ctas = 0;         // tensor-core modes: CTAs per frequency (0 = automatic)
   int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
-  bool ring_ok = false;
+  bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
+  bool pipe_ok = false;       // the pipelined kernel (compiled nfft) is used
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   int num_sms = 0;
 
@@ -144,6 +157,10 @@ size_t fft_ring_smem_bytes(const spod_plan_s& p);
 size_t fft_ring_stage_offset(const spod_plan_s& p);
 size_t fft_ring_plane_elems(const spod_plan_s& p);
 bool fft_ring_usable(const spod_plan_s& p, int smem_optin);
+size_t fft_pipe_smem_bytes(const spod_plan_s& p);
+bool fft_pipe_usable(const spod_plan_s& p, int smem_optin);
+cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+                                  cudaStream_t s);
 cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                                   cudaStream_t s);
 size_t eig_smem_bytes(int nb);
