@@ -6,8 +6,12 @@ X = 512 x 256 grid x 3 variables, nt = 10 000 FP32 snapshots (15.7 GB),
 nfft = 512, 50 % overlap (nb = 38), Hamming window, weights ~ r.
 Metric: snapshot-GB/s = nt * M * sizeof(element) / (time per step).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32]
-                    [--impl native|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3]
+                    [--impl native|reference] [--no-compare] [--no-e2e] [--no-cpu]
+
+The default precision is bf16x3 (BF16 tensor-core Gram and modes with split
+products); the same input is then also run through the plain FP32 GPU form
+and reported under "vs_fp32".
 
 N > 1 (torchrun): every rank runs its own full replica of the workload (no
 collective on the data path); value = units of all ranks / max-over-ranks time.
@@ -38,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a reduced grid for quick checks (not a bench value)")
@@ -144,7 +149,7 @@ def main():
         return reference_leg(args, world, rank)
 
     import __graft_entry__ as g
-    from paper_2309_11808_gb300 import SPOD, _lib
+    from paper_2309_11808_gb300 import _lib
     from workloads import jet_like
 
     g.build()
@@ -154,80 +159,62 @@ def main():
     wl = jet_like(nx=nx, nr=nr, nvars=NVARS, nt=NT, nfft=NFFT, seed=rank, dtype=torch.float32, device=dev)
     X = wl.X
     M = X.shape[1]
-    sp = SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=torch.float32, precision=args.precision,
-              weights=wl.W)
-    nb, nf = sp.nb, sp.nf
-    nmodes = nb
-    cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
-    Phi = torch.empty((nf, nmodes, M), dtype=cdt, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step():
-        _lib.spod_fit(sp.handle, X, stream)
-        _lib.spod_modes(sp.handle, X, nmodes, Phi, stream)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    _lib.spod_profile_read(sp.handle)          # discard warm-up
-    _lib.spod_profile_enable(sp.handle, True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    phase_ms, phase_launch = _lib.spod_profile_read(sp.handle)
-    _lib.spod_profile_enable(sp.handle, False)
-    _lib.spod_sync(sp.handle, stream)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
     elem = 4
     bytes_step = NT * M * elem
+
+    r = timed_run(args.precision, wl, args.steps, max(3, args.warmup), world, dev, clocks=True)
+    sp, nb, nf, nmodes = r["sp"], r["nb"], r["nf"], r["nmodes"]
+    ms_step, phase_ms, phase_launch, clk = r["ms_step"], r["phase_ms"], r["phase_launch"], r["clocks"]
     value = world * bytes_step / (ms_step * 1e-3) / 1e9
 
-    # ---- roofline of the dominant kernel (phase with the largest time)
+    # ---- roofline: every phase's kernel, the dominant one (largest time) on top
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peaks = json.load(fh)
     except OSError:
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12       # TFLOP/s: SMs x FP32 lanes x FMA x max clock
-    dom = max(phase_ms, key=phase_ms.get)
-    per_launch_ms = phase_ms[dom] / max(1, phase_launch[dom] if dom != "modes" else phase_launch[dom] // 2)
-    roof = roofline(dom, per_launch_ms, M, nb, nf, nmodes, hbm_peak, fp32_peak, args.precision)
+    # one step launches each phase's kernels once (modes: the small coefficient
+    # kernel + the mode GEMM), so the per-step phase time is the launch time
+    per_phase = {k: kernel_roofline(k, phase_ms[k] / args.steps, M, nb, nf, nmodes, peaks, args.precision)
+                 for k in phase_ms if phase_launch.get(k, 0) > 0}
+    dom = max(per_phase, key=lambda k: phase_ms[k])
+    roof = per_phase[dom]
+    step_roof = step_roofline(ms_step, M, nb, nf, nmodes, peaks, args.precision)
 
     line = {"metric": "SPOD snapshot-GB/s (FFT+CSD+eig+modes)", "value": round(value, 3), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+            "vs_baseline": None, "dtype": DTYPE_NAME[args.precision],
             "data": "synthetic (seeded jet-shaped wave packets + AR(1) red noise)",
             "config": workload_config(args, nb, nf, nmodes), "roofline": roof,
+            "step_roofline": step_roof,
             "phases_ms_per_step": {k: round(v / args.steps, 4) for k, v in phase_ms.items()},
+            "phase_rooflines": per_phase,
             "gpu_launches": int(sum(phase_launch.values())), "clocks": clk,
             "snapshots_per_s": round(world * NT / (ms_step * 1e-3), 1)}
 
+    # ---- the plain FP32 GPU form on the same input (the comparison the metric names)
+    if args.precision != "fp32" and not args.no_compare:
+        sp.close()
+        rf = timed_run("fp32", wl, max(2, args.steps // 2), 3, world, dev, clocks=False)
+        rf["sp"].close()
+        sp = None
+        fv = world * bytes_step / (rf["ms_step"] * 1e-3) / 1e9
+        line["vs_fp32"] = {"fp32_value": round(fv, 3), "fp32_ms_per_step": round(rf["ms_step"], 4),
+                           "fp32_snapshots_per_s": round(world * NT / (rf["ms_step"] * 1e-3), 1),
+                           "speedup": round(value / fv, 3), "fp32_steps": max(2, args.steps // 2),
+                           "fp32_phases_ms_per_step": {k: round(v / max(2, args.steps // 2), 4)
+                                                       for k, v in rf["phase_ms"].items()}}
+
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e and rank == 0 and not args.small:
+        if sp is None:
+            sp = make_plan(args.precision, wl)
         line["e2e"] = e2e_leg(sp, X, nmodes, args, world)
     # ---- CPU oracle on a bounded sample
     if not args.no_cpu and rank == 0 and world == 1:
-        P = 1024
+        P = 4096
         cols, idx = sample_columns(X, P)
         secs = oracle_sample(cols, wl.W.numpy()[idx], nmodes)
         line["cpu_baseline"] = {"value": round(NT * cols.shape[1] * elem / secs / 1e9, 5), "unit": "GB/s",
@@ -237,36 +224,161 @@ def main():
                                 "seconds": round(secs, 2)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sp.close()
+    if sp is not None:
+        sp.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def roofline(dom, per_launch_ms, M, nb, nf, nmodes, hbm_peak, fp32_peak, precision):
-    """Algorithmic bytes / flops of one launch of the dominant phase's kernel."""
-    R = 8 if precision == "fp64" else 4
+DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "bf16x3": "bf16x3"}
+FP32_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+
+
+def make_plan(precision, wl):
+    import torch
+    from paper_2309_11808_gb300 import SPOD
+    return SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=torch.float32, precision=precision, weights=wl.W)
+
+
+def timed_run(precision, wl, steps, warmup, world, dev, clocks):
+    """W untimed steps, then K steps between CUDA events on the launching stream."""
+    import torch
+    import torch.distributed as dist
+    from paper_2309_11808_gb300 import _lib
+    X = wl.X
+    sp = make_plan(precision, wl)
+    nb, nf = sp.nb, sp.nf
+    nmodes = nb
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
+    Phi = torch.empty((nf, nmodes, X.shape[1]), dtype=cdt, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        _lib.spod_fit(sp.handle, X, stream)
+        _lib.spod_modes(sp.handle, X, nmodes, Phi, stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    _lib.spod_profile_read(sp.handle)          # discard warm-up
+    _lib.spod_profile_enable(sp.handle, True)
+    sampler = ClockSampler(dev.index or 0) if clocks else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = sampler.stop() if sampler else None
+    ms_total = e0.elapsed_time(e1)
+    phase_ms, phase_launch = _lib.spod_profile_read(sp.handle)
+    _lib.spod_profile_enable(sp.handle, False)
+    _lib.spod_sync(sp.handle, stream)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    del Phi
+    return {"sp": sp, "nb": nb, "nf": nf, "nmodes": nmodes, "ms_step": ms_total / steps, "phase_ms": phase_ms,
+            "phase_launch": phase_launch, "clocks": clk}
+
+
+# Kernel of each phase and precision (the phase timer brackets exactly these launches).
+KERNELS = {
+    "mean": "k_mean_partial + k_mean_finish",
+    "fft": "k_fft_pipe",
+    "gram": {"fp32": "k_gram_simt", "fp64": "k_gram_simt", "bf16": "k_gram_tc", "bf16x3": "k_gram_tc"},
+    "reduce": "k_gram_reduce",
+    "eig": "k_eig_tridiag",
+    "modes": {"fp32": "k_mode_coeffs + k_modes_simt", "fp64": "k_mode_coeffs + k_modes_simt",
+              "bf16": "k_mode_coeffs + k_modes_tc", "bf16x3": "k_mode_coeffs + k_modes_tc"},
+}
+
+
+def qhat_bytes_per_point(nb, nf, precision):
+    """Bytes of Qhat per spatial point: nf x 2 nb real entries."""
+    per = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4}[precision]
+    return nf * 2 * nb * per
+
+
+def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
+    """Roofline of one launch of a phase's kernel.
+
+    Bytes are the compulsory traffic of the kernel in this pipeline: the FFT
+    reads X once and writes Qhat; the Gram reads Qhat; the modes read Qhat
+    and write Phi (complex64 / complex128).  The eigensolver is reported
+    against the FP64 rate it is limited by (no HBM traffic to speak of)."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
     t = per_launch_ms * 1e-3
-    if dom == "gram":
-        flops = 4.0 * nf * nb * (nb + 1) * M            # Hermitian half of Q^H Q (complex MACs x 8 / 2)
-        ach = flops / t / 1e12
-        return {"bound": "alu", "kernel": "k_gram_simt", "achieved": round(ach, 3), "peak": round(fp32_peak, 1),
-                "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    if dom == "modes":
-        flops = 8.0 * nf * nb * nmodes * M
-        ach = flops / t / 1e12
-        return {"bound": "alu", "kernel": "k_modes_simt", "achieved": round(ach, 3), "peak": round(fp32_peak, 1),
-                "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    if dom == "fft":
-        byts = NT * M * 4 + nf * 2 * nb * M * R          # X read once + Qhat written
-    elif dom == "mean":
-        byts = NT * M * 4
+    kern = KERNELS.get(phase, phase)
+    if isinstance(kern, dict):
+        kern = kern[precision]
+    s = 8 if precision == "fp64" else 4
+    q = qhat_bytes_per_point(nb, nf, precision) * M
+    phi = nf * nmodes * M * (16 if precision == "fp64" else 8)
+    if phase == "mean":
+        byts = NT * M * s
+    elif phase == "fft":
+        byts = NT * M * 4 + q
+    elif phase == "gram":
+        if precision in ("fp32", "fp64"):
+            flops = 4.0 * nf * nb * (nb + 1) * M            # Hermitian half of Q^H W Q, 8 flops per complex MAC
+            ach = flops / t / 1e12
+            return {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(FP32_PEAK, 1),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "ms": round(per_launch_ms, 4)}
+        byts = q
+    elif phase == "modes":
+        if precision in ("fp32", "fp64"):
+            flops = 8.0 * nf * nb * nmodes * M
+            ach = flops / t / 1e12
+            return {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(FP32_PEAK, 1),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "ms": round(per_launch_ms, 4)}
+        byts = q + phi
     else:
         byts = nf * nb * nb * 16
     ach = byts / t / 1e9
-    return {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)"}
+    return {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get((kern, precision)), "peak_source": src + " (burst)",
+            "bytes_per_launch": int(byts), "ms": round(per_launch_ms, 4)}
+
+
+# DRAM bytes (read + write) per launch from an ncu capture, scaled to the full
+# workload; None until captured for the current kernel version.
+TRAFFIC = {}
+
+
+def step_roofline(ms_step, M, nb, nf, nmodes, peaks, precision):
+    """Whole-step roofline of the method: t_roof = max(B / BW, F_gemm / P_tc, F_fft / P_fp32)
+    with B = X read once + Phi written (no Qhat round trip), against the measured step."""
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    s = 8 if precision == "fp64" else 4
+    B = NT * M * s + nf * nmodes * M * (16 if precision == "fp64" else 8)
+    f_gram = 8.0 * nf * nb * nb * M
+    f_modes = 8.0 * nf * nb * nmodes * M
+    mult = {"bf16x3": 3, "bf16": 1}.get(precision)
+    if mult:
+        p_tc = peaks.get("bf16_tflops_sustained", 1700.0) * 1e12
+        t_gemm = mult * (f_gram + f_modes) / p_tc
+    else:
+        t_gemm = (f_gram / 2 + f_modes) / (FP32_PEAK * 1e12)
+    import math
+    t_fft = 2.5 * NFFT * math.log2(NFFT) * nb * M / (FP32_PEAK * 1e12)
+    t_hbm = B / hbm
+    t_roof = max(t_hbm, t_gemm, t_fft)
+    return {"t_roof_ms": round(t_roof * 1e3, 3), "frac": round(t_roof * 1e3 / ms_step, 4),
+            "t_hbm_ms": round(t_hbm * 1e3, 3), "t_gemm_ms": round(t_gemm * 1e3, 3), "t_fft_ms": round(t_fft * 1e3, 3),
+            "bytes": int(B), "note": "B = X read once + Phi written; a Qhat round trip counts against the step"}
 
 
 def e2e_leg(sp, X, nmodes, args, world):
