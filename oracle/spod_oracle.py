@@ -446,3 +446,35 @@ def point_qhat(xcol: np.ndarray, d: Desc, mu_m: float) -> np.ndarray:
                      d.w(), np.array([mu_m]) if d.subtract_mean else None)[:, :, 0]
 
 
+
+
+def gram_at_freqs(d: Desc, fsel, get_chunk, chunk: int) -> np.ndarray:
+    """M_f (Eq. spod-discrete-snapshots) at the selected one-sided bins only.
+
+    For grids too large for a full FP64 transform: X is visited in spatial
+    chunks (``get_chunk(m0, m1)`` returns X[:, m0:m1], promoted exactly to
+    FP64); each chunk's columns get their own temporal mean over all nt
+    snapshots (a column's mean depends on that column alone), and Qhat is
+    formed from the rows of the DFT matrix for the bins in ``fsel`` (the plain
+    definition of Eq. blocks-ft restricted to those f).  Returns [len(fsel)][nb][nb].
+    """
+    fsel = np.asarray(fsel, dtype=np.int64)
+    W = d.W()
+    w = d.w()
+    c = 1.0 / w.sum()
+    E = dft_matrix(d.nfft)[fsel]                      # [F][nfft]
+    Er, Ei = np.ascontiguousarray(E.real), np.ascontiguousarray(E.imag)
+    step = d.nfft - d.noverlap
+    acc = np.zeros((len(fsel), d.nb, d.nb), dtype=np.complex128)
+    for m0 in range(0, d.M, chunk):
+        m1 = min(d.M, m0 + chunk)
+        xc = np.asarray(get_chunk(m0, m1), dtype=np.float64)
+        if d.subtract_mean:
+            xc = xc - time_mean(xc)[None, :]
+        Q = np.empty((len(fsel), d.nb, m1 - m0), dtype=np.complex128)
+        for l in range(d.nb):
+            xw = w[:, None] * xc[l * step: l * step + d.nfft]
+            Q[:, l, :] = c * (Er @ xw + 1j * (Ei @ xw))
+        Qw = np.conj(Q) * W[None, None, m0:m1]
+        acc += np.matmul(Qw, np.transpose(Q, (0, 2, 1)))
+    return acc / gram_denominator(d.nb, d.norm)

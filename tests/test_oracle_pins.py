@@ -347,3 +347,29 @@ def test_gradient_identity_weights_is_time_domain_parseval():
         ref[l * step:l * step + d.nfft] += 2 * C * (w ** 2)[:, None] * d.W()[None, :] * xt[l * step:l * step + d.nfft]
     ref -= ref.mean(axis=0)
     np.testing.assert_allclose(G, ref, atol=1e-12 * np.abs(ref).max())
+
+
+def test_gram_at_freqs_closed_form_and_full_gram():
+    # Selected-bin Gram over spatial chunks: closed-form planted eigenvalues
+    # (periodic Hamming, with a per-point offset removed by each chunk's own
+    # mean) and the full-transform Gram on a noisy case
+    npts, nt, nfft = 40 * 24, 1024, 128
+    W = torch.tensor(0.5 + _rng(21).random(npts))
+    off = torch.tensor(_rng(22).standard_normal(npts) * 5.0)
+    wl = planted(npts, 1, nt, nfft, nfft // 2, bins=(3, 17, 40), amps=(1.0, 2.0, 0.5), noise_std=0.0,
+                 weights=W, seed=23, offset=off)
+    d = O.Desc(nt=nt, M=npts, nfft=nfft, noverlap=nfft // 2, window=O.WIN_HAMMING_PERIODIC, weights=W.numpy())
+    X = wl.X.numpy()
+    fsel = [3, 4, 17, 40, 41, 55]
+    G = O.gram_at_freqs(d, fsel, lambda a, b: X[:, a:b], chunk=100)
+    lam = np.sort(np.linalg.eigvalsh(G), axis=1)[:, ::-1]
+    r = (0.23 / 0.54) ** 2
+    expect = {3: 0.25, 4: 0.25 * r, 17: 1.0, 40: 0.0625, 41: 0.0625 * r, 55: 0.0}
+    for i, f in enumerate(fsel):
+        assert abs(lam[i, 0] - expect[f]) < 1e-12, f
+        assert lam[i, 1] < 1e-12
+    rng = _rng(24)
+    Xn = X + 0.1 * rng.standard_normal(X.shape)
+    Gn = O.gram_at_freqs(d, fsel, lambda a, b: Xn[:, a:b], chunk=77)
+    full = O.gram(O.block_dft(Xn, nfft, nfft // 2, d.w(), O.time_mean(Xn)), d.W())
+    np.testing.assert_allclose(Gn, full[fsel], rtol=0, atol=1e-13 * np.abs(full).max())
