@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a reduced grid for quick checks (not a bench value)")
+    ap.add_argument("--grid", default=None, help="NXxNR grid for profiling runs (not a bench value)")
     return ap.parse_args()
 
 
@@ -156,6 +157,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     nx, nr = (64, 64) if args.small else (NX, NR)
+    if args.grid:
+        nx, nr = (int(v) for v in args.grid.lower().split("x"))
     wl = jet_like(nx=nx, nr=nr, nvars=NVARS, nt=NT, nfft=NFFT, seed=rank, dtype=torch.float32, device=dev)
     X = wl.X
     M = X.shape[1]
@@ -208,7 +211,7 @@ def main():
                                                        for k, v in rf["phase_ms"].items()}}
 
     # ---- end to end through the C ABI with host buffers
-    if not args.no_e2e and rank == 0 and not args.small:
+    if not args.no_e2e and rank == 0 and not args.small and not args.grid:
         if sp is None:
             sp = make_plan(args.precision, wl)
         line["e2e"] = e2e_leg(sp, X, nmodes, args, world)

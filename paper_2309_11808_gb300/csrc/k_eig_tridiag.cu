@@ -157,57 +157,76 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
   __syncthreads();
 
   // ---------------- 2. implicit QL with Wilkinson shifts; e[i] couples d[i], d[i+1]
+  // Warp 0 finds the end mm of the unreduced block (lanes test 32 indices at
+  // once), lane 0 runs the rotation chain.  FP64 is slow on this part, so the
+  // chain forms each rotation from one reciprocal square root (r^2 = f^2 + g^2,
+  // s = f / r, c = g / r) instead of hypot and two divisions; the scaled hypot
+  // path is kept for r^2 outside [2^-960, 2^960].
+  const int warp = tid >> 5, lane = tid & 31;
   for (int l = 0; l < n; ++l) {
     for (int iter = 0;; ++iter) {
-      if (tid == 0) {
-        int mm = l;
-        for (; mm < n - 1; ++mm) {
-          const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
-          if (fabs(e[mm]) <= 0x1p-53 * dd) break;
+      if (warp == 0) {
+        int mm = n - 1;
+        for (int base = l; base < n - 1; base += 32) {
+          const int i = base + lane;
+          bool split = false;
+          if (i < n - 1) split = fabs(e[i]) <= 0x1p-53 * (fabs(d[i]) + fabs(d[i + 1]));
+          const unsigned bal = __ballot_sync(0xffffffffu, split);
+          if (bal) { mm = base + __ffs(bal) - 1; break; }
         }
-        int nrot = 0;
-        if (mm != l) {
-          if (iter >= kMaxIter) {
-            ctl[0] = 1;
-            mm = l;                                    // give up on this eigenvalue
-          } else {
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? fabs(r) : -fabs(r)));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int i = mm - 1;
-            bool underflow = false;
-            for (; i >= l; --i) {
-              double ff = s * e[i];
-              const double b = c * e[i];
-              r = hypot(ff, g);
-              e[i + 1] = r;
-              if (r == 0.0) {
-                d[i + 1] -= p;
-                e[mm] = 0.0;
-                underflow = true;
-                break;
+        if (lane == 0) {
+          int nrot = 0;
+          if (mm != l) {
+            if (iter >= kMaxIter) {
+              ctl[0] = 1;
+              mm = l;                                    // give up on this eigenvalue
+            } else {
+              double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+              double r = sqrt(fma(g, g, 1.0));
+              g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+              double s = 1.0, c = 1.0, p = 0.0;
+              bool underflow = false;
+              for (int i = mm - 1; i >= l; --i) {
+                const double ff = s * e[i];
+                const double b = c * e[i];
+                const double r2 = fma(ff, ff, g * g);
+                if (r2 > 0x1p-960 && r2 < 0x1p960) {
+                  const double ri = rsqrt(r2);
+                  r = r2 * ri;
+                  s = ff * ri;
+                  c = g * ri;
+                } else {
+                  r = hypot(ff, g);
+                  if (r == 0.0) {
+                    e[i + 1] = 0.0;
+                    d[i + 1] -= p;
+                    e[mm] = 0.0;
+                    underflow = true;
+                    break;
+                  }
+                  s = ff / r;
+                  c = g / r;
+                }
+                e[i + 1] = r;
+                g = d[i + 1] - p;
+                r = fma(d[i] - g, s, 2.0 * c * b);
+                p = s * r;
+                d[i + 1] = g + p;
+                g = fma(c, r, -b);
+                rc[nrot] = c;
+                rsn[nrot] = s;
+                ++nrot;
               }
-              s = ff / r;
-              c = g / r;
-              g = d[i + 1] - p;
-              r = (d[i] - g) * s + 2.0 * c * b;
-              p = s * r;
-              d[i + 1] = g + p;
-              g = c * r - b;
-              rc[nrot] = c;
-              rsn[nrot] = s;
-              ++nrot;
-            }
-            if (!underflow) {
-              d[l] -= p;
-              e[l] = g;
-              e[mm] = 0.0;
+              if (!underflow) {
+                d[l] -= p;
+                e[l] = g;
+                e[mm] = 0.0;
+              }
             }
           }
+          ctl[1] = mm;
+          ctl[2] = nrot;
         }
-        ctl[1] = mm;
-        ctl[2] = nrot;
       }
       __syncthreads();
       const int mm = ctl[1], nrot = ctl[2];
@@ -218,8 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
           const int i = mm - 1 - q;
           const double c = rc[q], s = rsn[q];
           const double fz = zr[i + 1];
-          zr[i + 1] = s * zr[i] + c * fz;
-          zr[i] = c * zr[i] - s * fz;
+          zr[i + 1] = fma(s, zr[i], c * fz);
+          zr[i] = fma(c, zr[i], -s * fz);
         }
       }
       __syncthreads();
