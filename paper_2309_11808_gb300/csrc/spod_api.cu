@@ -383,6 +383,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
   const size_t o_eigws = nb > kEigSmemMaxNb ? carve(sizeof(double) * eig_tridiag_gws_doubles(nb, nf)) : 0;
   const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
+  const size_t o_bimg = p->tensor ? carve(modes_image_bytes(*p)) : 0;
   const size_t o_wc = carve(2 * R * (size_t)nf);
   const size_t o_qhat = carve(per_point * (size_t)chunk);
   p->ws.bytes = off;
@@ -409,6 +410,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_psi = reinterpret_cast<double*>(b + o_psi);
   p->d_eigws = nb > kEigSmemMaxNb ? reinterpret_cast<double*>(b + o_eigws) : nullptr;
   p->d_bmat = b + o_bmat;
+  if (p->tensor) p->d_bimg = b + o_bimg;
   p->d_wc = b + o_wc;
   p->d_qhat = b + o_qhat;
   if (d->precision == SPOD_PREC_BF16X3)
@@ -622,6 +624,10 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
   {
     Phase ph(p, SPOD_PHASE_MODES, s, 1);
     SPOD_CUDA(launch_mode_coeffs(*p, nmodes, s), "mode coefficient kernel");
+    if (p->tensor) {
+      SPOD_CUDA(launch_mode_image(*p, nmodes, s), "mode operand image kernel");
+      ph.n += 1;
+    }
   }
   if (p->qhat_valid) {
     Phase ph(p, SPOD_PHASE_MODES, s, 0);
@@ -681,6 +687,10 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
   Phase ph(p, SPOD_PHASE_BACKWARD, s, 0);
   SPOD_CUDA(launch_adj_gmat(*p, d_dLdlambda, s), "adjoint G kernel");
   ph.n += 1;
+  if (p->tensor) {
+    SPOD_CUDA(launch_mode_image(*p, p->nb, s), "adjoint operand image kernel");
+    ph.n += 1;
+  }
   alignas(64) CUtensorMap xmap;
   const CUtensorMap* xm = nullptr;
   if (!p->qhat_valid && p->ring_ok) {

@@ -100,6 +100,7 @@ struct spod_plan_s {
   double* d_lam = nullptr;         // [nf][nb]
   double* d_psi = nullptr;         // [nf][nb][nb][2]
   double* d_eigws = nullptr;       // [nf][2][nbp][nbp][2] eigen-solver scratch (large nb)
+  void* d_bimg = nullptr;          // tensor path: per-frequency BF16 B images of the mode GEMM
   void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa), or G_f
   void* d_wc = nullptr;            // [nf] complex compute type: c sum_n w_n e^{+2 pi i f n / nfft}
   void* d_radj = nullptr;          // [nf][nb][M] complex compute type: R_f of the adjoint (allocated on first use)
@@ -147,6 +148,8 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
                                   cudaStream_t s, bool adjoint = false);
 size_t gram_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_tc_smem_bytes(const spod_plan_s& p);
+size_t modes_image_bytes(const spod_plan_s& p);
+cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s);
 int gram_tc_splits(const spod_plan_s& p, int64_t nkb);
 
 cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, double* psi, double* gws,
