@@ -201,7 +201,9 @@ spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, vo
  * split across CTAs, never what is computed beyond floating-point grouping.
  * In spod_plan_set_tuning a zero field keeps the plan's current value. */
 typedef struct {
-  int gram_splits;        /* CTAs per frequency over the points of a chunk, 1..gram_splits_max */
+  int gram_splits;        /* FP32/FP64: CTAs per frequency over the points of a chunk; BF16/BF16X3:
+                             persistent CTAs of the tensor-core Gram (default one per SM);
+                             1..gram_splits_max */
   int gram_splits_max;    /* read-only: bound set by the plan's workspace */
   int gram_flush_blocks;  /* tensor-core Gram: 64-point blocks per FP32 accumulation group (1..64) */
   int modes_ctas;         /* tensor-core modes: CTAs per frequency (0 = automatic) */

@@ -2,94 +2,136 @@
 // M_f = kappa * Qhat_f^* W Qhat_f from BF16 operands (BF16 precision) or from
 // the split x = hi + lo (BF16X3 precision), FP32 accumulation in tensor memory.
 //
-// BF16X3 uses three MMAs per K step and still keeps all four product terms:
-// the Gram is symmetric, so with A1 = Yhi Yhi^T + Ylo Ylo^T and A2 = Yhi Ylo^T
-// (two TMEM accumulators), Y Y^T = A1 + A2 + A2^T.  Dropping Ylo Ylo^T instead
-// would bias the diagonal low by E[lo^2] / x^2 ~ 2.4e-6 and move small
-// eigenvalues by that much times (tr M_f / nb) / lambda_k.
-//
 // Real embedding: with Y_f = [Re Qhat_f ; Im Qhat_f] (2nb rows x points, K-major
-// in HBM), D = Y_f Y_f^T gives
+// in HBM; sqrt(W) is already folded into Qhat), D = Y_f Y_f^T gives
 //   Re M_f[l][l'] = D[l][l'] + D[nb+l][nb+l'],  Im M_f[l][l'] = D[l][nb+l'] - D[nb+l][l'].
-// One TMA box (64 points x NP rows, NP = 2nb rounded up to 16, 128-byte
-// swizzle) is both the A operand (M = 128 rows; rows >= NP are zero) and the
-// B operand (N = NP) of tcgen05.mma.cta_group::1.kind::f16, K = 16 per
-// instruction, 4 instructions per 64-point block (x3 for BF16X3).
+// An item is two 64-point blocks of one frequency; its stage holds the TMA
+// boxes (NP rows x 64 points x 2 blocks, NP = 2nb rounded up to 16, 128-byte
+// swizzle) of hi and, for BF16X3, of lo.  Per K step of 16 (N = NP):
+//   A1 (+)= hi hi^T   restarted every `flush` blocks (short FP32 runs in the
+//                      tensor core), drained into Kahan-compensated registers;
+//   A2 (+)= hi lo^T   BF16X3, one run per frequency segment (2^-8 of D, so its
+//                      tensor-core rounding is far below the FP32 level of D),
+//                      read once when the segment ends;
+// and Y Y^T = A1 + A2 + A2^T + lo lo^T, with lo hi^T = (hi lo^T)^T taken in FP64
+// when the partials are collected.  Of lo lo^T (2^-16 of D) only the diagonal
+// sum_p lo_r[p]^2 is kept, summed by two warps straight from the staged lo
+// tiles: its off-diagonal entries are sums of uncorrelated rounding products
+// (relative size 2^-16 / sqrt(points)), while the diagonal is a bias (about
+// 2.4e-6 of D) that would shift small eigenvalues.  A operand rows >= 2nb only
+// feed accumulator rows that are never read.
 //
-// Warp roles (320 threads): warp 8 lane 0 issues TMA into a 4-stage ring,
-// warp 9 lane 0 issues the MMAs, warps 0-7 (two per TMEM lane quadrant) drain
-// the accumulators every `flush` blocks of 64 points (short FP32 runs in the
-// tensor core) and add them into compensated FP32 (sum, carry) registers.
-// The accumulators are double-buffered in TMEM so draining overlaps the next
-// group's MMAs; the drain stages S1 = A1 + A2 and S2 = A2 in shared memory
-// (Y Y^T = S1 + S2^T) with one TMEM wait per 32 columns.  Partials per (split, frequency) go to the same FP64 buffer as
-// the SIMT kernel and are reduced in fixed order by k_gram_reduce.
+// Persistent CTAs (one per SM by default) walk a contiguous range of the
+// f-major list of (frequency, block pair) items.  Warp 8 issues TMA into a
+// ring of stages, warp 9 issues the MMAs, warps 0-7 drain TMEM (two warps per
+// lane quadrant, half of the columns each; quadrants without a row < 2nb
+// skip the reads) and warps 10-11 sum the lo squares.  When the CTA's run of
+// a frequency ends the sums go to slot (cta + f) (the pairs (cta, f) of
+// contiguous ranges are monotone in both, so cta + f is unique);
+// k_gram_tc_collect adds the slots of every frequency in CTA order (no
+// atomics: bit-reproducible) and k_gram_tc_finish forms M_f.
+#include <algorithm>
+
 #include "tc_common.cuh"
 
 namespace spod {
 namespace {
 
-constexpr int kStages = 4;
-constexpr int kTileBytes = 128 * 128;     // 128 rows x 64 BF16
+constexpr int kMaxStages = 8;
+constexpr int kKpb = 2;                   // 64-point blocks per item (one TMA copy per operand)
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
-constexpr int kThreadsGram = (kEpiWarps + 2) * 32;
-constexpr int kMaxPerThread = 9;          // nb <= 64: nb (nb+1) / 2 <= 9 * 256
-constexpr uint32_t kTmemCols = 512;       // buffer b: A1 at 256 b, A2 at 256 b + 128
+constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kDiagWarp0 = kEpiWarps + 2;
+constexpr int kDiagThreads = 64;
+constexpr int kThreadsGram = (kEpiWarps + 4) * 32;
+constexpr uint32_t kTmemCols = 512;       // A1 buffers at columns 0 and 128, A2 buffers at 256 and 384
 
 struct GramTcArgs {
-  int nb, rows2, np, nf, ne;
-  int64_t kb_per_split, nkb;              // 64-point blocks per split, blocks in the chunk
-  int first;
-  int flush;                              // blocks per FP32 accumulation group
+  int nb, r2, np, nf;
+  int64_t nkb;                            // items (block pairs) per frequency in this chunk
+  int64_t nblk;                           // 64-point blocks per frequency in this chunk
+  int64_t nitems;                         // nf * nkb
+  int flush;                              // items per A1 run
+  int nst;                                // pipeline stages
+  uint32_t box_bytes;                     // one 64-point block of one operand: NP rows x 128 bytes
 };
 
-// Neumaier compensated addition: (s, c) += y
-__device__ __forceinline__ void comp_add(float& s, float& c, float y) {
-  const float t = s + y;
-  c += fabsf(s) >= fabsf(y) ? (s - t) + y : (y - t) + s;
+// Kahan compensated addition: (s, c) += y
+__device__ __forceinline__ void kahan_add(float& s, float& c, float y) {
+  const float yy = y - c;
+  const float t = s + yy;
+  c = (t - s) - yy;
   s = t;
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 struct GramHdr {
-  uint64_t full[kStages], empty[kStages], accfull[2], accempty[2], drain;
+  uint64_t full[kMaxStages], empty[kMaxStages], accfull[2], accempty[2], a2empty[2], drain;
   uint32_t tmem_base;
   int abort;
-  volatile int decision;
 };
 
-template <bool X3>
+// Walks the group and segment structure of a CTA's item range: a segment is
+// the run of one frequency, a group at most `flush` consecutive items of a
+// segment.  All roles step it identically.
+struct GroupWalk {
+  int64_t fprev = -1;
+  int in_group = 0;
+  int g = -1, seg = -1;
+  bool sstart = false;
+  __device__ __forceinline__ bool step(int64_t f, int flush) {   // true when the item starts a group
+    sstart = f != fprev;
+    const bool start = sstart || in_group == flush;
+    if (sstart) ++seg;
+    if (start) { ++g; in_group = 0; }
+    ++in_group;
+    fprev = f;
+    return start;
+  }
+};
+
+// Slot layout (bytes): A1 (sum, carry) pairs [r2][r2] float2, A2 [r2][r2]
+// float, then the lo-square diagonal [r2] float.
+__host__ __device__ inline size_t gram_slot_bytes(int r2) { return (size_t)r2 * r2 * 12 + (size_t)r2 * 4; }
+
+template <bool X3, int HC>
 __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_constant__ CUtensorMap map_hi,
                                                    const __grid_constant__ CUtensorMap map_lo, GramTcArgs a,
-                                                   double* __restrict__ gpart, unsigned* __restrict__ gflags) {
+                                                   uint8_t* __restrict__ slots, unsigned* __restrict__ gflags) {
   using namespace tc;
   constexpr int NOPS = X3 ? 2 : 1;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   GramHdr* hdr = reinterpret_cast<GramHdr*>(sm);
   uint8_t* stages = sm + 1024;
-  const int RS = a.rows2 | 1;               // odd staging stride: conflict-free rows and columns
-  float* Ds = reinterpret_cast<float*>(stages + kStages * NOPS * kTileBytes);   // S1 = A1 + A2
-  float* Qs = Ds + a.rows2 * RS;                                                  // S2 = A2 (BF16X3)
-  uint32_t* pairs = reinterpret_cast<uint32_t*>(Qs + (X3 ? a.rows2 * RS : 0));
+  const uint32_t op_bytes = a.box_bytes * kKpb;          // one operand of an item
+  const uint32_t stage_bytes = op_bytes * NOPS;          // [hi blocks][lo blocks]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int s_idx = blockIdx.x, f = blockIdx.y;
-  const int64_t kb0 = (int64_t)s_idx * a.kb_per_split;
-  const int64_t kb1 = min(a.nkb, kb0 + a.kb_per_split);
-  const int nkbl = (int)max((int64_t)0, kb1 - kb0);
+  const int64_t i0 = a.nitems * blockIdx.x / gridDim.x;
+  const int64_t i1 = a.nitems * (blockIdx.x + 1) / gridDim.x;
+  const int nit = (int)(i1 - i0);
   const int FB = a.flush;
-  const int ngroups = (nkbl + FB - 1) / FB;
 
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < a.nst; ++i) {
       mbar_init(smem_u32(&hdr->full[i]), 1);
-      mbar_init(smem_u32(&hdr->empty[i]), 1);
+      // released by the MMA commit, and for BF16X3 also by the lo-square warps
+      mbar_init(smem_u32(&hdr->empty[i]), X3 ? 1 + kDiagThreads : 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&hdr->accfull[i]), 1);
       mbar_init(smem_u32(&hdr->accempty[i]), kEpiThreads);
+      mbar_init(smem_u32(&hdr->a2empty[i]), kEpiThreads);
     }
     mbar_init(smem_u32(&hdr->drain), 1);
     hdr->abort = 0;
@@ -99,148 +141,196 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
     tmem_alloc(smem_u32(&hdr->tmem_base), kTmemCols);
     tmem_relinquish();
   }
-  // rows np..127 of every stage tile are never written by TMA: zero them once
-  {
-    const int pad_bytes = (128 - a.np) * 128;
-    for (int t = 0; t < kStages * NOPS; ++t) {
-      uint4* p = reinterpret_cast<uint4*>(stages + t * kTileBytes + a.np * 128);
-      for (int i = tid; i < pad_bytes / 16; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
-    }
-  }
-  for (int e = tid; e < a.ne; e += blockDim.x) {
-    // e -> (l, l'), l <= l', row-major over the upper triangle
-    int l = 0, rem = e;
-    while (rem >= a.nb - l) { rem -= a.nb - l; ++l; }
-    pairs[e] = (uint32_t)l | ((uint32_t)(l + rem) << 16);
-  }
-  fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = hdr->tmem_base;
   volatile int* abort_flag = &hdr->abort;
 
-  if (warp == kTmaWarp && lane == 0 && nkbl > 0) {
+  if (warp == kTmaWarp && lane == 0 && nit > 0) {
     // ---------------- TMA producer
     prefetch_tmap(&map_hi);
     if (X3) prefetch_tmap(&map_lo);
-    const uint32_t bytes = (uint32_t)a.np * 128u * NOPS;
     int issued = 0;
-    for (int kb = 0; kb < nkbl; ++kb) {
-      const int s = kb % kStages, u = kb / kStages;
+    for (int i = 0; i < nit; ++i) {
+      const int64_t item = i0 + i;
+      const int64_t f = item / a.nkb, kp = item - f * a.nkb;
+      const int s = i % a.nst, u = i / a.nst;
       if (u >= 1 && !mbar_wait(smem_u32(&hdr->empty[s]), (u - 1) & 1, abort_flag, gflags)) break;
       const uint32_t fb = smem_u32(&hdr->full[s]);
-      mbar_arrive_expect_tx(fb, bytes);
-      const int kblk = (int)(kb0 + kb);        // 64-point block of the blocked Qhat layout
-      tma_load_4d(smem_u32(stages + (s * NOPS) * kTileBytes), &map_hi, 0, 0, f, kblk, fb);
-      if (X3) tma_load_4d(smem_u32(stages + (s * NOPS + 1) * kTileBytes), &map_lo, 0, 0, f, kblk, fb);
-      issued = kb + 1;
+      mbar_arrive_expect_tx(fb, stage_bytes);
+      uint8_t* st = stages + (size_t)s * stage_bytes;
+      tma_load_4d(smem_u32(st), &map_hi, 0, 0, (int)f, (int)(kp * kKpb), fb);
+      if (X3) tma_load_4d(smem_u32(st + op_bytes), &map_lo, 0, 0, (int)f, (int)(kp * kKpb), fb);
+      issued = i + 1;
     }
     // copies still in flight must land before the CTA can exit
-    for (int kb = max(0, issued - kStages); kb < issued; ++kb)
-      mbar_drain(smem_u32(&hdr->full[kb % kStages]), (kb / kStages) & 1, gflags);
-  } else if (warp == kMmaWarp && lane == 0 && nkbl > 0) {
+    for (int i = max(0, issued - a.nst); i < issued; ++i)
+      mbar_drain(smem_u32(&hdr->full[i % a.nst]), (i / a.nst) & 1, gflags);
+  } else if (warp == kMmaWarp && lane == 0 && nit > 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(128, a.np, 0, 0);
-    for (int kb = 0; kb < nkbl; ++kb) {
-      const int g = kb / FB, acc = g & 1;
-      const bool gfirst = (kb % FB) == 0;
-      if (gfirst && g >= 2 && !mbar_wait(smem_u32(&hdr->accempty[acc]), ((g >> 1) - 1) & 1, abort_flag, gflags))
+    GroupWalk gw;
+    for (int i = 0; i < nit; ++i) {
+      const int64_t item = i0 + i;
+      const int64_t f = item / a.nkb, kp = item - f * a.nkb;
+      const bool gstart = gw.step(f, FB);
+      const bool sstart = gw.sstart;
+      const int g = gw.g, acc = g & 1, sg = gw.seg, a2b = sg & 1;
+      const int64_t fn = (i + 1 < nit) ? (item + 1) / a.nkb : -1;
+      const bool gend = i + 1 == nit || fn != f || gw.in_group == FB;
+      if (gstart && g >= 2 && !mbar_wait(smem_u32(&hdr->accempty[acc]), ((g >> 1) - 1) & 1, abort_flag, gflags))
         break;
-      const int s = kb % kStages, u = kb / kStages;
+      if (X3 && sstart && sg >= 2 &&
+          !mbar_wait(smem_u32(&hdr->a2empty[a2b]), ((sg >> 1) - 1) & 1, abort_flag, gflags))
+        break;
+      const int s = i % a.nst, u = i / a.nst;
       if (!mbar_wait(smem_u32(&hdr->full[s]), u & 1, abort_flag, gflags)) break;
       tc_fence_after();
-      const uint32_t hi = smem_u32(stages + (s * NOPS) * kTileBytes);
-      const uint32_t lo = smem_u32(stages + (s * NOPS + 1) * kTileBytes);
-      const uint32_t d1 = tmem + (uint32_t)acc * 256u;
-      const uint32_t d2 = d1 + 128u;
+      const uint32_t st = smem_u32(stages + (size_t)s * stage_bytes);
+      const uint32_t d1 = tmem + (uint32_t)acc * 128u;
+      const uint32_t d2 = tmem + 256u + (uint32_t)a2b * 128u;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t first_k = (gfirst && k == 0) ? 0u : 1u;
-        const uint64_t dh = sdesc_sw128(hi + k * 32, 16, 1024);
-        mma_bf16(d1, dh, dh, idesc, first_k);
-        if (X3) {
-          const uint64_t dl = sdesc_sw128(lo + k * 32, 16, 1024);
-          mma_bf16(d1, dl, dl, idesc, 1u);
-          mma_bf16(d2, dh, dl, idesc, first_k);
+      for (int j = 0; j < kKpb; ++j) {
+        // a block past the chunk's points (odd block count) holds no data of this chunk
+        if (kp * kKpb + j >= a.nblk) break;
+        const uint32_t hi = st + (uint32_t)j * a.box_bytes;
+        const uint32_t lo = hi + op_bytes;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t dh = sdesc_sw128(hi + k * 32, 16, 1024);
+          mma_bf16(d1, dh, dh, idesc, (gstart && j == 0 && k == 0) ? 0u : 1u);     // A1 (+)= hi hi^T
+          if (X3) {
+            const uint64_t dl = sdesc_sw128(lo + k * 32, 16, 1024);
+            mma_bf16(d2, dh, dl, idesc, (sstart && j == 0 && k == 0) ? 0u : 1u);   // A2 (+)= hi lo^T
+          }
         }
       }
       mma_commit(smem_u32(&hdr->empty[s]));
-      if ((kb % FB) == FB - 1 || kb == nkbl - 1) mma_commit(smem_u32(&hdr->accfull[acc]));
+      if (gend) mma_commit(smem_u32(&hdr->accfull[acc]));
     }
     mma_commit(smem_u32(&hdr->drain));
     mbar_drain(smem_u32(&hdr->drain), 0, gflags);
-  } else if (warp < kEpiWarps) {
-    // ---------------- epilogue: TMEM -> FP32 staging -> compensated FP32 sums
-    float sr[kMaxPerThread], cr[kMaxPerThread], si[kMaxPerThread], ci[kMaxPerThread];
+  } else if (X3 && warp >= kDiagWarp0 && nit > 0) {
+    // ---------------- lo-square diagonal of every lo block.  Eight threads
+    // share a row (one 16-byte chunk each, so a warp reads 512 contiguous
+    // bytes: no bank conflicts); a row's chunks are permuted by the swizzle,
+    // which a sum over the row does not see.  Thread t keeps the partial sums
+    // of rows t/8 + 8 j in q[j]; the eight partials of a row are combined by
+    // shuffles when the CTA's run of a frequency ends.
+    const int t = tid - kDiagWarp0 * 32;
+    const int rsub = t >> 3, chunk = t & 7;
+    constexpr int kRowsPer = 16;                      // rows rsub + 8 j, j < 16: up to 128 rows
+    float q[kRowsPer];
 #pragma unroll
-    for (int j = 0; j < kMaxPerThread; ++j) { sr[j] = 0.f; cr[j] = 0.f; si[j] = 0.f; ci[j] = 0.f; }
-    const int row = (warp & 3) * 32 + lane;
-    const int half = warp >> 2;               // takes the 32-column chunks c0 = 32 (2 k + half)
-    const int nb = a.nb, r2 = a.rows2;
-    for (int g = 0; g < ngroups; ++g) {
-      const int acc = g & 1;
-      // every epilogue thread takes the same stop/continue decision, so none
-      // can be left behind in a named barrier
-      mbar_wait(smem_u32(&hdr->accfull[acc]), (g >> 1) & 1, abort_flag, gflags);
-      named_sync(1, kEpiThreads);
-      if (tid == 0) hdr->decision = *abort_flag;
-      named_sync(1, kEpiThreads);
-      if (hdr->decision) break;
-      tc_fence_after();
-      const uint32_t t1 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)acc * 256u;
-      // stage S1 = A1 + A2 and S2 = A2 row by row (D = S1 + S2^T); 32 columns of
-      // each accumulator per load batch, one wait per batch
-      for (int c0 = 32 * half; c0 < a.np; c0 += 64) {
-        float v[32], w[32];
-        if (X3) {
-          tmem_ld32x2(t1 + c0, t1 + 128 + c0, v, w);
-        } else {
-          tmem_ld32x2(t1 + c0, t1 + c0, v, w);
+    for (int j = 0; j < kRowsPer; ++j) q[j] = 0.f;
+    for (int i = 0; i < nit; ++i) {
+      const int64_t item = i0 + i;
+      const int64_t f = item / a.nkb, kp = item - f * a.nkb;
+      const int64_t fn = (i + 1 < nit) ? (item + 1) / a.nkb : -1;
+      const bool send = i + 1 == nit || fn != f;
+      const int s = i % a.nst, u = i / a.nst;
+      if (!mbar_wait(smem_u32(&hdr->full[s]), u & 1, abort_flag, gflags)) break;
+      const int nvalid = (int)min((int64_t)kKpb, a.nblk - kp * kKpb);
+      for (int b = 0; b < nvalid; ++b) {
+        const uint8_t* lo = stages + (size_t)s * stage_bytes + op_bytes + (size_t)b * a.box_bytes;
+#pragma unroll
+        for (int j = 0; j < kRowsPer; ++j) {
+          const int r = rsub + 8 * j;
+          if (r < a.r2) {
+            const uint4 w4 = *reinterpret_cast<const uint4*>(lo + (size_t)r * 128 + chunk * 16);
+            const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+            float acc = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float la = __uint_as_float(ws[e] << 16), lb = __uint_as_float(ws[e] & 0xFFFF0000u);
+              acc = fmaf(la, la, acc);
+              acc = fmaf(lb, lb, acc);
+            }
+            q[j] += acc;
+          }
         }
-        if (row < r2) {
+      }
+      mbar_arrive(smem_u32(&hdr->empty[s]));
+      if (send) {
+        float* dg = reinterpret_cast<float*>(slots + ((size_t)blockIdx.x + (size_t)f) * gram_slot_bytes(a.r2) +
+                                             (size_t)a.r2 * a.r2 * 12);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (c0 + i < r2) {
-              Ds[row * RS + c0 + i] = X3 ? v[i] + w[i] : v[i];
-              if (X3) Qs[row * RS + c0 + i] = w[i];
+        for (int j = 0; j < kRowsPer; ++j) {
+          float v = q[j];
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          v += __shfl_xor_sync(0xffffffffu, v, 4);
+          const int r = rsub + 8 * j;
+          if (chunk == 0 && r < a.r2) dg[r] = v;
+          q[j] = 0.f;
+        }
+      }
+    }
+  } else if (warp < kEpiWarps) {
+    // ---------------- epilogue: TMEM -> registers -> slots
+    const int quad = warp & 3, half = warp >> 2;
+    const int hcols = a.np / 2;                   // multiple of 8, <= HC
+    const int row = quad * 32 + lane;
+    const int col0 = half * hcols;
+    const bool active = quad * 32 < a.r2;         // this lane quadrant holds rows of D
+    float s1[HC], c1[HC];
+#pragma unroll
+    for (int j = 0; j < HC; ++j) { s1[j] = 0.f; c1[j] = 0.f; }
+    GroupWalk gw;
+    for (int i = 0; i < nit; ++i) {
+      const int64_t item = i0 + i;
+      const int64_t f = item / a.nkb;
+      gw.step(f, FB);
+      const int64_t fn = (i + 1 < nit) ? (item + 1) / a.nkb : -1;
+      const bool send = i + 1 == nit || fn != f;
+      const bool gend = send || gw.in_group == FB;
+      if (!gend) continue;
+      const int g = gw.g, acc = g & 1, a2b = gw.seg & 1;
+      if (!mbar_wait(smem_u32(&hdr->accfull[acc]), (g >> 1) & 1, abort_flag, gflags)) break;
+      tc_fence_after();
+      uint8_t* slot = slots + ((size_t)blockIdx.x + (size_t)f) * gram_slot_bytes(a.r2);
+      const bool wr = send && row < a.r2;
+      if (active) {
+        // this warp's A1 columns in one batch of loads and one wait
+        const uint32_t t1 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 128u + (uint32_t)col0;
+        float v[HC];
+#pragma unroll
+        for (int c = 0; c < HC / 8; ++c)
+          if (c * 8 < hcols) tmem_ld8(t1 + (uint32_t)(c * 8), v + c * 8);
+        tmem_wait_ld();
+        tc_fence_before();
+        mbar_arrive(smem_u32(&hdr->accempty[acc]));
+        float2* d1 = reinterpret_cast<float2*>(slot) + (size_t)row * a.r2 + col0;
+#pragma unroll
+        for (int j = 0; j < HC; ++j) {
+          if (j < hcols) {
+            kahan_add(s1[j], c1[j], v[j]);
+            if (send) {
+              if (wr && col0 + j < a.r2) d1[j] = make_float2(s1[j], c1[j]);
+              s1[j] = 0.f;
+              c1[j] = 0.f;
             }
           }
         }
-      }
-      tc_fence_before();
-      mbar_arrive(smem_u32(&hdr->accempty[acc]));
-      named_sync(1, kEpiThreads);
+        if (X3 && send) {
+          // the segment's A2 (its MMAs completed with the last group's)
+          const uint32_t t2 = tmem + ((uint32_t)(quad * 32) << 16) + 256u + (uint32_t)a2b * 128u + (uint32_t)col0;
 #pragma unroll
-      for (int j = 0; j < kMaxPerThread; ++j) {
-        const int e = tid + kEpiThreads * j;
-        if (e < a.ne) {
-          const uint32_t pr = pairs[e];
-          const int l = pr & 0xFFFF, lp = pr >> 16;
-          // D[i][k] = S1[i][k] + S2[k][i]
-          float d1 = Ds[l * RS + lp] + Ds[(nb + l) * RS + nb + lp];
-          float d2 = Ds[l * RS + nb + lp] - Ds[(nb + l) * RS + lp];
-          if (X3) {
-            d1 += Qs[lp * RS + l] + Qs[(nb + lp) * RS + nb + l];
-            d2 += Qs[(nb + lp) * RS + l] - Qs[lp * RS + nb + l];
-          }
-          comp_add(sr[j], cr[j], d1);
-          comp_add(si[j], ci[j], d2);
+          for (int c = 0; c < HC / 8; ++c)
+            if (c * 8 < hcols) tmem_ld8(t2 + (uint32_t)(c * 8), v + c * 8);
+          tmem_wait_ld();
+          tc_fence_before();
+          mbar_arrive(smem_u32(&hdr->a2empty[a2b]));
+          float* d2 = reinterpret_cast<float*>(slot + (size_t)a.r2 * a.r2 * 8) + (size_t)row * a.r2 + col0;
+#pragma unroll
+          for (int j = 0; j < HC; ++j)
+            if (j < hcols && wr && col0 + j < a.r2) d2[j] = v[j];
         }
-      }
-      named_sync(1, kEpiThreads);
-    }
-    double* gp = gpart + (((int64_t)s_idx * a.nf + f) * nb) * nb * 2;
-#pragma unroll
-    for (int j = 0; j < kMaxPerThread; ++j) {
-      const int e = tid + kEpiThreads * j;
-      if (e < a.ne) {
-        const uint32_t pr = pairs[e];
-        const int l = pr & 0xFFFF, lp = pr >> 16;
-        double* o = gp + ((int64_t)l * nb + lp) * 2;
-        const double vr = (double)sr[j] + (double)cr[j], vi = (double)si[j] + (double)ci[j];
-        if (a.first) { o[0] = vr; o[1] = vi; }
-        else { o[0] += vr; o[1] += vi; }
+      } else {
+        tc_fence_before();
+        mbar_arrive(smem_u32(&hdr->accempty[acc]));
+        if (X3 && send) mbar_arrive(smem_u32(&hdr->a2empty[a2b]));
       }
     }
   }
@@ -252,54 +342,134 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
   }
 }
 
-}  // namespace
+// CTA c's item range is [floor(c W / G), floor((c+1) W / G)); the CTA holding item i.
+__device__ __forceinline__ int64_t cta_of_item(int64_t i, int64_t W, int64_t G) { return ((i + 1) * G - 1) / W; }
 
-size_t gram_tc_smem_bytes(const spod_plan_s& p) {
-  const int nops = p.desc.precision == SPOD_PREC_BF16X3 ? 2 : 1;
-  const int r2 = 2 * p.nb;
-  const int ne = p.nb * (p.nb + 1) / 2;
-  return 1024 + 1024 + (size_t)kStages * nops * kTileBytes + sizeof(float) * r2 * (r2 | 1) * nops +
-         sizeof(uint32_t) * ne;
+// acc[f] (+)= sum over the CTAs c that covered frequency f of slot (c + f), in
+// CTA order, of D = A1 + A2 + A2^T + diag(lo lo^T) (A1 as a compensated (sum, carry) pair).
+__global__ void k_gram_tc_collect(const uint8_t* __restrict__ slots, int r2, int64_t nkb, int64_t G, int x3,
+                                  int first, double* __restrict__ acc) {
+  const int f = blockIdx.x;
+  const int64_t W = (int64_t)gridDim.x * nkb;
+  const int64_t c0 = cta_of_item((int64_t)f * nkb, W, G);
+  const int64_t c1 = cta_of_item((int64_t)(f + 1) * nkb - 1, W, G);
+  double* dst = acc + (int64_t)f * r2 * r2;
+  const size_t sb = gram_slot_bytes(r2);
+  for (int e = threadIdx.x; e < r2 * r2; e += blockDim.x) {
+    const int i = e / r2, j = e - i * r2;
+    double v = 0.0;
+    for (int64_t c = c0; c <= c1; ++c) {
+      const uint8_t* slot = slots + (size_t)(c + f) * sb;
+      const float2 sc = reinterpret_cast<const float2*>(slot)[e];
+      v += (double)sc.x + (double)sc.y;
+      if (x3) {
+        const float* a2 = reinterpret_cast<const float*>(slot + (size_t)r2 * r2 * 8);
+        v += (double)a2[e] + (double)a2[j * r2 + i];
+        if (i == j) v += (double)reinterpret_cast<const float*>(slot + (size_t)r2 * r2 * 12)[i];
+      }
+    }
+    dst[e] = first ? v : dst[e] + v;
+  }
 }
 
-int gram_tc_splits(const spod_plan_s& p, int64_t nkb) {
-  // splits per frequency: at least 8 waves of one CTA per SM, least tail
-  const int sms = p.num_sms > 0 ? p.num_sms : 148;
-  int best = 1;
-  double best_waste = 1e30;
-  for (int s = 1; s <= 32; ++s) {
-    if (s > nkb) break;
-    const int64_t ctas = (int64_t)s * p.nf;
-    const int64_t waves = (ctas + sms - 1) / sms;
-    const double waste = (double)(waves * sms - ctas) / (double)ctas + (waves < 4 ? 1.0 : 0.0);
-    if (waste < best_waste - 1e-9) { best_waste = waste; best = s; }
+// M_f from D = Y Y^T: upper triangle formed, kappa applied, Hermitian completion, NaN check.
+__global__ void k_gram_tc_finish(const double* __restrict__ acc, int nb, double kappa, double* __restrict__ gram,
+                                 unsigned* __restrict__ flags) {
+  const int f = blockIdx.x;
+  const int r2 = 2 * nb;
+  const double* D = acc + (int64_t)f * r2 * r2;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e - i * nb;
+    const int l = min(i, j), lp = max(i, j);
+    double vr = D[l * r2 + lp] + D[(nb + l) * r2 + nb + lp];
+    double vi = D[l * r2 + nb + lp] - D[(nb + l) * r2 + lp];
+    vr *= kappa;
+    vi *= kappa;
+    if (i > j) vi = -vi;
+    if (i == j) {
+      vi = 0.0;
+      if (!isfinite(vr)) atomicOr(flags, FLAG_NAN);
+    }
+    double* o = gram + (((int64_t)f * nb + i) * nb + j) * 2;
+    o[0] = vr;
+    o[1] = vi;
   }
-  return best;
+}
+
+size_t gram_tc_smem_stages(const spod_plan_s& p, int nst) {
+  const int nops = p.desc.precision == SPOD_PREC_BF16X3 ? 2 : 1;
+  const size_t np = (size_t)((2 * p.nb + 15) / 16 * 16);
+  // + the rows an M = 128 A operand reads past the last stage's last block
+  return 1024 + 1024 + (size_t)nst * nops * kKpb * np * 128 + (128 - np) * 128;
+}
+
+template <bool X3, int HC>
+cudaError_t launch_gram_tc_t(const spod_plan_s& p, const GramTcArgs& a, int grid, size_t smem, cudaStream_t s) {
+  auto kern = k_gram_tc<X3, HC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreadsGram, smem, s>>>(p.tmap_hi2, X3 ? p.tmap_lo2 : p.tmap_hi2, a,
+                                        reinterpret_cast<uint8_t*>(p.d_gslot), p.d_flags);
+  return cudaGetLastError();
+}
+
+template <bool X3>
+cudaError_t launch_gram_tc_x(const spod_plan_s& p, const GramTcArgs& a, int grid, size_t smem, cudaStream_t s) {
+  const int hc = a.np / 2;                 // columns per epilogue thread, a multiple of 8
+  if (hc <= 16) return launch_gram_tc_t<X3, 16>(p, a, grid, smem, s);
+  if (hc <= 24) return launch_gram_tc_t<X3, 24>(p, a, grid, smem, s);
+  if (hc <= 32) return launch_gram_tc_t<X3, 32>(p, a, grid, smem, s);
+  if (hc <= 40) return launch_gram_tc_t<X3, 40>(p, a, grid, smem, s);
+  if (hc <= 48) return launch_gram_tc_t<X3, 48>(p, a, grid, smem, s);
+  return launch_gram_tc_t<X3, 64>(p, a, grid, smem, s);
+}
+
+}  // namespace
+
+// Shared memory of the smallest (2-stage) configuration; launches use up to 8 stages.
+size_t gram_tc_smem_bytes(const spod_plan_s& p) { return gram_tc_smem_stages(p, 2); }
+
+// Slots of the persistent kernel, (max CTAs + nf - 1) x 12 (2 nb)^2 bytes (counted
+// in doubles), and the per-frequency FP64 accumulator of D over chunks, nf x (2 nb)^2.
+size_t gram_tc_slot_doubles(const spod_plan_s& p, int max_ctas) {
+  return ((size_t)(max_ctas + p.nf - 1) * gram_slot_bytes(2 * p.nb) + 7) / 8;
+}
+size_t gram_tc_acc_doubles(const spod_plan_s& p) { return (size_t)p.nf * (2 * p.nb) * (2 * p.nb); }
+
+// Persistent CTAs of the tensor-core Gram: one per SM unless tuned.
+int gram_tc_ctas(const spod_plan_s& p) {
+  const int sms = p.num_sms > 0 ? p.num_sms : 148;
+  return p.gram_splits > 0 ? std::min(p.gram_splits, p.gram_splits_max) : sms;
 }
 
 cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s) {
   GramTcArgs a;
   a.nb = p.nb;
-  a.rows2 = 2 * p.nb;
+  a.r2 = 2 * p.nb;
   a.np = (2 * p.nb + 15) / 16 * 16;
   a.nf = p.nf;
-  a.ne = p.nb * (p.nb + 1) / 2;
-  a.nkb = (mcount + 63) / 64;
-  const int splits = p.gram_splits;
-  a.kb_per_split = (a.nkb + splits - 1) / splits;
-  a.first = first ? 1 : 0;
   a.flush = p.gram_flush > 0 ? p.gram_flush : 4;
-  const size_t smem = gram_tc_smem_bytes(p);
-  dim3 grid((unsigned)splits, (unsigned)p.nf);
-  if (p.desc.precision == SPOD_PREC_BF16X3) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gram_tc<true><<<grid, kThreadsGram, smem, s>>>(p.tmap_hi, p.tmap_lo, a, p.d_gpart, p.d_flags);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gram_tc<false><<<grid, kThreadsGram, smem, s>>>(p.tmap_hi, p.tmap_hi, a, p.d_gpart, p.d_flags);
-  }
+  a.box_bytes = (uint32_t)a.np * 128u;
+  a.nblk = (mcount + 63) / 64;
+  a.nkb = (a.nblk + kKpb - 1) / kKpb;
+  a.nitems = a.nkb * p.nf;
+  a.flush = std::max(1, a.flush / kKpb);  // the flush interval is given in 64-point blocks
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device);
+  a.nst = kMaxStages;
+  while (a.nst > 2 && gram_tc_smem_stages(p, a.nst) > (size_t)optin) --a.nst;
+  const size_t smem = gram_tc_smem_stages(p, a.nst);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(gram_tc_ctas(p), a.nitems));
+  cudaError_t e = p.desc.precision == SPOD_PREC_BF16X3 ? launch_gram_tc_x<true>(p, a, grid, smem, s)
+                                                        : launch_gram_tc_x<false>(p, a, grid, smem, s);
+  if (e != cudaSuccess) return e;
+  k_gram_tc_collect<<<p.nf, 256, 0, s>>>(reinterpret_cast<const uint8_t*>(p.d_gslot), a.r2, a.nkb, grid,
+                                         p.desc.precision == SPOD_PREC_BF16X3 ? 1 : 0, first ? 1 : 0, p.d_gacc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc_finish(const spod_plan_s& p, cudaStream_t s) {
+  k_gram_tc_finish<<<p.nf, 256, 0, s>>>(p.d_gacc, p.nb, p.kappa, p.d_gram, p.d_flags);
   return cudaGetLastError();
 }
 

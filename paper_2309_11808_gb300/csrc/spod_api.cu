@@ -201,12 +201,13 @@ spod_status make_qhat_maps(spod_plan_s* p) {
                               (cuuint64_t)(p->chunk_points / kQBlock)};
   const cuuint64_t row = (cuuint64_t)kQBlock * 2;
   const cuuint64_t strides[3] = {row, row * 2 * p->nb, row * 2 * p->nb * p->nf};
-  const cuuint32_t box[4] = {(cuuint32_t)kQBlock, (cuuint32_t)((2 * p->nb + 15) / 16 * 16), 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   void* bases[2] = {p->d_qhat, p->d_qlo ? p->d_qlo : p->d_qhat};
-  CUtensorMap* maps[2] = {&p->tmap_hi, &p->tmap_lo};
-  for (int i = 0; i < 2; ++i) {
-    CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, bases[i], dims, strides, box, estr,
+  CUtensorMap* maps[4] = {&p->tmap_hi, &p->tmap_lo, &p->tmap_hi2, &p->tmap_lo2};
+  for (int i = 0; i < 4; ++i) {
+    // boxes of one 64-point block, and of two consecutive blocks (fewer, larger copies)
+    const cuuint32_t box[4] = {(cuuint32_t)kQBlock, (cuuint32_t)((2 * p->nb + 15) / 16 * 16), 1, i < 2 ? 1u : 2u};
+    CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, bases[i & 1], dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -359,8 +360,9 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     p->mean_splits = (int)std::min<int64_t>(sp, 4096);
   }
   if (p->tensor) {
-    p->gram_splits = gram_tc_splits(*p, (chunk + 63) / 64);
-    p->gram_splits_max = (int)std::max<int64_t>(p->gram_splits, std::min<int64_t>(32, (chunk + 63) / 64));
+    // persistent tensor-core Gram: one CTA per SM by default (tunable up to two per SM)
+    p->gram_splits = p->num_sms > 0 ? p->num_sms : 148;
+    p->gram_splits_max = 2 * p->gram_splits;
   } else {
     int64_t s = (2048 + p->nf - 1) / p->nf;
     s = std::max<int64_t>(1, std::min<int64_t>(s, (chunk + 255) / 256));
@@ -377,7 +379,9 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_tw = carve(2 * R * p->nfft);
   const size_t o_sqrtW = carve(R * p->Mpad);
   const size_t o_rsqrtW = carve(R * p->Mpad);
-  const size_t o_gpart = carve(sizeof(double) * 2 * (size_t)p->gram_splits_max * nf * nb * nb);
+  const size_t o_gpart = p->tensor ? 0 : carve(sizeof(double) * 2 * (size_t)p->gram_splits_max * nf * nb * nb);
+  const size_t o_gslot = p->tensor ? carve(sizeof(double) * gram_tc_slot_doubles(*p, p->gram_splits_max)) : 0;
+  const size_t o_gacc = p->tensor ? carve(sizeof(double) * gram_tc_acc_doubles(*p)) : 0;
   const size_t o_gram = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
   const size_t o_lam = carve(sizeof(double) * (size_t)nf * nb);
   const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
@@ -404,7 +408,12 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_tw = b + o_tw;
   p->d_sqrtW = b + o_sqrtW;
   p->d_rsqrtW = b + o_rsqrtW;
-  p->d_gpart = reinterpret_cast<double*>(b + o_gpart);
+  if (p->tensor) {
+    p->d_gslot = reinterpret_cast<double*>(b + o_gslot);
+    p->d_gacc = reinterpret_cast<double*>(b + o_gacc);
+  } else {
+    p->d_gpart = reinterpret_cast<double*>(b + o_gpart);
+  }
   p->d_gram = reinterpret_cast<double*>(b + o_gram);
   p->d_lam = reinterpret_cast<double*>(b + o_lam);
   p->d_psi = reinterpret_cast<double*>(b + o_psi);
@@ -550,13 +559,14 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
       Phase ph(p, SPOD_PHASE_FFT, s, 1);
       if (spod_status st = run_fft_chunk(p, d_X, xm, m0, mc, s)) return st;
     }
-    Phase ph(p, SPOD_PHASE_GRAM, s, 1);
+    Phase ph(p, SPOD_PHASE_GRAM, s, p->tensor ? 2 : 1);
     if (p->tensor) SPOD_CUDA(launch_gram_tc_chunk(*p, mc, m0 == 0, s), "tensor-core gram kernel");
     else SPOD_CUDA(launch_gram_chunk(*p, mc, m0 == 0, s), "gram kernel");
   }
   {
     Phase ph(p, SPOD_PHASE_REDUCE, s, 1);
-    SPOD_CUDA(launch_gram_reduce(*p, s), "gram reduce kernel");
+    if (p->tensor) SPOD_CUDA(launch_gram_tc_finish(*p, s), "gram finish kernel");
+    else SPOD_CUDA(launch_gram_reduce(*p, s), "gram reduce kernel");
   }
   {
     Phase ph(p, SPOD_PHASE_EIG, s, 1);

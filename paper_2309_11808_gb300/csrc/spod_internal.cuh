@@ -91,10 +91,14 @@ struct spod_plan_s {
   bool tensor = false;             // BF16 / BF16X3: Gram and modes on the tensor cores
   CUtensorMap tmap_hi;            // TMA maps of d_qhat / d_qlo: dims {chunk, 2nb, nf}, box {64, round16(2nb), 1}
   CUtensorMap tmap_lo;
+  CUtensorMap tmap_hi2;           // the same planes, box {64, round16(2nb), 1, 2}: two 64-point blocks per copy
+  CUtensorMap tmap_lo2;
   CUtensorMap tmap_fst_hi;         // FFT output store maps: dims {chunk, 2nb, nf}, box {16, 1, 256}
   CUtensorMap tmap_fst_lo;         //   (FP32 planes, or BF16 hi / lo)
   bool fst_maps = false;
   int fst_fbox = 0;                // frequency rows per FFT output store box
+  double* d_gslot = nullptr;       // tensor path: FP64 (cta + f) slots of D = Y Y^T
+  double* d_gacc = nullptr;        // tensor path: [nf][2 nb][2 nb] FP64 D accumulated over chunks
   double* d_gpart = nullptr;       // [gram_splits][nf][nb][nb][2] FP64 partial Grams
   double* d_gram = nullptr;        // [nf][nb][nb][2] reduced Gram (kappa applied)
   double* d_lam = nullptr;         // [nf][nb]
@@ -150,7 +154,10 @@ size_t gram_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_image_bytes(const spod_plan_s& p);
 cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s);
-int gram_tc_splits(const spod_plan_s& p, int64_t nkb);
+size_t gram_tc_slot_doubles(const spod_plan_s& p, int max_ctas);
+size_t gram_tc_acc_doubles(const spod_plan_s& p);
+int gram_tc_ctas(const spod_plan_s& p);
+cudaError_t launch_gram_tc_finish(const spod_plan_s& p, cudaStream_t s);
 
 cudaError_t launch_eig_buffers(const double* gram, int nf, int nb, double* lam, double* psi, double* gws,
                                unsigned* flags, cudaStream_t s);

@@ -333,4 +333,9 @@ def test_tensor_path_chunked_matches_single_pass(nfft):
     for r in (a, b):
         well, normwise, _ = lam_gate_report(r["lam"], r["ref"].lam)
         assert well <= 1e-5 and normwise <= 1e-5
-    assert np.allclose(a["lam"], b["lam"], rtol=1e-5, atol=1e-12 * a["lam"].max())
+    # chunking changes only the FP32 accumulation order: compare normwise, and
+    # relatively where lambda_1 / lambda_j <= 10 (Weyl)
+    la, lb = a["lam"], b["lam"]
+    assert (np.abs(la - lb).max(axis=1) / la[:, 0]).max() <= 2e-6
+    well = la * 10.0 >= la[:, :1]
+    assert (np.abs(la - lb) / la)[well].max() <= 1e-5
