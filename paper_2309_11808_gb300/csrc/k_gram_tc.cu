@@ -84,11 +84,11 @@ struct GramHdr {
 // the run of one frequency, a group at most `flush` consecutive items of a
 // segment.  All roles step it identically.
 struct GroupWalk {
-  int64_t fprev = -1;
+  int fprev = -1;
   int in_group = 0;
   int g = -1, seg = -1;
   bool sstart = false;
-  __device__ __forceinline__ bool step(int64_t f, int flush) {   // true when the item starts a group
+  __device__ __forceinline__ bool step(int f, int flush) {   // true when the item starts a group
     sstart = f != fprev;
     const bool start = sstart || in_group == flush;
     if (sstart) ++seg;
@@ -96,6 +96,25 @@ struct GroupWalk {
     ++in_group;
     fprev = f;
     return start;
+  }
+};
+
+// Position of a CTA's item in the (frequency, block pair) list and in the
+// stage ring, advanced without divisions (the issuing threads are on the
+// critical path of every item).
+struct Cursor {
+  int f, kp;          // frequency, block pair within it
+  int s, ph;          // stage, parity of the ring pass (i / nst) & 1
+  __device__ __forceinline__ void init(int64_t item0, int nkb) {
+    f = (int)(item0 / nkb);
+    kp = (int)(item0 - (int64_t)f * nkb);
+    s = 0;
+    ph = 0;
+  }
+  __device__ __forceinline__ bool last_of_f(int nkb) const { return kp + 1 == nkb; }
+  __device__ __forceinline__ void next(int nkb, int nst) {
+    if (++kp == nkb) { kp = 0; ++f; }
+    if (++s == nst) { s = 0; ph ^= 1; }
   }
 };
 
@@ -121,6 +140,7 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
   const int64_t i1 = a.nitems * (blockIdx.x + 1) / gridDim.x;
   const int nit = (int)(i1 - i0);
   const int FB = a.flush;
+  const int nkb = (int)a.nkb, nblk = (int)a.nblk;
 
   if (tid == 0) {
     for (int i = 0; i < a.nst; ++i) {
@@ -152,16 +172,16 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
     prefetch_tmap(&map_hi);
     if (X3) prefetch_tmap(&map_lo);
     int issued = 0;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.nkb, kp = item - f * a.nkb;
-      const int s = i % a.nst, u = i / a.nst;
-      if (u >= 1 && !mbar_wait(smem_u32(&hdr->empty[s]), (u - 1) & 1, abort_flag, gflags)) break;
+    Cursor cu;
+    cu.init(i0, nkb);
+    for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
+      const int s = cu.s;
+      if (i >= a.nst && !mbar_wait(smem_u32(&hdr->empty[s]), cu.ph ^ 1, abort_flag, gflags)) break;
       const uint32_t fb = smem_u32(&hdr->full[s]);
       mbar_arrive_expect_tx(fb, stage_bytes);
       uint8_t* st = stages + (size_t)s * stage_bytes;
-      tma_load_4d(smem_u32(st), &map_hi, 0, 0, (int)f, (int)(kp * kKpb), fb);
-      if (X3) tma_load_4d(smem_u32(st + op_bytes), &map_lo, 0, 0, (int)f, (int)(kp * kKpb), fb);
+      tma_load_4d(smem_u32(st), &map_hi, 0, 0, cu.f, cu.kp * kKpb, fb);
+      if (X3) tma_load_4d(smem_u32(st + op_bytes), &map_lo, 0, 0, cu.f, cu.kp * kKpb, fb);
       issued = i + 1;
     }
     // copies still in flight must land before the CTA can exit
@@ -171,21 +191,21 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(128, a.np, 0, 0);
     GroupWalk gw;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.nkb, kp = item - f * a.nkb;
+    Cursor cu;
+    cu.init(i0, nkb);
+    for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
+      const int f = cu.f, kp = cu.kp;
       const bool gstart = gw.step(f, FB);
       const bool sstart = gw.sstart;
       const int g = gw.g, acc = g & 1, sg = gw.seg, a2b = sg & 1;
-      const int64_t fn = (i + 1 < nit) ? (item + 1) / a.nkb : -1;
-      const bool gend = i + 1 == nit || fn != f || gw.in_group == FB;
+      const bool gend = i + 1 == nit || cu.last_of_f(nkb) || gw.in_group == FB;
       if (gstart && g >= 2 && !mbar_wait(smem_u32(&hdr->accempty[acc]), ((g >> 1) - 1) & 1, abort_flag, gflags))
         break;
       if (X3 && sstart && sg >= 2 &&
           !mbar_wait(smem_u32(&hdr->a2empty[a2b]), ((sg >> 1) - 1) & 1, abort_flag, gflags))
         break;
-      const int s = i % a.nst, u = i / a.nst;
-      if (!mbar_wait(smem_u32(&hdr->full[s]), u & 1, abort_flag, gflags)) break;
+      const int s = cu.s;
+      if (!mbar_wait(smem_u32(&hdr->full[s]), cu.ph, abort_flag, gflags)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(stages + (size_t)s * stage_bytes);
       const uint32_t d1 = tmem + (uint32_t)acc * 128u;
@@ -193,7 +213,7 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
 #pragma unroll
       for (int j = 0; j < kKpb; ++j) {
         // a block past the chunk's points (odd block count) holds no data of this chunk
-        if (kp * kKpb + j >= a.nblk) break;
+        if (kp * kKpb + j >= nblk) break;
         const uint32_t hi = st + (uint32_t)j * a.box_bytes;
         const uint32_t lo = hi + op_bytes;
 #pragma unroll
@@ -224,14 +244,14 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
     float q[kRowsPer];
 #pragma unroll
     for (int j = 0; j < kRowsPer; ++j) q[j] = 0.f;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.nkb, kp = item - f * a.nkb;
-      const int64_t fn = (i + 1 < nit) ? (item + 1) / a.nkb : -1;
-      const bool send = i + 1 == nit || fn != f;
-      const int s = i % a.nst, u = i / a.nst;
-      if (!mbar_wait(smem_u32(&hdr->full[s]), u & 1, abort_flag, gflags)) break;
-      const int nvalid = (int)min((int64_t)kKpb, a.nblk - kp * kKpb);
+    Cursor cu;
+    cu.init(i0, nkb);
+    for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
+      const int f = cu.f, kp = cu.kp;
+      const bool send = i + 1 == nit || cu.last_of_f(nkb);
+      const int s = cu.s;
+      if (!mbar_wait(smem_u32(&hdr->full[s]), cu.ph, abort_flag, gflags)) break;
+      const int nvalid = min(kKpb, nblk - kp * kKpb);
       for (int b = 0; b < nvalid; ++b) {
         const uint8_t* lo = stages + (size_t)s * stage_bytes + op_bytes + (size_t)b * a.box_bytes;
 #pragma unroll
@@ -278,12 +298,12 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
 #pragma unroll
     for (int j = 0; j < HC; ++j) { s1[j] = 0.f; c1[j] = 0.f; }
     GroupWalk gw;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.nkb;
+    Cursor cu;
+    cu.init(i0, nkb);
+    for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
+      const int f = cu.f;
       gw.step(f, FB);
-      const int64_t fn = (i + 1 < nit) ? (item + 1) / a.nkb : -1;
-      const bool send = i + 1 == nit || fn != f;
+      const bool send = i + 1 == nit || cu.last_of_f(nkb);
       const bool gend = send || gw.in_group == FB;
       if (!gend) continue;
       const int g = gw.g, acc = g & 1, a2b = gw.seg & 1;

@@ -103,6 +103,24 @@ __global__ void k_mode_image(const float* __restrict__ bmat, int nb, int nm, int
   }
 }
 
+// Position of a CTA's item in the (frequency, tile) list and in the stage
+// ring, advanced without divisions (the issuing threads are on the critical
+// path of every item).
+struct Cursor {
+  int f, tp;          // frequency, 128-point tile within it
+  int s, ph;          // stage, parity of the ring pass (i / nst) & 1
+  __device__ __forceinline__ void init(int64_t item0, int ntp) {
+    f = (int)(item0 / ntp);
+    tp = (int)(item0 - (int64_t)f * ntp);
+    s = 0;
+    ph = 0;
+  }
+  __device__ __forceinline__ void next(int ntp, int nst) {
+    if (++tp == ntp) { tp = 0; ++f; }
+    if (++s == nst) { s = 0; ph ^= 1; }
+  }
+};
+
 template <bool X3>
 __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_constant__ CUtensorMap map_hi,
                                                     const __grid_constant__ CUtensorMap map_lo, ModesTcArgs a,
@@ -122,6 +140,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
   const int64_t i0 = a.nitems * blockIdx.x / gridDim.x;
   const int64_t i1 = a.nitems * (blockIdx.x + 1) / gridDim.x;
   const int nit = (int)(i1 - i0);
+  const int ntp = (int)a.ntp;
 
   if (tid == 0) {
     for (int i = 0; i < a.nst; ++i) {
@@ -153,10 +172,11 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     prefetch_tmap(&map_hi);
     if (X3) prefetch_tmap(&map_lo);
     int issued = 0, seg = 0, segs_loaded = 0;
-    int64_t fcur = -1;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.ntp, tp = item - f * a.ntp;
+    int fcur = -1;
+    Cursor cu;
+    cu.init(i0, ntp);
+    for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
+      const int f = cu.f, tp = cu.tp;
       if (f != fcur) {
         // the MMAs of the previous frequency must be done with B before it is replaced
         if (seg >= 1 && !mbar_wait(smem_u32(&hdr->bempty), (seg - 1) & 1, abort_flag, gflags)) break;
@@ -169,18 +189,15 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
         fcur = f;
         ++seg;
       }
-      const int s = i % a.nst, u = i / a.nst;
-      if (u >= 1 && !mbar_wait(smem_u32(&hdr->empty[s]), (u - 1) & 1, abort_flag, gflags)) break;
+      const int s = cu.s;
+      if (i >= a.nst && !mbar_wait(smem_u32(&hdr->empty[s]), cu.ph ^ 1, abort_flag, gflags)) break;
       const uint32_t fb = smem_u32(&hdr->full[s]);
       mbar_arrive_expect_tx(fb, stage_bytes);
       uint8_t* st = stages + (size_t)s * stage_bytes;
-      const int kb = (int)(2 * tp);
-      tma_load_4d(smem_u32(st), &map_hi, 0, 0, (int)f, kb, fb);
-      tma_load_4d(smem_u32(st + a.box_bytes), &map_hi, 0, 0, (int)f, kb + 1, fb);
-      if (X3) {
-        tma_load_4d(smem_u32(st + 2 * a.box_bytes), &map_lo, 0, 0, (int)f, kb, fb);
-        tma_load_4d(smem_u32(st + 3 * a.box_bytes), &map_lo, 0, 0, (int)f, kb + 1, fb);
-      }
+      const int kb = 2 * tp;
+      // one copy per operand: the tile's two 64-point blocks side by side
+      tma_load_4d(smem_u32(st), &map_hi, 0, 0, f, kb, fb);
+      if (X3) tma_load_4d(smem_u32(st + 2 * a.box_bytes), &map_lo, 0, 0, f, kb, fb);
       issued = i + 1;
     }
     // copies still in flight must land before the CTA can exit
@@ -194,10 +211,11 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     const uint32_t katom_bytes = (uint32_t)a.nn * 128u;
     const int nk16 = a.np / 16;
     int seg = 0;
-    int64_t fcur = -1;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.ntp;
+    int fcur = -1;
+    Cursor cu;
+    cu.init(i0, ntp);
+    for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
+      const int f = cu.f;
       if (f != fcur) {
         if (seg >= 1) mma_commit(smem_u32(&hdr->bempty));   // B of the previous frequency is released
         if (!mbar_wait(smem_u32(&hdr->bfull), seg & 1, abort_flag, gflags)) break;
@@ -206,8 +224,8 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
       }
       const int acc = i & 1;
       if (i >= 2 && !mbar_wait(smem_u32(&hdr->accempty[acc]), ((i >> 1) - 1) & 1, abort_flag, gflags)) break;
-      const int s = i % a.nst, u = i / a.nst;
-      if (!mbar_wait(smem_u32(&hdr->full[s]), u & 1, abort_flag, gflags)) break;
+      const int s = cu.s;
+      if (!mbar_wait(smem_u32(&hdr->full[s]), cu.ph, abort_flag, gflags)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(stages + (size_t)s * stage_bytes);
       const uint32_t d = tmem + (uint32_t)acc * 128u;
@@ -236,9 +254,10 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     const int hcols = a.nn / 2;                     // columns of this warp: [half * hcols, +hcols)
     const int k0 = half * (hcols / 2);              // first mode of this warp
     const int nm = a.nmodes;
-    for (int i = 0; i < nit; ++i) {
-      const int64_t item = i0 + i;
-      const int64_t f = item / a.ntp, tp = item - f * a.ntp;
+    Cursor cu;
+    cu.init(i0, ntp);
+    for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
+      const int f = cu.f, tp = cu.tp;
       const int acc = i & 1;
       if (!mbar_wait(smem_u32(&hdr->accfull[acc]), (i >> 1) & 1, abort_flag, gflags)) break;
       tc_fence_after();
@@ -329,13 +348,13 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
   if (p.desc.precision == SPOD_PREC_BF16X3) {
     cudaError_t e = cudaFuncSetAttribute(k_modes_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_modes_tc<true><<<(unsigned)grid, kThreadsModes, smem, s>>>(p.tmap_hi, p.tmap_lo, a,
+    k_modes_tc<true><<<(unsigned)grid, kThreadsModes, smem, s>>>(p.tmap_hi2, p.tmap_lo2, a,
                                                                  static_cast<const uint8_t*>(p.d_bimg), scale,
                                                                  static_cast<float2*>(d_Phi), p.d_flags);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_modes_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_modes_tc<false><<<(unsigned)grid, kThreadsModes, smem, s>>>(p.tmap_hi, p.tmap_hi, a,
+    k_modes_tc<false><<<(unsigned)grid, kThreadsModes, smem, s>>>(p.tmap_hi2, p.tmap_hi2, a,
                                                                   static_cast<const uint8_t*>(p.d_bimg), scale,
                                                                   static_cast<float2*>(d_Phi), p.d_flags);
   }
