@@ -117,13 +117,20 @@ __device__ __forceinline__ void pass_oop(const float2* __restrict__ src, float2*
       for (int r = 0; r < RAD; ++r) v[i][r] = src[(b + r * nbut) * PC + col];
     }
   }
+  // when PBSTEP is a multiple of NS all of this thread's butterflies share k
+  float2 tk[RAD];
+  if constexpr (PBSTEP % NS == 0) {
+    const int k = b0 % NS;
+#pragma unroll
+    for (int r = 1; r < RAD; ++r) tk[r] = tw[r * k * stw];
+  }
 #pragma unroll
   for (int i = 0; i < MAXB; ++i) {
     const int b = b0 + i * PBSTEP;
     if (nbut % PBSTEP == 0 || b < nbut) {
       const int k = b % NS, g = b / NS;
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) v[i][r] = cmul(v[i][r], tw[r * k * stw]);
+      for (int r = 1; r < RAD; ++r) v[i][r] = cmul(v[i][r], (PBSTEP % NS == 0) ? tk[r] : tw[r * k * stw]);
       dft_small<RAD, float2, float>(v[i]);
       const int base = g * NS * RAD + k;
 #pragma unroll
@@ -173,42 +180,61 @@ template <> struct PSeq<720> {
 };
 
 // Separate the two real spectra of each column (even point: (Z[f] + conj
-// Z[N-f]) / 2, odd point: (Z[f] - conj Z[N-f]) / 2i), fold sqrt(W) (sa, sb
-// carry the 1/2) and store rows re = l and im = nb + l of every frequency.
+// Z[N-f]) / 2, odd point: (Z[f] - conj Z[N-f]) / 2i), fold sqrt(W) (sw carries
+// the 1/2) and store rows re = l and im = nb + l of every frequency.  A thread
+// takes two adjacent columns (four points): 16-byte shared loads, and one
+// 16-byte (FP32) or 8-byte (BF16) store per output plane and frequency.
+constexpr int kOutCp = PC / 2;                 // column pairs per tile
+constexpr int kOutFStep = PTHREADS / kOutCp;   // frequencies between a thread's consecutive ones
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float bf16_lo_f(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
 template <int OUTK, int N>
 __device__ __forceinline__ void output_phase(const float2* __restrict__ src, const PipeArgs& a, int l,
-                                             int64_t lm0, float sa, float sb, void* __restrict__ qout,
+                                             int64_t lm0, const float (&sw)[4], void* __restrict__ qout,
                                              void* __restrict__ qlo) {
-  const int col = threadIdx.x % PC;
-  const int f0 = threadIdx.x / PC;
+  const int cp = threadIdx.x % kOutCp;
+  const int f0 = threadIdx.x / kOutCp;
   // FP32 planes are planar [nf][2 nb][chunk]; BF16 planes are blocked by 64
   // points, [chunk / 64][nf][2 nb][64] (see qhat_blocked_offset)
   constexpr bool BLK = OUTK != OUT_NATIVE;
   const int64_t rs = BLK ? (int64_t)kQBlock : a.chunk;           // row stride
   const int64_t rowstride = (int64_t)2 * a.nb * rs;              // one frequency
   const int64_t imoff = (int64_t)a.nb * rs;
-  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lm0 + 2 * col)
-                  : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lm0 + 2 * col;
-  for (int f = f0; f < a.nf; f += PBSTEP, o += PBSTEP * rowstride) {
-    const float2 zf = src[f * PC + col];
-    const float2 zc = src[((f == 0) ? 0 : N - f) * PC + col];
-    const float ra = (zf.x + zc.x) * sa, ia = (zf.y - zc.y) * sa;
-    const float rb = (zf.y + zc.y) * sb, ib = (zc.x - zf.x) * sb;
+  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lm0 + 4 * cp)
+                  : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lm0 + 4 * cp;
+  const float4* src4 = reinterpret_cast<const float4*>(src);
+  for (int f = f0; f < a.nf; f += kOutFStep, o += kOutFStep * rowstride) {
+    const float4 zf = src4[f * kOutCp + cp];                        // columns 2cp, 2cp+1 at bin f
+    const float4 zc = src4[((f == 0) ? 0 : N - f) * kOutCp + cp];   // ... at bin N-f
+    // points 4cp, 4cp+1 (column 2cp) and 4cp+2, 4cp+3 (column 2cp+1)
+    const float r0 = (zf.x + zc.x) * sw[0], i0 = (zf.y - zc.y) * sw[0];
+    const float r1 = (zf.y + zc.y) * sw[1], i1 = (zc.x - zf.x) * sw[1];
+    const float r2 = (zf.z + zc.z) * sw[2], i2 = (zf.w - zc.w) * sw[2];
+    const float r3 = (zf.w + zc.w) * sw[3], i3 = (zc.z - zf.z) * sw[3];
     if constexpr (OUTK == OUT_NATIVE) {
       float* q = static_cast<float*>(qout);
-      *reinterpret_cast<float2*>(q + o) = make_float2(ra, rb);
-      *reinterpret_cast<float2*>(q + o + imoff) = make_float2(ia, ib);
+      *reinterpret_cast<float4*>(q + o) = make_float4(r0, r1, r2, r3);
+      *reinterpret_cast<float4*>(q + o + imoff) = make_float4(i0, i1, i2, i3);
     } else {
       __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
-      const __nv_bfloat162 hr = __floats2bfloat162_rn(ra, rb);
-      const __nv_bfloat162 hi = __floats2bfloat162_rn(ia, ib);
-      *reinterpret_cast<__nv_bfloat162*>(qh + o) = hr;
-      *reinterpret_cast<__nv_bfloat162*>(qh + o + imoff) = hi;
+      const uint32_t hr01 = pack_bf16x2(r0, r1), hr23 = pack_bf16x2(r2, r3);
+      const uint32_t hi01 = pack_bf16x2(i0, i1), hi23 = pack_bf16x2(i2, i3);
+      *reinterpret_cast<uint2*>(qh + o) = make_uint2(hr01, hr23);
+      *reinterpret_cast<uint2*>(qh + o + imoff) = make_uint2(hi01, hi23);
       if constexpr (OUTK == OUT_BF16X3) {
         __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qlo);
-        const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi);
-        *reinterpret_cast<__nv_bfloat162*>(ql + o) = __floats2bfloat162_rn(ra - fr.x, rb - fr.y);
-        *reinterpret_cast<__nv_bfloat162*>(ql + o + imoff) = __floats2bfloat162_rn(ia - fi.x, ib - fi.y);
+        const uint32_t lr01 = pack_bf16x2(r0 - bf16_lo_f(hr01), r1 - bf16_hi_f(hr01));
+        const uint32_t lr23 = pack_bf16x2(r2 - bf16_lo_f(hr23), r3 - bf16_hi_f(hr23));
+        const uint32_t li01 = pack_bf16x2(i0 - bf16_lo_f(hi01), i1 - bf16_hi_f(hi01));
+        const uint32_t li23 = pack_bf16x2(i2 - bf16_lo_f(hi23), i3 - bf16_hi_f(hi23));
+        *reinterpret_cast<uint2*>(ql + o) = make_uint2(lr01, lr23);
+        *reinterpret_cast<uint2*>(ql + o + imoff) = make_uint2(li01, li23);
       }
     }
   }
@@ -288,19 +314,20 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
   for (int64_t t = t_first; t < a.ntiles; t += t_step) {
     const int64_t lm0 = t * PTP;
     const int64_t gm0 = a.m0 + lm0;
-    float mhi0 = 0.f, mlo0 = 0.f, mhi1 = 0.f, mlo1 = 0.f, sa = 0.f, sb = 0.f;
+    float mhi0 = 0.f, mlo0 = 0.f, mhi1 = 0.f, mlo1 = 0.f;
+    float sw[4];                     // 0.5 sqrt(W) of the output phase's four points (zero past mcount)
     {
       const int64_t lm = lm0 + 2 * col;
-      if (lm < a.mcount) {
-        sa = 0.5f * sqrtW[gm0 + 2 * col];
-        if (a.subtract_mean) { const double d = mu[gm0 + 2 * col]; mhi0 = (float)d; mlo0 = (float)(d - (double)mhi0); }
+      if (a.subtract_mean && lm < a.mcount) {
+        const double d = mu[gm0 + 2 * col]; mhi0 = (float)d; mlo0 = (float)(d - (double)mhi0);
       }
-      if (lm + 1 < a.mcount) {
-        sb = 0.5f * sqrtW[gm0 + 2 * col + 1];
-        if (a.subtract_mean) {
-          const double d = mu[gm0 + 2 * col + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
-        }
+      if (a.subtract_mean && lm + 1 < a.mcount) {
+        const double d = mu[gm0 + 2 * col + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
       }
+      const int cp = tid % kOutCp;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        sw[q] = (lm0 + 4 * cp + q < a.mcount) ? 0.5f * sqrtW[gm0 + 4 * cp + q] : 0.f;
     }
     int rb = 0;                      // ring slot of the block's first row
     for (int l = 0; l < a.nb; ++l) {
@@ -320,7 +347,7 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
         }
       }
       const float2* spec = S::rest(bA, bB, tw);
-      output_phase<OUTK, N>(spec, a, l, lm0, sa, sb, qout, qlo);
+      output_phase<OUTK, N>(spec, a, l, lm0, sw, qout, qlo);
       rb += a.step;
       if (rb >= N) rb -= N;
       par ^= (S::P & 1);
