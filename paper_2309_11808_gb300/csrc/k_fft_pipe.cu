@@ -209,7 +209,13 @@ __device__ __forceinline__ void output_phase(const float2* __restrict__ src, con
   int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lm0 + 4 * cp)
                   : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lm0 + 4 * cp;
   const float4* src4 = reinterpret_cast<const float4*>(src);
-  for (int f = f0; f < a.nf; f += kOutFStep, o += kOutFStep * rowstride) {
+  // compile-time trip count (nf = N/2 + 1): the iterations' loads overlap
+  constexpr int kIters = (N / 2 + 1 + kOutFStep - 1) / kOutFStep;
+#pragma unroll
+  for (int it = 0; it < kIters; ++it) {
+    const int f = f0 + it * kOutFStep;
+    if (f >= a.nf) break;
+    if (it > 0) o += kOutFStep * rowstride;
     const float4 zf = src4[f * kOutCp + cp];                        // columns 2cp, 2cp+1 at bin f
     const float4 zc = src4[((f == 0) ? 0 : N - f) * kOutCp + cp];   // ... at bin N-f
     // points 4cp, 4cp+1 (column 2cp) and 4cp+2, 4cp+3 (column 2cp+1)
