@@ -237,6 +237,17 @@ DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "bf16x3": "bf16x3"}
 FP32_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
 
 
+def max_over_ranks(x: float, dev) -> float:
+    """The slowest rank's value (the job's time) when running under torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_plan(precision, wl):
     import torch
     from paper_2309_11808_gb300 import SPOD
@@ -285,10 +296,7 @@ def timed_run(precision, wl, steps, warmup, world, dev, clocks):
     phase_ms, phase_launch = _lib.spod_profile_read(sp.handle)
     _lib.spod_profile_enable(sp.handle, False)
     _lib.spod_sync(sp.handle, stream)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
     del Phi
     return {"sp": sp, "nb": nb, "nf": nf, "nmodes": nmodes, "ms_step": ms_total / steps, "phase_ms": phase_ms,
             "phase_launch": phase_launch, "clocks": clk}
