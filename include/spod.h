@@ -194,7 +194,13 @@ spod_status spod_run_host(spod_plan_t plan, const void* h_X, int nmodes, void* h
 spod_status spod_sync(spod_plan_t plan, void* stream);
 
 /* Fit n plans on n inputs with one CUDA-graph launch (datasets of different
- * grid size, nt and nfft).  Equivalent to n spod_fit calls.  */
+ * grid size, nt and nfft; Sec. 4.2 analyses several reanalysis records).
+ * The results equal n spod_fit calls.  The first call captures the n fits
+ * into a graph with one branch per dataset (independent datasets run
+ * concurrently); later calls with the same plans, inputs and launch
+ * parameters relaunch the cached graph.  All plans must be on one device and
+ * distinct.  Asynchronous on `stream` like spod_fit; errors of the capture
+ * are returned, device-side conditions by the next spod_sync of each plan. */
 spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream);
 
 /* Launch-shape knobs (the autotuner's interface).  They change how work is
@@ -212,6 +218,15 @@ typedef struct {
 spod_status spod_plan_get_tuning(spod_plan_t plan, spod_tuning* tuning);
 /* SPOD_EINVAL for values outside the stated ranges; takes effect from the next fit/modes call. */
 spod_status spod_plan_set_tuning(spod_plan_t plan, const spod_tuning* tuning);
+
+/* Autotuner: runs spod_fit on d_X (device, as spod_fit) under candidate
+ * launch shapes (the Gram's CTA split: persistent CTAs per GPU for the
+ * tensor-core path, CTAs per frequency for the SIMT path), times each with
+ * CUDA events on `stream` and keeps the fastest; gram_flush_blocks, which
+ * changes rounding, is not searched.  Synchronises the stream; the plan holds
+ * the last fit's results afterwards.  chosen (may be NULL) receives the
+ * tuning kept.  No counterpart in the paper (an engineering aid). */
+spod_status spod_plan_autotune(spod_plan_t plan, const void* d_X, void* stream, spod_tuning* chosen);
 
 /* Phases of the hot path, for per-phase timing. */
 typedef enum {

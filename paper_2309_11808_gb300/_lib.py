@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "SPOD_OK", 1: "SPOD_EINVAL", 2: "SPOD_ENOMEM", 3: "SPOD_ECUDA
 EXPORTED = ["spod_desc_init", "spod_plan_create", "spod_plan_destroy", "spod_plan_get_info", "spod_fit",
             "spod_get_eigs", "spod_get_gram", "spod_get_freqs", "spod_modes", "spod_backward",
             "spod_run_host", "spod_sync", "spod_fit_batch", "spod_profile_enable", "spod_profile_read",
-            "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning",
+            "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning", "spod_plan_autotune",
             "spod_last_error", "spod_version"]
 
 PHASES = ["mean", "fft", "gram", "reduce", "eig", "modes", "backward"]
@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
         L.spod_eigh_batched_noalloc.argtypes = [P, C.c_int, C.c_int, P, P, P]
         L.spod_plan_get_tuning.argtypes = [P, C.POINTER(spod_tuning)]
         L.spod_plan_set_tuning.argtypes = [P, C.POINTER(spod_tuning)]
+        L.spod_plan_autotune.argtypes = [P, P, P, C.POINTER(spod_tuning)]
         L.spod_last_error.restype = C.c_char_p
         L.spod_version.restype = C.c_char_p
         for name in EXPORTED[:-2]:
@@ -210,6 +211,12 @@ def spod_plan_get_tuning(plan: int) -> spod_tuning:
 def spod_plan_set_tuning(plan: int, gram_splits: int = 0, gram_flush_blocks: int = 0, modes_ctas: int = 0) -> None:
     t = spod_tuning(int(gram_splits), 0, int(gram_flush_blocks), int(modes_ctas))
     check(lib().spod_plan_set_tuning(plan, C.byref(t)), "spod_plan_set_tuning")
+
+
+def spod_plan_autotune(plan: int, X, stream=None) -> spod_tuning:
+    t = spod_tuning()
+    check(lib().spod_plan_autotune(plan, _ptr(X), _stream(stream), C.byref(t)), "spod_plan_autotune")
+    return t
 
 
 def spod_last_error() -> str:

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -244,6 +246,8 @@ spod_status spod_desc_init(spod_plan_desc* d) {
   return SPOD_OK;
 }
 
+static std::atomic<uint64_t> g_plan_uid{0};
+
 spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   if (!out) return fail(SPOD_EINVAL, "out is NULL");
   *out = nullptr;
@@ -272,6 +276,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   spod_plan_s* p = new (std::nothrow) spod_plan_s();
   if (!p) return fail(SPOD_ENOMEM, "host allocation failed");
   p->desc = *d;
+  p->uid = ++g_plan_uid;
   p->desc.user_window = nullptr;
   p->desc.weights = nullptr;
   p->npoints = npoints;
@@ -785,6 +790,7 @@ spod_status spod_plan_set_tuning(spod_plan_t p, const spod_tuning* t) {
   if (t->gram_splits) p->gram_splits = t->gram_splits;
   if (t->gram_flush_blocks) p->gram_flush = t->gram_flush_blocks;
   p->modes_ctas = t->modes_ctas;
+  ++p->version;
   return SPOD_OK;
 }
 
@@ -817,10 +823,158 @@ spod_status spod_profile_read(spod_plan_t p, double* ms, int64_t* launches) {
   return st;
 }
 
+// ---- spod_fit_batch: the n fits captured once into a CUDA graph with one
+// branch per dataset (independent plans run concurrently and fill the GPU
+// when a dataset alone would not), then relaunched while the plans, their
+// launch parameters and the inputs stay the same.
+namespace {
+struct BatchGraph {
+  int device = -1;
+  std::vector<uint64_t> key;                 // (uid, version, X) per plan
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t origin = nullptr;             // capture stream
+  std::vector<cudaStream_t> side;            // one branch per dataset
+  std::vector<cudaEvent_t> ev;               // fork + joins
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch;             // one cached graph per device
+
+spod_status batch_resources(BatchGraph& bg, int n) {
+  if (!bg.origin) SPOD_CUDA(cudaStreamCreateWithFlags(&bg.origin, cudaStreamNonBlocking), "batch stream");
+  while ((int)bg.side.size() < n) {
+    cudaStream_t st;
+    SPOD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch stream");
+    bg.side.push_back(st);
+  }
+  while ((int)bg.ev.size() < n + 1) {
+    cudaEvent_t e;
+    SPOD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batch event");
+    bg.ev.push_back(e);
+  }
+  return SPOD_OK;
+}
+}  // namespace
+
 spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream) {
   if (!plans || !d_X || n < 0) return fail(SPOD_EINVAL, "bad batch arguments");
-  for (int i = 0; i < n; ++i)
-    if (spod_status st = spod_fit(plans[i], d_X[i], stream)) return st;
+  if (n == 0) return SPOD_OK;
+  std::vector<uint64_t> key;
+  for (int i = 0; i < n; ++i) {
+    if (spod_status st = check_plan(plans[i])) return st;
+    if (spod_status st = check_ptr(d_X[i], "d_X[i]")) return st;
+    if (plans[i]->device != plans[0]->device) return fail(SPOD_EINVAL, "batch plans must share one device");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(SPOD_EINVAL, "a plan appears twice in the batch");
+    key.push_back(plans[i]->uid);
+    key.push_back(plans[i]->version);
+    key.push_back((uint64_t)reinterpret_cast<uintptr_t>(d_X[i]));
+  }
+  DeviceGuard g(plans[0]->device);
+  if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plans' device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchGraph* bgp = nullptr;
+  for (auto& b : g_batch)
+    if (b.device == plans[0]->device) bgp = &b;
+  if (!bgp) {
+    g_batch.emplace_back();
+    bgp = &g_batch.back();
+    bgp->device = plans[0]->device;
+  }
+  BatchGraph& bg = *bgp;
+  if (!(bg.exec && bg.key == key)) {
+    if (spod_status st = batch_resources(bg, n)) return st;
+    if (bg.exec) { cudaGraphExecDestroy(bg.exec); bg.exec = nullptr; }
+    bg.key.clear();
+    // the work must be in stream order after anything already queued on `stream`
+    // only at launch; capture happens on a private stream
+    SPOD_CUDA(cudaStreamBeginCapture(bg.origin, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+    spod_status st = SPOD_OK;
+    std::string msg;
+    std::vector<int> prof(n);
+    if (cudaEventRecord(bg.ev[0], bg.origin) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "fork event");
+    for (int i = 0; i < n && st == SPOD_OK; ++i) {
+      prof[i] = plans[i]->prof;
+      plans[i]->prof = 0;                    // phase events stay outside the graph
+      if (cudaStreamWaitEvent(bg.side[i], bg.ev[0], 0) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError(), "fork");
+      } else {
+        st = spod_fit(plans[i], d_X[i], bg.side[i]);
+        if (st == SPOD_OK && (cudaEventRecord(bg.ev[i + 1], bg.side[i]) != cudaSuccess ||
+                              cudaStreamWaitEvent(bg.origin, bg.ev[i + 1], 0) != cudaSuccess))
+          st = cuda_fail(cudaGetLastError(), "join");
+      }
+      plans[i]->prof = prof[i];
+    }
+    if (st != SPOD_OK) msg = spod_last_error();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(bg.origin, &graph);
+    if (st != SPOD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(st, "batch capture: " + msg);
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "end graph capture");
+    const cudaError_t ei = cudaGraphInstantiate(&bg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) { bg.exec = nullptr; return cuda_fail(ei, "instantiate graph"); }
+    bg.key = key;
+  }
+  SPOD_CUDA(cudaGraphLaunch(bg.exec, s), "graph launch");
+  for (int i = 0; i < n; ++i) plans[i]->last_stream = s;
+  return SPOD_OK;
+}
+
+// ---- spod_plan_autotune: time spod_fit under candidate launch shapes on
+// the caller's input and keep the fastest.  Only how work is split across
+// CTAs is searched; the FP32 accumulation interval (gram_flush_blocks),
+// which changes rounding, is left as it is.
+spod_status spod_plan_autotune(spod_plan_t p, const void* d_X, void* stream, spod_tuning* chosen) {
+  if (spod_status st = check_plan(p)) return st;
+  if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int sms = p->num_sms > 0 ? p->num_sms : 148;
+  std::vector<int> cand;
+  if (p->tensor) {
+    for (int c : {sms, sms / 2, sms + sms / 2, 2 * sms})
+      if (c >= 1 && c <= p->gram_splits_max) cand.push_back(c);
+  } else {
+    const int d = p->gram_splits;
+    for (int c : {d, d / 2, d * 2, d * 4, (d * 3) / 2})
+      if (c >= 1 && c <= p->gram_splits_max) cand.push_back(c);
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  const int keep_splits = p->gram_splits;
+  const int prof = p->prof;
+  p->prof = 0;
+  cudaEvent_t e0, e1;
+  SPOD_CUDA(cudaEventCreate(&e0), "event");
+  SPOD_CUDA(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  int best_c = keep_splits;
+  spod_status st = SPOD_OK;
+  for (int c : cand) {
+    p->gram_splits = c;
+    st = spod_fit(p, d_X, stream);                       // warm-up
+    if (st != SPOD_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && st == SPOD_OK; ++r) st = spod_fit(p, d_X, stream);
+    cudaEventRecord(e1, s);
+    if (st != SPOD_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune timing"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_c = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->gram_splits = st == SPOD_OK ? best_c : keep_splits;
+  p->prof = prof;
+  ++p->version;
+  if (st != SPOD_OK) return st;
+  if (chosen) spod_plan_get_tuning(p, chosen);
   return SPOD_OK;
 }
 

@@ -54,6 +54,8 @@ struct Workspace {
 }  // namespace spod
 
 struct spod_plan_s {
+  uint64_t uid = 0;        // unique per plan (never reused): keys cached CUDA graphs
+  uint64_t version = 0;    // bumped when launch parameters change (tuning, profiling)
   spod_plan_desc desc{};
   int64_t npoints = 0, M = 0, Mpad = 0, nt = 0;
   int nvars = 0, nfft = 0, noverlap = 0, step = 0, nb = 0, nf = 0;

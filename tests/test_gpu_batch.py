@@ -1,0 +1,102 @@
+"""Batched fits of several datasets of uneven grid size, nt and nfft in one
+CUDA-graph launch (spod_fit_batch), and the launch-shape autotuner.
+
+The datasets follow the ERA5-shaped recipe (lat-lon grids, two variables,
+cos(latitude) weights, AR(1) red noise plus planted annual and diurnal-bin
+patterns) on small grids, with the nfft set of the six one-year records
+(256, 384, 512, 720).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import geo_like
+
+pytestmark = pytest.mark.gpu
+
+cuda = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")
+
+# (nlat, nlon, nt, nfft): uneven grids (ragged point counts), nt and nfft per dataset
+SETS = [(19, 36, 1460, 256), (37, 72, 2190, 384), (23, 40, 2920, 512), (31, 44, 2190, 720),
+        (29, 50, 1460, 256), (17, 30, 4380, 720)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _make(prec):
+    from paper_2309_11808_gb300 import SPOD
+    wls, sps = [], []
+    for i, (nla, nlo, nt, nfft) in enumerate(SETS):
+        wl = geo_like(nla, nlo, nt, nfft, seed=40 + i, dtype=torch.float32, device="cuda:0")
+        wls.append(wl)
+        sps.append(SPOD(wl.npoints, wl.nvars, nt, nfft, nfft // 2, precision=prec, weights=wl.W))
+    return wls, sps
+
+
+@cuda
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_batch_graph_equals_individual_fits(prec):
+    from paper_2309_11808_gb300 import _lib
+    wls, sps = _make(prec)
+    ref = []
+    for wl, sp in zip(wls, sps):
+        sp.fit(wl.X)
+        ref.append(sp.eigs())
+    torch.cuda.synchronize()
+    handles = [sp.handle for sp in sps]
+    for rep in range(2):                           # capture, then relaunch of the cached graph
+        _lib.spod_fit_batch(handles, [wl.X for wl in wls], torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for sp, r in zip(sps, ref):
+            assert np.array_equal(sp.eigs(), r)
+    # a new input for one dataset: the graph is captured again
+    X2 = wls[2].X * 1.5
+    _lib.spod_fit_batch(handles, [wl.X for wl in wls[:2]] + [X2] + [wl.X for wl in wls[3:]],
+                        torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    l2, r2 = sps[2].eigs(), 2.25 * ref[2]
+    assert (np.abs(l2 - r2).max(axis=1) / r2[:, 0]).max() <= 1e-5   # the split rounds 1.5 X anew
+    assert np.array_equal(sps[1].eigs(), ref[1])
+    # one dataset against the FP64 oracle
+    wl, (nla, nlo, nt, nfft) = wls[3], SETS[3]
+    d = O.Desc(nt=nt, M=wl.X.shape[1], nfft=nfft, noverlap=nfft // 2, window=O.WIN_HAMMING,
+               weights=wl.W.numpy().astype(np.float64))
+    fit = O.spod_fit(wl.X.double().cpu().numpy(), d, dft="fft")
+    lam = sps[3].eigs()
+    normwise = (np.abs(lam - fit.lam).max(axis=1) / fit.lam[:, 0]).max()
+    assert normwise <= (1e-5 if prec == "bf16x3" else 1e-6)
+    for sp in sps:
+        sp.close()
+
+
+@cuda
+def test_batch_rejects_duplicates():
+    from paper_2309_11808_gb300 import _lib, SpodError
+    wls, sps = _make("fp32")
+    with pytest.raises(SpodError):
+        _lib.spod_fit_batch([sps[0].handle, sps[0].handle], [wls[0].X, wls[0].X], torch.cuda.current_stream())
+    for sp in sps:
+        sp.close()
+
+
+@cuda
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_autotune_keeps_results(prec):
+    from paper_2309_11808_gb300 import _lib
+    wls, sps = _make(prec)
+    wl, sp = wls[1], sps[1]
+    sp.fit(wl.X)
+    lam0 = sp.eigs()
+    t = _lib.spod_plan_autotune(sp.handle, wl.X, torch.cuda.current_stream())
+    assert 1 <= t.gram_splits <= t.gram_splits_max
+    sp.fit(wl.X)
+    lam1 = sp.eigs()
+    # only the grouping of partial sums may change
+    assert (np.abs(lam1 - lam0).max(axis=1) / lam0[:, 0]).max() <= 1e-6
+    for s in sps:
+        s.close()
