@@ -202,57 +202,74 @@ __global__ void k_mode_coeffs(const double* __restrict__ lam, const double* __re
 }
 
 // Phi[f][k][m] = (1/sqrt(W_m)) sum_l Qhat'[f][l][m] B_f[l][k]   (SIMT)
-// One CTA per (tile of blockDim.x points, frequency), modes k0 .. k0+kc-1.
-template <typename R>
+// One CTA per (tile of 2 * blockDim.x points, frequency).  B_f (all modes,
+// rows padded with zeros to a multiple of KG) sits in shared memory; each
+// thread takes two adjacent points and walks the modes in groups of KG,
+// reading its two points' Qhat pairs from global memory (L1-resident after
+// the first group) and B_f as 16-byte broadcast loads.
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <typename R, int KG>
 __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, int64_t rs, int nb, int nmodes,
-                                                    int k0, int kc, int64_t mcount, int64_t m0, int64_t M,
-                                                    const R* __restrict__ bmat, const R* __restrict__ rsqrtW,
+                                                    int nmp, int64_t mcount, int64_t m0, int64_t M,
+                                                    const R* __restrict__ bmat, const R* __restrict__ scale,
                                                     R* __restrict__ phi) {
-  const int TPM = blockDim.x;
+  using V2 = typename Cplx<R>::T;
   const int f = blockIdx.y;
-  const int64_t lm0 = (int64_t)blockIdx.x * TPM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sB = reinterpret_cast<R*>(smem_raw);          // [nb][kc][2]
-  R* sQ = sB + 2 * nb * kc;                         // [2nb][TPM]
-  const R* Bf = bmat + (size_t)f * nb * nmodes * 2;
-  for (int e = threadIdx.x; e < nb * kc; e += blockDim.x) {
-    const int l = e / kc, k = e - l * kc;
-    sB[2 * e] = Bf[(l * nmodes + k0 + k) * 2];
-    sB[2 * e + 1] = Bf[(l * nmodes + k0 + k) * 2 + 1];
-  }
-  const R* qf = qhat + (int64_t)f * 2 * nb * rs;
-  for (int e = threadIdx.x; e < 2 * nb * TPM; e += blockDim.x) {
-    const int row = e / TPM, k = e - row * TPM;
-    R v = 0;
-    if (lm0 + k < mcount) v = qf[(int64_t)row * rs + lm0 + k];
-    sQ[e] = v;
+  V2* sB = reinterpret_cast<V2*>(smem_raw);                       // [nb][nmp]
+  const V2* Bf = reinterpret_cast<const V2*>(bmat) + (size_t)f * nb * nmodes;
+  for (int e = threadIdx.x; e < nb * nmp; e += blockDim.x) {
+    const int l = e / nmp, k = e - l * nmp;
+    V2 z;
+    z.x = 0; z.y = 0;
+    sB[e] = k < nmodes ? Bf[l * nmodes + k] : z;
   }
   __syncthreads();
-  const int t = threadIdx.x;
-  const int64_t lm = lm0 + t;
+  const int64_t lm = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
   if (lm >= mcount) return;
+  const bool two = lm + 1 < mcount;
   const int64_t m = m0 + lm;
-  const R rw = rsqrtW[m];
-  using V2 = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
-  V2* out = reinterpret_cast<V2*>(phi);
-  for (int kb = 0; kb < kc; kb += 4) {
-    R accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
-    for (int l = 0; l < nb; ++l) {
-      const R qr = sQ[l * TPM + t], qi = sQ[(nb + l) * TPM + t];
+  const R s0 = scale[m], s1 = two ? scale[m + 1] : (R)0;
+  // point lm + 1 < mpad: the FFT wrote zeros past mcount, so the pair load stays in the chunk
+  const R* qf = qhat + (int64_t)f * 2 * nb * rs + lm;
+  const bool vec = (M % 2) == 0;                                  // two points = one aligned 2-complex store
+  for (int k0 = 0; k0 < nmodes; k0 += KG) {
+    R ar0[KG], ai0[KG], ar1[KG], ai1[KG];
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const int k = min(kb + kk, kc - 1);
-        const R br = sB[(l * kc + k) * 2], bi = sB[(l * kc + k) * 2 + 1];
-        accr[kk] += qr * br - qi * bi;
-        acci[kk] += qr * bi + qi * br;
+    for (int j = 0; j < KG; ++j) { ar0[j] = 0; ai0[j] = 0; ar1[j] = 0; ai1[j] = 0; }
+    for (int l = 0; l < nb; ++l) {
+      const V2 qr = *reinterpret_cast<const V2*>(qf + (int64_t)l * rs);        // Re, points lm and lm + 1
+      const V2 qi = *reinterpret_cast<const V2*>(qf + (int64_t)(nb + l) * rs); // Im
+      const V2* bl = sB + l * nmp + k0;
+#pragma unroll
+      for (int j = 0; j < KG; ++j) {
+        const V2 b = bl[j];
+        ar0[j] += qr.x * b.x - qi.x * b.y;
+        ai0[j] += qr.x * b.y + qi.x * b.x;
+        ar1[j] += qr.y * b.x - qi.y * b.y;
+        ai1[j] += qr.y * b.y + qi.y * b.x;
       }
     }
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const int k = kb + kk;
-      if (k >= kc) break;
-      V2 v; v.x = accr[kk] * rw; v.y = acci[kk] * rw;
-      out[((int64_t)f * nmodes + k0 + k) * M + m] = v;
+    for (int j = 0; j < KG; ++j) {
+      const int k = k0 + j;
+      if (k >= nmodes) break;
+      R* o = phi + (((int64_t)f * nmodes + k) * M + m) * 2;
+      if (two && vec && sizeof(R) == 4) {
+        *reinterpret_cast<float4*>(o) = make_float4((float)(ar0[j] * s0), (float)(ai0[j] * s0),
+                                                    (float)(ar1[j] * s1), (float)(ai1[j] * s1));
+      } else {
+        V2 v;
+        v.x = ar0[j] * s0; v.y = ai0[j] * s0;
+        *reinterpret_cast<V2*>(o) = v;
+        if (two) {
+          v.x = ar1[j] * s1; v.y = ai1[j] * s1;
+          *reinterpret_cast<V2*>(o + 2) = v;
+        }
+      }
     }
   }
 }
@@ -299,28 +316,20 @@ cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s)
 template <typename R>
 static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
                                   cudaStream_t s, int* nlaunch, bool adjoint) {
-  // point tile and mode group sized to stay within 160 KB of shared memory
-  const size_t cap = 160 * 1024;
-  int tpm = 128;
-  while (tpm > 32 && sizeof(R) * 2 * (size_t)p.nb * (tpm + 4) > cap) tpm /= 2;
-  int kg = nmodes;
-  while (kg > 4 && sizeof(R) * 2 * (size_t)p.nb * (tpm + kg) > cap) kg = (kg + 1) / 2;
-  auto kern = k_modes_simt<R>;
-  const size_t smem_max = sizeof(R) * 2 * (size_t)p.nb * (tpm + kg);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  constexpr int KG = sizeof(R) == 8 ? 8 : 16;
+  const int nmp = (nmodes + KG - 1) / KG * KG;
+  const size_t smem = sizeof(typename Cplx<R>::T) * (size_t)p.nb * nmp;
+  auto kern = k_modes_simt<R, KG>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((mcount + tpm - 1) / tpm), (unsigned)p.nf);
-  for (int k0 = 0; k0 < nmodes; k0 += kg) {
-    const int kc = std::min(kg, nmodes - k0);
-    const size_t smem = sizeof(R) * 2 * (size_t)p.nb * (tpm + kc);
-    kern<<<grid, tpm, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, nmodes, k0, kc, mcount, m0,
-                                 p.M, static_cast<const R*>(p.d_bmat),
-                                 static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW),
-                                 static_cast<R*>(d_Phi));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    ++*nlaunch;
-  }
+  constexpr int threads = 128;
+  dim3 grid((unsigned)((mcount + 2 * threads - 1) / (2 * threads)), (unsigned)p.nf);
+  kern<<<grid, threads, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, nmodes, nmp, mcount, m0,
+                                   p.M, static_cast<const R*>(p.d_bmat),
+                                   static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW), static_cast<R*>(d_Phi));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ++*nlaunch;
   return cudaSuccess;
 }
 

@@ -18,6 +18,15 @@ namespace {
 constexpr int TK = 32;        // points staged per step
 constexpr int kFlush = 256;   // FP32 -> FP64 promotion interval (points)
 
+__device__ __forceinline__ void load4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_gram_simt(const R* __restrict__ qhat, int64_t rs, int nb, int64_t mcount,
                                                    int64_t per_split, int first, double* __restrict__ gpart,
@@ -68,11 +77,11 @@ __global__ void __launch_bounds__(256) k_gram_simt(const R* __restrict__ qhat, i
       const int kmax = (int)min((int64_t)TK, p1 - pb);
       for (int k = 0; k < kmax; ++k) {
         R xr[4], xi[4], yr[4], yi[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          xr[i] = sR[k * RS + 4 * I + i]; xi[i] = sI[k * RS + 4 * I + i];
-          yr[i] = sR[k * RS + 4 * J + i]; yi[i] = sI[k * RS + 4 * J + i];
-        }
+        // 4-wide shared loads (rows are padded to a multiple of 4)
+        load4(sR + k * RS + 4 * I, xr);
+        load4(sI + k * RS + 4 * I, xi);
+        load4(sR + k * RS + 4 * J, yr);
+        load4(sI + k * RS + 4 * J, yi);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
