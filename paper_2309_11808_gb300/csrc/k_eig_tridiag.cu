@@ -162,7 +162,18 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
   // chain forms each rotation from one reciprocal square root (r^2 = f^2 + g^2,
   // s = f / r, c = g / r) instead of hypot and two divisions; the scaled hypot
   // path is kept for r^2 outside [2^-960, 2^960].
+  // A coupling also counts as negligible below eps * ||T||_inf: dropping it moves
+  // no eigenvalue by more than that (Weyl), the normwise accuracy of the
+  // reduction itself.  Without this floor the purely relative test can stall on
+  // a cluster of rounding-level eigenvalues of a rank-deficient Gram (nb > M).
   const int warp = tid >> 5, lane = tid & 31;
+  double tfloor = 0.0;
+  if (warp == 0) {
+    double m = 0.0;
+    for (int i = lane; i < n; i += 32) m = fmax(m, fabs(d[i]) + fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    tfloor = 0x1p-53 * m;
+  }
   for (int l = 0; l < n; ++l) {
     for (int iter = 0;; ++iter) {
       if (warp == 0) {
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
         for (int base = l; base < n - 1; base += 32) {
           const int i = base + lane;
           bool split = false;
-          if (i < n - 1) split = fabs(e[i]) <= 0x1p-53 * (fabs(d[i]) + fabs(d[i + 1]));
+          if (i < n - 1) split = fabs(e[i]) <= fmax(0x1p-53 * (fabs(d[i]) + fabs(d[i + 1])), tfloor);
           const unsigned bal = __ballot_sync(0xffffffffu, split);
           if (bal) { mm = base + __ffs(bal) - 1; break; }
         }

@@ -3,21 +3,29 @@
 // SIMT arithmetic (FP32 or FP64) from the planar Qhat written by the FFT
 // kernel (sqrt(W) already folded in).
 //
-// Grid: (split s, frequency f).  Each CTA owns a contiguous range of the
-// chunk's points and one thread per 4x4 tile of the upper triangle of the
-// nb x nb complex Gram.  FP32 partial sums are promoted to FP64 every kFlush
-// points.  Partials are kept per split in FP64 and added chunk after chunk in
+// Grid: (split s, frequency f, tile group).  Each CTA owns a contiguous range
+// of the chunk's points; four groups of 64 threads share it point by point,
+// one thread per 4x4 tile of the upper triangle of the nb x nb complex Gram
+// in each group.  FP32 partial sums are promoted to FP64 every 256 points of
+// a thread (FP64 sums stay in registers).  Partials are kept per split in FP64 and added chunk after chunk in
 // stream order, then summed over splits in a fixed order by k_gram_reduce:
 // no atomics, so the result is bit-reproducible (the in-GPU counterpart of
 // the paper's single reduction of the Gram over ranks, Sec. 3.1).
+#include <algorithm>
+
 #include "spod_internal.cuh"
 
 namespace spod {
 namespace {
 
-constexpr int TK = 32;        // points staged per step
-constexpr int kFlush = 256;   // FP32 -> FP64 promotion interval (points)
+constexpr int TK = 32;        // points staged per round
+constexpr int KSUB = 4;       // thread groups splitting a round's points (point k goes to group k % KSUB)
+constexpr int TPG = 64;       // threads per group: one 4x4 complex tile of the upper triangle each
+constexpr int kThreads = KSUB * TPG;
+constexpr int kFlushRounds = 32;
+constexpr size_t kGramSimtSmemMax = 227 * 1024;   // FP32 -> FP64 promotion every 32 rounds (TK * 32 / KSUB = 256 points a thread)
 
+// 4-wide shared loads (rows are padded to a multiple of 4)
 __device__ __forceinline__ void load4(const float* p, float* v) {
   const float4 a = *reinterpret_cast<const float4*>(p);
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -27,21 +35,34 @@ __device__ __forceinline__ void load4(const double* p, double* v) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// One CTA per (split of the chunk's points, frequency, group of 64 tiles).
+// Rounds of TK points are staged (transposed, [point][row]) into nbuf shared
+// buffers: the next round's global loads are issued before the current round
+// is used, and stored after it (into the other buffer, or into the same one
+// after a barrier when only one fits).  Thread (group q, tile t) accumulates
+// tile t over the round's points k = q, q + KSUB, ...; FP32 partial sums are
+// added into FP64 sums in shared memory every kFlushRounds rounds, and the
+// KSUB groups' FP64 sums are combined in group order at the end (for FP64 the
+// combining area overlays the staging buffers, which are idle by then).
 template <typename R>
-__global__ void __launch_bounds__(256) k_gram_simt(const R* __restrict__ qhat, int64_t rs, int nb, int64_t mcount,
-                                                   int64_t per_split, int first, double* __restrict__ gpart,
-                                                   int nf) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_gram_simt(const R* __restrict__ qhat, int64_t rs, int nb,
+                                                           int64_t mcount, int64_t per_split, int first, int nbuf,
+                                                           double* __restrict__ gpart, int nf) {
+  constexpr bool kPromote = sizeof(R) == 4;
   const int s = blockIdx.x;
   const int f = blockIdx.y;
   const int ntl = (nb + 3) / 4;
   const int RS = 4 * ntl;                       // staged row stride (rows padded with zeros)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sR = reinterpret_cast<R*>(smem_raw);       // [TK][RS]
-  R* sI = sR + TK * RS;                         // [TK][RS]
+  double* acc64 = reinterpret_cast<double*>(smem_raw);             // [32][kThreads]
+  R* stage = kPromote ? reinterpret_cast<R*>(acc64 + 32 * kThreads)  // [nbuf][re, im][TK][RS]
+                      : reinterpret_cast<R*>(smem_raw);
+  const int buf_elems = 2 * TK * RS;
 
-  // this thread's tile (I <= J) of the upper triangle; grid.z splits the tiles
+  const int tid = threadIdx.x;
+  const int q = tid / TPG;
   const int ntiles = ntl * (ntl + 1) / 2;
-  const int tix = blockIdx.z * blockDim.x + threadIdx.x;
+  const int tix = blockIdx.z * TPG + (tid % TPG);
   int I = 0, J = 0;
   const bool active = tix < ntiles;
   {
@@ -49,35 +70,87 @@ __global__ void __launch_bounds__(256) k_gram_simt(const R* __restrict__ qhat, i
     while (active && t >= ntl - row) { t -= ntl - row; ++row; }
     I = row; J = row + t;
   }
+  if (kPromote) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) acc64[e * kThreads + tid] = 0.0;
+  }
 
   const int64_t p0 = (int64_t)s * per_split;
   const int64_t p1 = min(mcount, p0 + per_split);
   const R* qf = qhat + (int64_t)f * 2 * nb * rs;
+  const int nrounds = p1 > p0 ? (int)((p1 - p0 + TK - 1) / TK) : 0;
 
-  R ar[4][4], ai[4][4];
-  double dr[4][4], di[4][4];
+  // staging: element e of a round = (plane c, row l, point k), point fastest (coalesced)
+  constexpr int kMaxPer = (2 * 64 * TK + kThreads - 1) / kThreads;   // nb <= 64
+  R pre[kMaxPer];
+  auto fetch = [&](int r) {
+    const int64_t pb = p0 + (int64_t)r * TK;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < kMaxPer; ++j) {
+      const int idx = tid + j * kThreads;
+      R v = 0;
+      if (idx < buf_elems) {
+        const int row = idx / TK, k = idx - row * TK;
+        const int c = row / RS, l = row - c * RS;
+        if (l < nb && pb + k < p1) v = qf[((int64_t)c * nb + l) * rs + pb + k];
+      }
+      pre[j] = v;
+    }
+  };
+  auto put = [&](int b, int r) {
+    R* st = stage + b * buf_elems;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { ar[i][j] = 0; ai[i][j] = 0; dr[i][j] = 0; di[i][j] = 0; }
-
-  int since_flush = 0;
-  for (int64_t pb = p0; pb < p1; pb += TK) {
-    __syncthreads();
-    // stage rows (re: 0..nb-1, im: nb..2nb-1) of points [pb, pb+TK)
-    for (int idx = threadIdx.x; idx < 2 * RS * TK; idx += blockDim.x) {
+    for (int j = 0; j < kMaxPer; ++j) {
+      const int idx = tid + j * kThreads;
+      if (idx < buf_elems) {
+        const int row = idx / TK, k = idx - row * TK;
+        const int c = row / RS, l = row - c * RS;
+        st[c * TK * RS + k * RS + l] = pre[j];
+      }
+    }
+    // rows beyond the prefetched ones (nb > 64) are copied directly
+    const int64_t pb = p0 + (int64_t)r * TK;
+    for (int idx = kMaxPer * kThreads + tid; idx < buf_elems; idx += kThreads) {
       const int row = idx / TK, k = idx - row * TK;
       const int c = row / RS, l = row - c * RS;
       R v = 0;
       if (l < nb && pb + k < p1) v = qf[((int64_t)c * nb + l) * rs + pb + k];
-      (c == 0 ? sR : sI)[k * RS + l] = v;
+      st[c * TK * RS + k * RS + l] = v;
     }
-    __syncthreads();
+  };
+
+  R ar[4][4], ai[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { ar[i][j] = 0; ai[i][j] = 0; }
+  auto flush = [&]() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double* er = acc64 + (2 * (4 * i + j)) * kThreads + tid;
+        double* ei = er + kThreads;
+        if (kPromote) { *er += (double)ar[i][j]; *ei += (double)ai[i][j]; }
+        else { *er = (double)ar[i][j]; *ei = (double)ai[i][j]; }
+        ar[i][j] = 0; ai[i][j] = 0;
+      }
+  };
+
+  if (nrounds > 0) {
+    fetch(0);
+    put(0, 0);
+  }
+  __syncthreads();
+  for (int r = 0; r < nrounds; ++r) {
+    const int b = nbuf == 2 ? (r & 1) : 0;
+    if (r + 1 < nrounds) fetch(r + 1);        // in flight while this round is used
     if (active) {
-      const int kmax = (int)min((int64_t)TK, p1 - pb);
-      for (int k = 0; k < kmax; ++k) {
+      const R* sR = stage + b * buf_elems;
+      const R* sI = sR + TK * RS;
+#pragma unroll 4
+      for (int k = q; k < TK; k += KSUB) {
         R xr[4], xi[4], yr[4], yi[4];
-        // 4-wide shared loads (rows are padded to a multiple of 4)
         load4(sR + k * RS + 4 * I, xr);
         load4(sI + k * RS + 4 * I, xi);
         load4(sR + k * RS + 4 * J, yr);
@@ -91,20 +164,18 @@ __global__ void __launch_bounds__(256) k_gram_simt(const R* __restrict__ qhat, i
             ai[i][j] += xr[i] * yi[j] - xi[i] * yr[j];
           }
       }
-      since_flush += kmax;
-      if (sizeof(R) == 4 && since_flush >= kFlush) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            dr[i][j] += (double)ar[i][j]; di[i][j] += (double)ai[i][j];
-            ar[i][j] = 0; ai[i][j] = 0;
-          }
-        since_flush = 0;
-      }
+      if (kPromote && (r + 1) % kFlushRounds == 0) flush();
     }
+    if (r + 1 < nrounds) {
+      if (nbuf == 1) __syncthreads();          // one buffer: wait until every thread has used it
+      put(nbuf == 2 ? (b ^ 1) : 0, r + 1);     // with two, the other buffer was last read in round r - 1
+    }
+    __syncthreads();
   }
-  if (!active) return;
+  if (active || !kPromote) flush();            // FP64: every thread writes its slots (staging is idle)
+  __syncthreads();
+  if (!active || q != 0) return;
+  // combine the KSUB groups in group order, then write the tile
   double* g = gpart + (((int64_t)s * nf + f) * nb) * nb * 2;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -112,8 +183,11 @@ __global__ void __launch_bounds__(256) k_gram_simt(const R* __restrict__ qhat, i
     for (int j = 0; j < 4; ++j) {
       const int li = 4 * I + i, lj = 4 * J + j;
       if (li >= nb || lj >= nb || lj < li) continue;
-      const double vr = dr[i][j] + (double)ar[i][j];
-      const double vi = di[i][j] + (double)ai[i][j];
+      double vr = 0.0, vi = 0.0;
+      for (int qq = 0; qq < KSUB; ++qq) {
+        vr += acc64[(2 * (4 * i + j)) * kThreads + qq * TPG + (tid % TPG)];
+        vi += acc64[(2 * (4 * i + j) + 1) * kThreads + qq * TPG + (tid % TPG)];
+      }
       double* e = g + ((int64_t)li * nb + lj) * 2;
       if (first) { e[0] = vr; e[1] = vi; }
       else { e[0] += vr; e[1] += vi; }
@@ -143,25 +217,41 @@ __global__ void k_gram_reduce(const double* __restrict__ gpart, int splits, int 
   }
 }
 
+// Staging buffers (two when they fit) and shared bytes for element size rb.
+int gram_simt_nbuf(int nb, size_t rb, size_t* smem_out) {
+  const size_t acc = sizeof(double) * 32 * kThreads;
+  const size_t buf = 2 * (size_t)TK * 4 * ((nb + 3) / 4) * rb;
+  auto total = [&](int n) { return rb == 4 ? acc + n * buf : std::max(acc, n * buf); };
+  const int nbuf = total(2) <= kGramSimtSmemMax ? 2 : 1;
+  *smem_out = total(nbuf);
+  return nbuf;
+}
+
 template <typename R>
 cudaError_t launch_gram_t(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s) {
   const int ntl = (p.nb + 3) / 4;
   const int ntiles = ntl * (ntl + 1) / 2;
-  const int threads = min(256, max(32, ((ntiles + 31) / 32) * 32));
-  const int groups = (ntiles + threads - 1) / threads;
-  const size_t smem = 2 * (size_t)TK * 4 * ntl * sizeof(R);
+  const int groups = (ntiles + TPG - 1) / TPG;
+  size_t smem = 0;
+  const int nbuf = gram_simt_nbuf(p.nb, sizeof(R), &smem);
   auto kern = k_gram_simt<R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t per = (mcount + p.gram_splits - 1) / p.gram_splits;
   per = ((per + TK - 1) / TK) * TK;
   dim3 grid((unsigned)p.gram_splits, (unsigned)p.nf, (unsigned)groups);
-  kern<<<grid, threads, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, mcount, per,
-                                   first ? 1 : 0, p.d_gpart, p.nf);
+  kern<<<grid, kThreads, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, mcount, per,
+                                   first ? 1 : 0, nbuf, p.d_gpart, p.nf);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t gram_simt_smem_bytes(const spod_plan_s& p) {
+  size_t smem = 0;
+  gram_simt_nbuf(p.nb, p.f64 ? 8 : 4, &smem);
+  return smem;
+}
 
 cudaError_t launch_gram_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s) {
   return p.f64 ? launch_gram_t<double>(p, mcount, first, s) : launch_gram_t<float>(p, mcount, first, s);

@@ -337,6 +337,8 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   }
   if (fft_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
     return bail(SPOD_EUNSUPPORTED, "nfft too large for the shared-memory FFT");
+  if (!p->tensor && gram_simt_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
+    return bail(SPOD_EUNSUPPORTED, "nb too large for the shared-memory Gram kernel");
   if (p->tensor && (gram_tc_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin ||
                     modes_tc_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin))
     return bail(SPOD_EUNSUPPORTED, "tensor-core kernels do not fit in shared memory for this nb");

@@ -156,6 +156,7 @@ size_t gram_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_image_bytes(const spod_plan_s& p);
 cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s);
+size_t gram_simt_smem_bytes(const spod_plan_s& p);
 size_t gram_tc_slot_doubles(const spod_plan_s& p, int max_ctas);
 size_t gram_tc_acc_doubles(const spod_plan_s& p);
 int gram_tc_ctas(const spod_plan_s& p);

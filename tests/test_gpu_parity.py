@@ -127,6 +127,7 @@ SHAPES = [
     (20, 1, 720, 720, 0),       # nfft = 720 = 2^4 3^2 5, nb = 1 (1 x 1 Gram)
     (64, 1, 260, 125, 0),       # 5^3, nb = 2, tail of 10 samples
     (96, 1, 130, 2, 1),         # smallest nfft, nb = 129 (> the shared-memory eigen-solver size)
+    (40, 1, 257, 2, 1),         # nb = 256, the largest supported (FP64 Gram stages one buffer)
 ]
 
 
