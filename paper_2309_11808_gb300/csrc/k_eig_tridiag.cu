@@ -1,19 +1,34 @@
 // Batched Hermitian eigen-decomposition of the Grams M_f by Householder
-// tridiagonalisation and implicit QL iteration (FP64, one CTA per frequency).
+// tridiagonalisation and implicit QL iteration (one 256-thread CTA per
+// frequency).
 //
-// 1. Reduction (n-1 steps): for column k, the reflector H_k = I - tau v v^H
+// 1. Reduction (n-1 steps, FP64): for column k, the reflector H_k = I - tau v v^H
 //    (v[0] = 1) with H_k^H (a, x)^T = (beta, 0)^T, beta real, annihilates
 //    A[k+2:, k] and makes the subdiagonal real; the trailing block is updated
 //    as A <- H_k^H A H_k = A - v w^H - w v^H with p = tau A v and
 //    w = p - (tau/2)(p^H v) v.  Then A = Q T Q^H, Q = H_0 H_1 ... H_{n-2}, T real
 //    symmetric tridiagonal.
-// 2. Implicit QL with Wilkinson shifts on (d, e): thread 0 runs each sweep's
-//    chain of plane rotations and records them; all threads then apply the
-//    sequence to their rows of the real eigenvector matrix Z.
-// 3. Back-transform V = Q Z, columns in parallel.
+// 2. Three warp roles run at once:
+//    * warp 0: implicit QL with Wilkinson shifts on (d, e); lane 0 runs each
+//      sweep's chain of plane rotations and publishes (cosine, sine) into one
+//      of two buffers;
+//    * warps 1-2: apply each published sweep to the rows of the real
+//      eigenvector matrix Z (FP64), one buffer behind the chain;
+//    * warps 3-7: form Q explicitly from the stored reflectors (FP64).
+//    Named barriers hand the two rotation buffers back and forth.
+// 3. V = Q Z (FP64, all threads).
 // 4. Eigenvalues descending (ties: lower index first); eigenvectors unit
 //    2-norm with the largest-modulus entry (lowest index on ties) real positive.
-// About 10 n^3 FP64 operations against ~150 n^3 for the cyclic Jacobi solver.
+//
+// On this part a dependent FP64 operation costs about 14 times a FP32 one, and
+// every FP64 warp instruction occupies the FP64 pipe about as long whatever
+// the number of active lanes.  So the one-thread rotation chain, a long run of
+// dependent operations, runs in FP64 only for the FP64 precision; for the
+// others it runs in double-FP32 (an unevaluated sum of two floats, about 48
+// bits) on T scaled by a power of two.  Matrices keep odd row strides (in 8-
+// and 16-byte units) so column walks fall in distinct shared-memory banks, and
+// the reduction's matrix-vector product reads columns (A is Hermitian) split
+// over all warps.
 #include "spod_internal.cuh"
 
 namespace spod {
@@ -21,6 +36,18 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxIter = 60;           // QL iterations per eigenvalue
+constexpr int kBarFull = 1;            // named barriers 1, 2: rotation buffer published
+constexpr int kBarEmpty = 3;           // named barriers 3, 4: rotation buffer applied
+constexpr int kBarQ = 5;               // named barrier of the Q-forming warps
+constexpr int kRotThreads = 96;        // warp 0 + warps 1-2
+constexpr int kQThreads = kThreads - kRotThreads;
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -43,47 +70,358 @@ __device__ double2 block_sum2(double2 v, double2* red) {
   return t;
 }
 
+__host__ __device__ constexpr int odd_stride(int n) { return n | 1; }
+
+// ---- double-FP32 ("df64") arithmetic: value = h + l, |l| <= ulp(h) / 2.
+// Error-free transformations (Knuth's TwoSum, Dekker's Fast2Sum, the FMA
+// product) and the double-word sum and product of Joldes, Muller and Popescu
+// (ACM TOMS 44(2), 2017: accurate DW + DW, DW x DW).  Explicit _rn intrinsics
+// keep the compiler from contracting or reordering them.
+struct dw {
+  float h, l;
+};
+__device__ __forceinline__ dw dw_of(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float t = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, t)), __fsub_rn(b, t));
+  return {s, e};
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+  const dw s = two_sum(x.h, y.h), t = two_sum(x.l, y.l);
+  const dw v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
+}
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+  const float ch = __fmul_rn(x.h, y.h);
+  const float cl1 = __fmaf_rn(x.h, y.h, -ch);
+  const float tl1 = __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.l));
+  const float cl2 = __fmaf_rn(x.l, y.h, tl1);
+  return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+__device__ __forceinline__ dw dw_mul2(dw x) { return {2.0f * x.h, 2.0f * x.l}; }   // exact
+// x / y: an FP32 quotient and two residual corrections.
+__device__ __forceinline__ dw dw_div(dw x, dw y) {
+  const float q1 = __fdividef(x.h, y.h);
+  const dw r1 = dw_sub(x, dw_mul(y, dw_of(q1)));
+  const float q2 = __fdividef(r1.h, y.h);
+  const dw r2 = dw_sub(r1, dw_mul(y, dw_of(q2)));
+  const float q3 = __fdividef(r2.h, y.h);
+  return dw_add(fast_two_sum(q1, q2), dw_of(q3));
+}
+// 1 / sqrt(x), x > 0 normal: y0 = rsqrtf(x_h), e = 1 - x y0^2 in df64, then the
+// second-order step y = y0 (1 + e/2 + 3 e^2/8) (error O(e^3), e ~ 2^-22).
+__device__ __forceinline__ dw dw_rsqrt(dw x) {
+  const float y0 = rsqrtf(x.h);
+  const float p = __fmul_rn(y0, y0);
+  const dw y2 = {p, __fmaf_rn(y0, y0, -p)};           // y0^2 exactly
+  const dw e = dw_sub(dw_of(1.0f), dw_mul(x, y2));
+  const float u = __fmaf_rn(e.h, __fmaf_rn(0.375f, e.h, 0.5f), 0.5f * e.l);
+  return fast_two_sum(y0, __fmul_rn(y0, u));
+}
+__device__ __forceinline__ dw dw_from_double(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double dw_to_double(dw v) { return (double)v.h + (double)v.l; }
+
+// One implicit QL sweep with a Wilkinson shift over the unreduced block
+// [l, mm] of (d, e) (one thread); records the rotations' cosines and sines for
+// the eigenvector update and returns their number.  FP64 form.
+__device__ __noinline__ int ql_sweep_f64(double* d, double* e, int l, int mm, double* rc, double* rsn) {
+  // shift: g = (d_l+1 - d_l) / (2 e_l), r = sqrt(g^2 + 1), g = d_mm - d_l + e_l / (g + sign(g) r)
+  double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+  double r = sqrt(fma(g, g, 1.0));
+  g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+  double s = 1.0, c = 1.0, p = 0.0;
+  int nrot = 0;
+  for (int i = mm - 1; i >= l; --i) {
+    const double ff = s * e[i];
+    const double b = c * e[i];
+    const double r2 = fma(ff, ff, g * g);
+    if (r2 > 0x1p-960 && r2 < 0x1p960) {     // one reciprocal square root
+      const double ri = rsqrt(r2);
+      r = r2 * ri;
+      s = ff * ri;
+      c = g * ri;
+    } else {                                  // scaled form outside that range
+      r = hypot(ff, g);
+      if (r == 0.0) {                         // the block splits at i + 1
+        e[i + 1] = 0.0;
+        d[i + 1] -= p;
+        e[mm] = 0.0;
+        return nrot;
+      }
+      s = ff / r;
+      c = g / r;
+    }
+    e[i + 1] = r;
+    g = d[i + 1] - p;
+    r = fma(d[i] - g, s, 2.0 * c * b);
+    p = s * r;
+    d[i + 1] = g + p;
+    g = fma(c, r, -b);
+    rc[nrot] = c;
+    rsn[nrot] = s;
+    ++nrot;
+  }
+  d[l] -= p;
+  e[l] = g;
+  e[mm] = 0.0;
+  return nrot;
+}
+
+// The same sweep in df64 on the scaled (d, e) held as (h, l) float pairs.
+__device__ __noinline__ int ql_sweep_dw(float2* dd, float2* ee, int l, int mm, double* rc, double* rsn) {
+  auto D = [&](int i) { const float2 v = dd[i]; return dw{v.x, v.y}; };
+  auto E = [&](int i) { const float2 v = ee[i]; return dw{v.x, v.y}; };
+  auto setD = [&](int i, dw v) { dd[i] = make_float2(v.h, v.l); };
+  auto setE = [&](int i, dw v) { ee[i] = make_float2(v.h, v.l); };
+  const dw dl = D(l), el = E(l);
+  dw g = dw_div(dw_sub(D(l + 1), dl), dw_mul2(el));
+  const dw t = dw_add(dw_mul(g, g), dw_of(1.0f));
+  const dw r0 = dw_mul(t, dw_rsqrt(t));
+  g = dw_add(dw_sub(D(mm), dl), dw_div(el, g.h >= 0.0f ? dw_add(g, r0) : dw_sub(g, r0)));
+  dw s = dw_of(1.0f), c = dw_of(1.0f), p = dw_of(0.0f);
+  int nrot = 0;
+  for (int i = mm - 1; i >= l; --i) {
+    const dw ei = E(i);
+    dw ff = dw_mul(s, ei), gg = g;
+    const dw b = dw_mul(c, ei);
+    float post = 1.0f;
+    dw r2 = dw_add(dw_mul(ff, ff), dw_mul(gg, gg));
+    if (r2.h < 0x1p-100f) {                 // tiny pair: rescale by an exact power of two
+      ff = {ff.h * 0x1p64f, ff.l * 0x1p64f};
+      gg = {gg.h * 0x1p64f, gg.l * 0x1p64f};
+      post = 0x1p-64f;
+      r2 = dw_add(dw_mul(ff, ff), dw_mul(gg, gg));
+    }
+    if (!(r2.h > 0x1p-120f)) {              // both negligible: the block splits at i + 1
+      setE(i + 1, dw_of(0.0f));
+      setD(i + 1, dw_sub(D(i + 1), p));
+      setE(mm, dw_of(0.0f));
+      return nrot;
+    }
+    const dw ri = dw_rsqrt(r2);
+    const dw rr = dw_mul(r2, ri);
+    setE(i + 1, {rr.h * post, rr.l * post});
+    s = dw_mul(ff, ri);
+    c = dw_mul(gg, ri);
+    g = dw_sub(D(i + 1), p);
+    const dw u = dw_add(dw_mul(dw_sub(D(i), g), s), dw_mul2(dw_mul(c, b)));
+    p = dw_mul(s, u);
+    setD(i + 1, dw_add(g, p));
+    g = dw_sub(dw_mul(c, u), b);
+    rc[nrot] = dw_to_double(c);
+    rsn[nrot] = dw_to_double(s);
+    ++nrot;
+  }
+  setD(l, dw_sub(D(l), p));
+  setE(l, g);
+  setE(mm, dw_of(0.0f));
+  return nrot;
+}
+
+// Warp 0: QL on (d, e), publishing every sweep with rotations into buffer
+// (published count) & 1; then a terminator (nrot = -1).  Before a buffer is
+// rewritten the appliers must have released it; at the end the last buffer
+// is waited for, so every arrival on the named barriers is matched.
+template <bool kDW>
+__device__ void ql_producer(double* d, double* e, int n, double* rc, double* rsn, int* ctl) {
+  const int lane = threadIdx.x & 31;
+  double tn = 0.0;
+  for (int i = lane; i < n; i += 32) tn = fmax(tn, fabs(d[i]) + fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0));
+  for (int o = 16; o > 0; o >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+  // A coupling counts as negligible when |e_i| <= u (|d_i| + |d_i+1|) or
+  // |e_i| <= u ||T||_inf (u = 2^-53 in FP64, 2^-47 in df64): dropping it moves
+  // no eigenvalue by more than that (Weyl).  Without the absolute floor the
+  // relative test can stall on a cluster of rounding-level eigenvalues of a
+  // rank-deficient Gram (nb > M).
+  double sc = 1.0;
+  float2* dd = reinterpret_cast<float2*>(d);
+  float2* ee = reinterpret_cast<float2*>(e);
+  if constexpr (kDW) {
+    sc = scalbn(1.0, tn > 0.0 ? -ilogb(tn) : 0);      // ||T||_inf * sc in [1, 2)
+    for (int i = lane; i < n; i += 32) {
+      const dw a = dw_from_double(d[i] * sc), b = dw_from_double(e[i] * sc);
+      dd[i] = make_float2(a.h, a.l);
+      ee[i] = make_float2(b.h, b.l);
+    }
+    __syncwarp();
+  }
+  const double tfloor = 0x1p-53 * tn;
+  const float tfloor_f = 0x1p-47f * (float)(tn * sc);
+  int pub = 0;
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0;; ++iter) {
+      int mm = n - 1;
+      for (int base = l; base < n - 1; base += 32) {
+        const int i = base + lane;
+        bool split = false;
+        if (i < n - 1) {
+          if constexpr (kDW)
+            split = fabsf(ee[i].x) <= fmaxf(0x1p-47f * (fabsf(dd[i].x) + fabsf(dd[i + 1].x)), tfloor_f);
+          else
+            split = fabs(e[i]) <= fmax(0x1p-53 * (fabs(d[i]) + fabs(d[i + 1])), tfloor);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, split);
+        if (bal) { mm = base + __ffs(bal) - 1; break; }
+      }
+      if (mm == l) break;
+      if (iter >= kMaxIter) {                 // give up on this eigenvalue
+        if (lane == 0) ctl[0] = 1;
+        break;
+      }
+      const int slot = pub & 1;
+      if (pub >= 2) named_sync(kBarEmpty + slot, kRotThreads);
+      int nrot = 0;
+      if (lane == 0) {
+        double* rcs = rc + slot * n;
+        double* rss = rsn + slot * n;
+        if constexpr (kDW) nrot = ql_sweep_dw(dd, ee, l, mm, rcs, rss);
+        else nrot = ql_sweep_f64(d, e, l, mm, rcs, rss);
+        ctl[2 + 2 * slot] = mm;
+        ctl[3 + 2 * slot] = nrot;
+      }
+      nrot = __shfl_sync(0xffffffffu, nrot, 0);
+      __syncwarp();
+      if (nrot > 0) {
+        __threadfence_block();
+        named_arrive(kBarFull + slot, kRotThreads);
+        ++pub;
+      }
+    }
+  }
+  const int slot = pub & 1;
+  if (pub >= 2) named_sync(kBarEmpty + slot, kRotThreads);
+  if (lane == 0) ctl[3 + 2 * slot] = -1;
+  __syncwarp();
+  __threadfence_block();
+  named_arrive(kBarFull + slot, kRotThreads);
+  if (pub >= 1) named_sync(kBarEmpty + ((pub - 1) & 1), kRotThreads);
+  if constexpr (kDW) {
+    for (int i = lane; i < n; i += 32) {
+      const float2 a = dd[i];
+      d[i] = dw_to_double({a.x, a.y}) / sc;
+    }
+  }
+}
+
+// Warps 1-2: apply each published sweep (columns i+1, i for i = mm-1 down) to
+// the rows of Z.
+__device__ void ql_applier(double* Z, int ldz, int n, const double* rc, const double* rsn, const int* ctl) {
+  const int t = threadIdx.x - 32;
+  for (int q = 0;; ++q) {
+    const int slot = q & 1;
+    named_sync(kBarFull + slot, kRotThreads);
+    const int mm = ctl[2 + 2 * slot], nrot = ctl[3 + 2 * slot];
+    if (nrot < 0) break;
+    const double* rcs = rc + slot * n;
+    const double* rss = rsn + slot * n;
+    for (int row = t; row < n; row += 64) {
+      double* zr = Z + (size_t)row * ldz;
+      for (int j = 0; j < nrot; ++j) {
+        const int i = mm - 1 - j;
+        const double c = rcs[j], s = rss[j];
+        const double fz = zr[i + 1];
+        zr[i + 1] = fma(s, zr[i], c * fz);
+        zr[i] = fma(c, zr[i], -s * fz);
+      }
+    }
+    named_arrive(kBarEmpty + slot, kRotThreads);
+  }
+}
+
+// Warps 3-7: Q = H_0 H_1 ... H_{n-2} from the reflectors stored below the
+// subdiagonal of A (v_0 = 1 in place), applied to I in reverse order; after
+// H_{n-2} .. H_{k+1}, rows and columns up to k are still those of I, so H_k
+// touches the block [k+1:, k+1:] only.
+__device__ void form_q(const double2* A, double2* Qm, int lda, int n, const double2* tau, double2* sv) {
+  const int t = threadIdx.x - kRotThreads;
+  for (int idx = t; idx < n * n; idx += kQThreads) {
+    const int r = idx / n, c = idx - r * n;
+    Qm[(size_t)r * lda + c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+  named_sync(kBarQ, kQThreads);
+  for (int k = n - 2; k >= 0; --k) {
+    const double2 tk = tau[k];
+    if (tk.x == 0.0 && tk.y == 0.0) continue;
+    const int m = n - k - 1;
+    // s_j = tau v^H Q[k+1:, j]
+    for (int j = t; j < m; j += kQThreads) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int i = 0; i < m; ++i) {
+        const double2 c = cmulc(A[(size_t)(k + 1 + i) * lda + k], Qm[(size_t)(k + 1 + i) * lda + k + 1 + j]);
+        s.x += c.x; s.y += c.y;
+      }
+      sv[j] = cmul(tk, s);
+    }
+    named_sync(kBarQ, kQThreads);
+    for (int idx = t; idx < m * m; idx += kQThreads) {
+      const int i = idx / m, j = idx - i * m;
+      const double2 c = cmul(A[(size_t)(k + 1 + i) * lda + k], sv[j]);
+      double2& q = Qm[(size_t)(k + 1 + i) * lda + k + 1 + j];
+      q.x -= c.x;
+      q.y -= c.y;
+    }
+    named_sync(kBarQ, kQThreads);
+  }
+}
+
+template <bool kDW>
 __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restrict__ gram, int n,
                                                           double* __restrict__ lam, double* __restrict__ psi,
                                                           double* __restrict__ gws, unsigned* __restrict__ flags) {
   const int f = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5;
+  const int lda = odd_stride(n);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* red = reinterpret_cast<double2*>(smem_raw);          // [32]
   double2* tau = red + 32;                                       // [n]
-  double2* pv = tau + n;                                         // [n] p / w
-  double* d = reinterpret_cast<double*>(pv + n);                 // [n]
+  double2* pv = tau + n;                                         // [n] p / w; later s of form_q
+  double2* vv = pv + n;                                          // [n] reflector, contiguous
+  double2* part = vv + n;                                        // [kThreads] matrix-vector partial sums
+  double* d = reinterpret_cast<double*>(part + kThreads);        // [n]
   double* e = d + n;                                             // [n]
-  double* rc = e + n;                                            // [n] rotation cosines
-  double* rsn = rc + n;                                          // [n] rotation sines
-  int* ctl = reinterpret_cast<int*>(rsn + n);                    // [4] control words
-  // per frequency: A [n][n] complex, Lv [n][n] complex (reflector copy), Z [n][n] real
+  double* rc = e + n;                                            // [2][n] rotation cosines
+  double* rsn = rc + 2 * n;                                      // [2][n] rotation sines
+  int* ctl = reinterpret_cast<int*>(rsn + 2 * n);                // [8] control words
+  // per frequency: A [n][lda] complex (reflectors, then V), Q [n][lda] complex, Z [n][lda] real
   double2* A;
   {
-    uint8_t* after = reinterpret_cast<uint8_t*>(ctl + 4);
+    uint8_t* after = reinterpret_cast<uint8_t*>(ctl + 8);
     after = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(after) + 15) & ~uintptr_t(15));
     // per-frequency stride rounded up to an even number of doubles: double2 needs 16-byte alignment
-    const size_t stride = ((size_t)5 * n * n + 1) & ~(size_t)1;
+    const size_t stride = ((size_t)5 * n * lda + 1) & ~(size_t)1;
     A = (n <= kEigSmemMaxNb) ? reinterpret_cast<double2*>(after) : reinterpret_cast<double2*>(gws + (size_t)f * stride);
   }
-  double2* Lv = A + (size_t)n * n;
-  double* Z = reinterpret_cast<double*>(Lv + (size_t)n * n);
-  double2* V = A;   // the back-transform overwrites A once the reflectors are copied to Lv
+  double2* Qm = A + (size_t)n * lda;
+  double* Z = reinterpret_cast<double*>(Qm + (size_t)n * lda);
   const double2* G = reinterpret_cast<const double2*>(gram) + (size_t)f * n * n;
-  for (int i = tid; i < n * n; i += nth) A[i] = G[i];
+  for (int i = tid; i < n * n; i += nth) {
+    const int r = i / n, c = i - r * n;
+    A[(size_t)r * lda + c] = G[i];
+  }
   __syncthreads();
 
   // ---------------- 1. Householder reduction to real tridiagonal form
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;                    // length of x = A[k+1:, k]
-    double2 part = make_double2(0.0, 0.0);
+    double2 pt = make_double2(0.0, 0.0);
     for (int i = 1 + tid; i < m; i += nth) {
-      const double2 x = A[(k + 1 + i) * n + k];
-      part.x += x.x * x.x + x.y * x.y;
+      const double2 x = A[(size_t)(k + 1 + i) * lda + k];
+      pt.x += x.x * x.x + x.y * x.y;
     }
-    const double xn2 = block_sum2(part, red).x;   // |x[1:]|^2
+    const double xn2 = block_sum2(pt, red).x;   // |x[1:]|^2
     if (tid == 0) {
-      const double2 alpha = A[(k + 1) * n + k];
+      const double2 alpha = A[(size_t)(k + 1) * lda + k];
       double2 t = make_double2(0.0, 0.0);
       double beta = alpha.x;                     // stays alpha when no reflection is needed
       double2 scale = make_double2(0.0, 0.0);
@@ -93,8 +431,8 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
         t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
         // scale = 1 / (alpha - beta)
         const double2 den = make_double2(alpha.x - beta, alpha.y);
-        const double dd = den.x * den.x + den.y * den.y;
-        scale = make_double2(den.x / dd, -den.y / dd);
+        const double dd2 = den.x * den.x + den.y * den.y;
+        scale = make_double2(den.x / dd2, -den.y / dd2);
       }
       tau[k] = t;
       e[k] = beta;
@@ -105,191 +443,92 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
     const double2 scale = pv[0];
     __syncthreads();
     if (t.x == 0.0 && t.y == 0.0) continue;
-    // v = (1, x[1:] * scale), stored in place below the subdiagonal
-    for (int i = 1 + tid; i < m; i += nth) A[(k + 1 + i) * n + k] = cmul(A[(k + 1 + i) * n + k], scale);
-    if (tid == 0) A[(k + 1) * n + k] = make_double2(1.0, 0.0);
-    __syncthreads();
-    // p = tau * A22 v   (A22 = A[k+1:, k+1:])
+    // v = (1, x[1:] * scale): stored in place below the subdiagonal and in vv
     for (int i = tid; i < m; i += nth) {
-      double2 s = make_double2(0.0, 0.0);
-      const double2* row = A + (size_t)(k + 1 + i) * n + (k + 1);
-      for (int j = 0; j < m; ++j) {
-        const double2 a = row[j], v = A[(k + 1 + j) * n + k];
-        s.x += a.x * v.x - a.y * v.y;
-        s.y += a.x * v.y + a.y * v.x;
+      double2* a = A + (size_t)(k + 1 + i) * lda + k;
+      const double2 v = i == 0 ? make_double2(1.0, 0.0) : cmul(*a, scale);
+      *a = v;
+      vv[i] = v;
+    }
+    __syncthreads();
+    // p = tau * A22 v with A22 Hermitian: p_i = tau sum_j conj(A22[j][i]) v_j,
+    // S partial sums per i over j = s, s + S, ... (consecutive threads read
+    // consecutive columns), added in a fixed order
+    const int S = max(1, min(8, nth / m));
+    if (tid < S * m) {
+      const int i = tid % m, sidx = tid / m;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j = sidx; j < m; j += S) {
+        const double2 c = cmulc(A[(size_t)(k + 1 + j) * lda + (k + 1 + i)], vv[j]);
+        acc.x += c.x; acc.y += c.y;
       }
-      pv[i] = cmul(t, s);
+      part[sidx * m + i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) {
+      double2 acc = part[i];
+      for (int q = 1; q < S; ++q) { acc.x += part[q * m + i].x; acc.y += part[q * m + i].y; }
+      pv[i] = cmul(t, acc);
     }
     __syncthreads();
     // w = p - (tau/2) (p^H v) v
     double2 dot = make_double2(0.0, 0.0);
     for (int i = tid; i < m; i += nth) {
-      const double2 c = cmulc(pv[i], A[(k + 1 + i) * n + k]);
+      const double2 c = cmulc(pv[i], vv[i]);
       dot.x += c.x; dot.y += c.y;
     }
     dot = block_sum2(dot, red);
     const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), dot);
     __syncthreads();
     for (int i = tid; i < m; i += nth) {
-      const double2 v = A[(k + 1 + i) * n + k];
-      const double2 c = cmul(al, v);
+      const double2 c = cmul(al, vv[i]);
       pv[i] = make_double2(pv[i].x + c.x, pv[i].y + c.y);
     }
     __syncthreads();
     // A22 -= v w^H + w v^H
     for (int idx = tid; idx < m * m; idx += nth) {
       const int i = idx / m, j = idx - i * m;
-      const double2 vi = A[(k + 1 + i) * n + k], vj = A[(k + 1 + j) * n + k];
+      const double2 vi = vv[i], vj = vv[j];
       const double2 wi = pv[i], wj = pv[j];
-      double2& a = A[(k + 1 + i) * n + (k + 1 + j)];
+      double2& a = A[(size_t)(k + 1 + i) * lda + (k + 1 + j)];
       // v_i conj(w_j) + w_i conj(v_j)
       a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
       a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
     }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += nth) d[i] = A[i * n + i].x;
-  for (int idx = tid; idx < n * n; idx += nth) Z[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+  for (int i = tid; i < n; i += nth) d[i] = A[(size_t)i * lda + i].x;
+  for (int idx = tid; idx < n * n; idx += nth) {
+    const int r = idx / n, c = idx - r * n;
+    Z[(size_t)r * lda + c] = r == c ? 1.0 : 0.0;
+  }
   if (tid == 0) {
     e[n - 1] = 0.0;
     ctl[0] = 0;   // not-converged flag
   }
   __syncthreads();
 
-  // ---------------- 2. implicit QL with Wilkinson shifts; e[i] couples d[i], d[i+1]
-  // Warp 0 finds the end mm of the unreduced block (lanes test 32 indices at
-  // once), lane 0 runs the rotation chain.  FP64 is slow on this part, so the
-  // chain forms each rotation from one reciprocal square root (r^2 = f^2 + g^2,
-  // s = f / r, c = g / r) instead of hypot and two divisions; the scaled hypot
-  // path is kept for r^2 outside [2^-960, 2^960].
-  // A coupling also counts as negligible below eps * ||T||_inf: dropping it moves
-  // no eigenvalue by more than that (Weyl), the normwise accuracy of the
-  // reduction itself.  Without this floor the purely relative test can stall on
-  // a cluster of rounding-level eigenvalues of a rank-deficient Gram (nb > M).
-  const int warp = tid >> 5, lane = tid & 31;
-  double tfloor = 0.0;
-  if (warp == 0) {
-    double m = 0.0;
-    for (int i = lane; i < n; i += 32) m = fmax(m, fabs(d[i]) + fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    tfloor = 0x1p-53 * m;
-  }
-  for (int l = 0; l < n; ++l) {
-    for (int iter = 0;; ++iter) {
-      if (warp == 0) {
-        int mm = n - 1;
-        for (int base = l; base < n - 1; base += 32) {
-          const int i = base + lane;
-          bool split = false;
-          if (i < n - 1) split = fabs(e[i]) <= fmax(0x1p-53 * (fabs(d[i]) + fabs(d[i + 1])), tfloor);
-          const unsigned bal = __ballot_sync(0xffffffffu, split);
-          if (bal) { mm = base + __ffs(bal) - 1; break; }
-        }
-        if (lane == 0) {
-          int nrot = 0;
-          if (mm != l) {
-            if (iter >= kMaxIter) {
-              ctl[0] = 1;
-              mm = l;                                    // give up on this eigenvalue
-            } else {
-              double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-              double r = sqrt(fma(g, g, 1.0));
-              g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-              double s = 1.0, c = 1.0, p = 0.0;
-              bool underflow = false;
-              for (int i = mm - 1; i >= l; --i) {
-                const double ff = s * e[i];
-                const double b = c * e[i];
-                const double r2 = fma(ff, ff, g * g);
-                if (r2 > 0x1p-960 && r2 < 0x1p960) {
-                  const double ri = rsqrt(r2);
-                  r = r2 * ri;
-                  s = ff * ri;
-                  c = g * ri;
-                } else {
-                  r = hypot(ff, g);
-                  if (r == 0.0) {
-                    e[i + 1] = 0.0;
-                    d[i + 1] -= p;
-                    e[mm] = 0.0;
-                    underflow = true;
-                    break;
-                  }
-                  s = ff / r;
-                  c = g / r;
-                }
-                e[i + 1] = r;
-                g = d[i + 1] - p;
-                r = fma(d[i] - g, s, 2.0 * c * b);
-                p = s * r;
-                d[i + 1] = g + p;
-                g = fma(c, r, -b);
-                rc[nrot] = c;
-                rsn[nrot] = s;
-                ++nrot;
-              }
-              if (!underflow) {
-                d[l] -= p;
-                e[l] = g;
-                e[mm] = 0.0;
-              }
-            }
-          }
-          ctl[1] = mm;
-          ctl[2] = nrot;
-        }
-      }
-      __syncthreads();
-      const int mm = ctl[1], nrot = ctl[2];
-      // apply the recorded rotations (columns i+1, i for i = mm-1 down) to every row of Z
-      for (int row = tid; row < n; row += nth) {
-        double* zr = Z + (size_t)row * n;
-        for (int q = 0; q < nrot; ++q) {
-          const int i = mm - 1 - q;
-          const double c = rc[q], s = rsn[q];
-          const double fz = zr[i + 1];
-          zr[i + 1] = fma(s, zr[i], c * fz);
-          zr[i] = fma(c, zr[i], -s * fz);
-        }
-      }
-      __syncthreads();
-      if (mm == l) break;
-    }
-  }
+  // ---------------- 2. QL (warp 0) | Z updates (warps 1-2) | Q (warps 3-7)
+  if (warp == 0) ql_producer<kDW>(d, e, n, rc, rsn, ctl);
+  else if (warp < 3) ql_applier(Z, lda, n, rc, rsn, ctl);
+  else form_q(A, Qm, lda, n, tau, pv);
+  __syncthreads();
   if (tid == 0 && ctl[0]) atomicOr(flags, FLAG_NOTCONV);
 
-  // ---------------- 3. V = Q Z: apply H_{n-2}, ..., H_0 to Z
-  double2* vs = pv;   // s_j of one reflector
+  // ---------------- 3. V = Q Z (into A's storage)
+  double2* V = A;
   for (int idx = tid; idx < n * n; idx += nth) {
-    const int i = idx / n, k = idx - i * n;
-    Lv[idx] = (i > k) ? A[idx] : make_double2(0.0, 0.0);
+    const int i = idx / n, j = idx - i * n;
+    const double2* qr = Qm + (size_t)i * lda;
+    double sx = 0.0, sy = 0.0;
+    for (int q = 0; q < n; ++q) {
+      const double z = Z[(size_t)q * lda + j];
+      sx = fma(qr[q].x, z, sx);
+      sy = fma(qr[q].y, z, sy);
+    }
+    V[(size_t)i * lda + j] = make_double2(sx, sy);
   }
   __syncthreads();
-  for (int idx = tid; idx < n * n; idx += nth) V[idx] = make_double2(Z[idx], 0.0);
-  __syncthreads();
-  for (int k = n - 2; k >= 0; --k) {
-    const double2 t = tau[k];
-    if (t.x == 0.0 && t.y == 0.0) continue;
-    const int m = n - k - 1;
-    // s_j = v^H V[k+1:, j] ; V[k+1:, j] -= tau v s_j
-    for (int j = tid; j < n; j += nth) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int i = 0; i < m; ++i) {
-        const double2 c = cmulc(Lv[(k + 1 + i) * n + k], V[(k + 1 + i) * n + j]);
-        s.x += c.x; s.y += c.y;
-      }
-      vs[j] = cmul(t, s);
-    }
-    __syncthreads();
-    for (int idx = tid; idx < m * n; idx += nth) {
-      const int i = idx / n, j = idx - i * n;
-      const double2 c = cmul(Lv[(k + 1 + i) * n + k], vs[j]);
-      double2& vv = V[(k + 1 + i) * n + j];
-      vv.x -= c.x;
-      vv.y -= c.y;
-    }
-    __syncthreads();
-  }
 
   // ---------------- 4. sort, normalise, phase, scatter
   for (int i = tid; i < n; i += nth) {
@@ -302,19 +541,19 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
     double nrm = 0.0, best = -1.0;
     int piv = 0;
     for (int j = 0; j < n; ++j) {
-      const double2 v = V[j * n + i];
+      const double2 v = V[(size_t)j * lda + i];
       const double m2 = v.x * v.x + v.y * v.y;
       nrm += m2;
       if (m2 > best) { best = m2; piv = j; }
     }
-    const double2 pvv = V[piv * n + i];
+    const double2 pvv = V[(size_t)piv * lda + i];
     const double pm = hypot(pvv.x, pvv.y);
     const double inv = 1.0 / sqrt(nrm);
     const double2 ph = make_double2(pvv.x / pm * inv, -pvv.y / pm * inv);
     lam[(size_t)f * n + rank] = li;
     double2* out = reinterpret_cast<double2*>(psi) + (size_t)f * n * n;
     for (int j = 0; j < n; ++j) {
-      double2 v = cmul(V[j * n + i], ph);
+      double2 v = cmul(V[(size_t)j * lda + i], ph);
       if (j == piv) v.y = 0.0;
       out[j * n + rank] = v;
     }
@@ -324,21 +563,24 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
 }  // namespace
 
 size_t eig_tridiag_smem_bytes(int nb) {
-  size_t b = sizeof(double2) * (32 + 2 * (size_t)nb) + sizeof(double) * 4 * (size_t)nb + 4 * sizeof(int) + 16;
-  if (nb <= kEigSmemMaxNb) b += sizeof(double) * 5 * (size_t)nb * nb;
+  const size_t lda = (size_t)odd_stride(nb);
+  size_t b = sizeof(double2) * (32 + 3 * (size_t)nb + kThreads) + sizeof(double) * 6 * (size_t)nb +
+             8 * sizeof(int) + 16;
+  if (nb <= kEigSmemMaxNb) b += sizeof(double) * 5 * (size_t)nb * lda;
   return b;
 }
 
 size_t eig_tridiag_gws_doubles(int nb, int nf) {
-  // per frequency: A (n^2 complex) + reflector copy (n^2 complex) + Z (n^2 real)
-  return (size_t)nf * (((size_t)5 * nb * nb + 1) & ~(size_t)1);
+  // per frequency: A and Q (n x lda complex) and Z (n x lda real)
+  return (size_t)nf * (((size_t)5 * nb * odd_stride(nb) + 1) & ~(size_t)1);
 }
 
 cudaError_t launch_eig_tridiag(const spod_plan_s& p, cudaStream_t s) {
   const size_t smem = eig_tridiag_smem_bytes(p.nb);
-  cudaError_t e = cudaFuncSetAttribute(k_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = p.f64 ? k_eig_tridiag<false> : k_eig_tridiag<true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_eig_tridiag<<<p.nf, kThreads, smem, s>>>(p.d_gram, p.nb, p.d_lam, p.d_psi, p.d_eigws, p.d_flags);
+  kern<<<p.nf, kThreads, smem, s>>>(p.d_gram, p.nb, p.d_lam, p.d_psi, p.d_eigws, p.d_flags);
   return cudaGetLastError();
 }
 
