@@ -73,19 +73,24 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t_end = time.perf_counter() + 5.0           # let the sampler run before the timed region
+        while not self.rows and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons over the samples taken
+        between host times t0 and t1 (the timed region), else over all."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -94,17 +99,21 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        rows = [r for t, r in self.rows if t0 is None or t0 <= t <= t1]
+        window = "timed region"
+        if not rows:
+            rows, window = [r for _, r in self.rows], "whole run (no sample fell inside the timed region)"
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             if len(r) >= 9:
                 for i, n in enumerate(names):
                     if r[5 + i].lower().startswith("active"):
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 # --------------------------------------------------------------- oracle leg
@@ -217,7 +226,7 @@ def main():
         line["e2e"] = e2e_leg(sp, X, nmodes, args, world)
     # ---- CPU oracle on a bounded sample
     if not args.no_cpu and rank == 0 and world == 1:
-        P = 4096
+        P = 12288                   # ~10 s of oracle work on the host cores
         cols, idx = sample_columns(X, P)
         secs = oracle_sample(cols, wl.W.numpy()[idx], nmodes)
         line["cpu_baseline"] = {"value": round(NT * cols.shape[1] * elem / secs / 1e9, 5), "unit": "GB/s",
@@ -235,6 +244,7 @@ def main():
 
 DTYPE_NAME = {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "bf16x3": "bf16x3"}
 FP32_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+FP64_PEAK = 1.25                                  # TFLOP/s: nominal GB300 FP64 rate
 
 
 def max_over_ranks(x: float, dev) -> float:
@@ -284,14 +294,16 @@ def timed_run(precision, wl, steps, warmup, world, dev, clocks):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    h0 = time.perf_counter()
     e0.record(stream)
     for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    h1 = time.perf_counter()
     if world > 1:
         dist.barrier()
-    clk = sampler.stop() if sampler else None
+    clk = sampler.stop(h0, h1) if sampler else None
     ms_total = e0.elapsed_time(e1)
     phase_ms, phase_launch = _lib.spod_profile_read(sp.handle)
     _lib.spod_profile_enable(sp.handle, False)
@@ -305,12 +317,15 @@ def timed_run(precision, wl, steps, warmup, world, dev, clocks):
 # Kernel of each phase and precision (the phase timer brackets exactly these launches).
 KERNELS = {
     "mean": "k_mean_partial + k_mean_finish",
-    "fft": "k_fft_pipe",
-    "gram": {"fp32": "k_gram_simt", "fp64": "k_gram_simt", "bf16": "k_gram_tc", "bf16x3": "k_gram_tc"},
-    "reduce": "k_gram_reduce",
+    "fft": {"fp32": "k_fft_pipe", "fp64": "k_fft", "bf16": "k_fft_pipe", "bf16x3": "k_fft_pipe"},
+    "gram": {"fp32": "k_gram_simt", "fp64": "k_gram_simt", "bf16": "k_gram_tc + k_gram_tc_collect",
+             "bf16x3": "k_gram_tc + k_gram_tc_collect"},
+    "reduce": {"fp32": "k_gram_reduce", "fp64": "k_gram_reduce", "bf16": "k_gram_tc_finish",
+               "bf16x3": "k_gram_tc_finish"},
     "eig": "k_eig_tridiag",
     "modes": {"fp32": "k_mode_coeffs + k_modes_simt", "fp64": "k_mode_coeffs + k_modes_simt",
-              "bf16": "k_mode_coeffs + k_modes_tc", "bf16x3": "k_mode_coeffs + k_modes_tc"},
+              "bf16": "k_mode_coeffs + k_mode_image + k_modes_tc",
+              "bf16x3": "k_mode_coeffs + k_mode_image + k_modes_tc"},
 }
 
 
@@ -326,7 +341,8 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
     Bytes are the compulsory traffic of the kernel in this pipeline: the FFT
     reads X once and writes Qhat; the Gram reads Qhat; the modes read Qhat
     and write Phi (complex64 / complex128).  The eigensolver is reported
-    against the FP64 rate it is limited by (no HBM traffic to speak of)."""
+    against the nominal FP64 rate (no HBM traffic to speak of; it is bound by
+    the latency of its dependent FP64 / double-FP32 chains, not by that rate)."""
     hbm = peaks.get("hbm_gbs", 6800.0)
     src = "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
     t = per_launch_ms * 1e-3
@@ -345,7 +361,7 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
             flops = 4.0 * nf * nb * (nb + 1) * M            # Hermitian half of Q^H W Q, 8 flops per complex MAC
             ach = flops / t / 1e12
             return {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(FP32_PEAK, 1),
-                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": None,
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": TRAFFIC.get((phase, precision)),
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "ms": round(per_launch_ms, 4)}
         byts = q
     elif phase == "modes":
@@ -353,20 +369,35 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
             flops = 8.0 * nf * nb * nmodes * M
             ach = flops / t / 1e12
             return {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(FP32_PEAK, 1),
-                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": None,
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": TRAFFIC.get((phase, precision)),
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "ms": round(per_launch_ms, 4)}
         byts = q + phi
+    elif phase == "eig":
+        # Householder 16/3 n^3, Q formation 16/3 n^3, V = Q Z 4 n^3, Z rotations ~6 n^3 (real flops)
+        flops = (16.0 / 3 + 16.0 / 3 + 4.0 + 6.0) * nb ** 3 * nf
+        ach = flops / t / 1e12
+        return {"bound": "alu", "kernel": kern, "achieved": round(ach, 4), "peak": FP64_PEAK,
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK, 4), "traffic": None,
+                "peak_source": "nominal GB300 FP64 rate (latency-bound kernel)", "ms": round(per_launch_ms, 4)}
     else:
         byts = nf * nb * nb * 16
     ach = byts / t / 1e9
     return {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get((kern, precision)), "peak_source": src + " (burst)",
+            "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get((phase, precision)), "peak_source": src + " (burst)",
             "bytes_per_launch": int(byts), "ms": round(per_launch_ms, 4)}
 
 
-# DRAM bytes (read + write) per launch from an ncu capture, scaled to the full
-# workload; None until captured for the current kernel version.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of a phase's main kernel from one ncu
+# capture on the 64 x 64 x 3 grid (M = 12 288, same nt / nfft), scaled by the
+# points processed (x 32) to the full grid; the summaries are in profiles/.
+# Absent entries: no capture of the current kernel version.
+TRAFFIC = {
+    ("fft", "bf16x3"): int((490.987776 + 909.537536) * 1e6 * 32),    # k_fft_pipe<float, 1, 512>
+    ("gram", "bf16x3"): int((960.324864 + 19.772928) * 1e6 * 32),    # k_gram_tc<1, 40>
+    ("modes", "bf16x3"): int((976.955392 + 907.371776) * 1e6 * 32),  # k_modes_tc<1>
+    ("gram", "fp32"): int((961.233 + 25.105920) * 1e6 * 32),         # k_gram_simt<float>
+    ("modes", "fp32"): int((1016.175 + 920.394496) * 1e6 * 32),      # k_modes_simt<float, 16>
+}
 
 
 def step_roofline(ms_step, M, nb, nf, nmodes, peaks, precision):
