@@ -1,8 +1,13 @@
 // Persistent block DFT (Eqs. blocks, blocks-ft, blocks-k) for the nfft values
 // with a compiled radix sequence (256, 384, 512, 720).
 //
-// Two CTAs of 256 threads per SM walk tiles of 16 spatial points; each CTA
-// transforms the Welch blocks l = 0 .. nb-1 of its tile in order.  The tile's
+// Persistent CTAs walk tiles of TP spatial points (TP = 32: one 512-thread CTA
+// per SM; TP = 16: two 256-thread CTAs per SM, for nfft = 720 and FP64 input,
+// whose rings do not fit twice); each CTA transforms the Welch blocks
+// l = 0 .. nb-1 of its tile in order.  The wider tile halves the number of
+// 128-byte lines per stored byte in the output phase (a line of the BF16
+// blocked layout holds 64 points of one row) and makes every TMA ring row a
+// full 128-byte line.  The tile's
 // time rows arrive by TMA into a ring of exactly nfft rows: block 0 loads
 // nfft rows, each later block only its step new rows, written over the rows
 // the previous block no longer needs, so every sample of X is read from HBM
@@ -30,10 +35,16 @@ namespace {
 
 using namespace fft;
 
-constexpr int PTP = 16;               // points per tile
-constexpr int PC = PTP / 2;           // complex columns (point pairs)
-constexpr int PTHREADS = 256;
-constexpr int PBSTEP = PTHREADS / PC; // butterflies between a thread's consecutive ones
+// Tile geometry: TP points, TP/2 complex columns, 16 threads per point.
+template <int TP>
+struct Geo {
+  static constexpr int PTP = TP;                   // points per tile
+  static constexpr int PC = TP / 2;                // complex columns (point pairs)
+  static constexpr int THREADS = 16 * TP;
+  static constexpr int BSTEP = THREADS / PC;       // butterflies between a thread's consecutive ones (32)
+  static constexpr int OUTCP = PC / 2;             // column pairs per tile
+  static constexpr int OUTFSTEP = THREADS / OUTCP; // bins between a thread's consecutive ones (64)
+};
 
 struct PipeArgs {
   int64_t m0, mcount, chunk, ntiles;
@@ -64,10 +75,11 @@ template <> struct PairLoad<double> {
 
 // Pass 0 (Ns = 1, no twiddles): butterfly inputs come from the ring rows of
 // the current block with the mean removed and the window applied.
-template <typename Tin, int N, int RAD>
+template <typename Tin, int TP, int N, int RAD>
 __device__ __forceinline__ void pass_first(const Tin* __restrict__ ring, int rb, float2* __restrict__ dst,
                                            const float* __restrict__ wsm, float mhi0, float mlo0, float mhi1,
                                            float mlo1) {
+  constexpr int PTP = Geo<TP>::PTP, PC = Geo<TP>::PC, PBSTEP = Geo<TP>::BSTEP;
   constexpr int nbut = N / RAD;
   constexpr int MAXB = (nbut + PBSTEP - 1) / PBSTEP;
   const int col = threadIdx.x % PC;
@@ -100,9 +112,10 @@ __device__ __forceinline__ void pass_first(const Tin* __restrict__ ring, int rb,
 }
 
 // Out-of-place Stockham pass with compile-time radix and stride.
-template <int N, int RAD, int NS>
+template <int TP, int N, int RAD, int NS>
 __device__ __forceinline__ void pass_oop(const float2* __restrict__ src, float2* __restrict__ dst,
                                          const float2* __restrict__ tw) {
+  constexpr int PC = Geo<TP>::PC, PBSTEP = Geo<TP>::BSTEP;
   constexpr int nbut = N / RAD;
   constexpr int MAXB = (nbut + PBSTEP - 1) / PBSTEP;
   constexpr int stw = N / (NS * RAD);
@@ -141,12 +154,12 @@ __device__ __forceinline__ void pass_oop(const float2* __restrict__ src, float2*
 
 // Passes 1 .. P-1, each followed by a barrier; returns the buffer holding
 // the spectrum.
-template <int N, int NS, int R0, int... RS>
+template <int TP, int N, int NS, int R0, int... RS>
 __device__ __forceinline__ const float2* run_rest(float2* src, float2* dst, const float2* tw) {
-  pass_oop<N, R0, NS>(src, dst, tw);
+  pass_oop<TP, N, R0, NS>(src, dst, tw);
   __syncthreads();
   if constexpr (sizeof...(RS) > 0) {
-    return run_rest<N, NS * R0, RS...>(dst, src, tw);
+    return run_rest<TP, N, NS * R0, RS...>(dst, src, tw);
   } else {
     return dst;
   }
@@ -156,26 +169,30 @@ __device__ __forceinline__ const float2* run_rest(float2* src, float2* dst, cons
 template <int N> struct PSeq;
 template <> struct PSeq<256> {
   static constexpr int R0 = 8, P = 3;
+  template <int TP>
   static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
-    return run_rest<256, 8, 8, 4>(a, b, t);
+    return run_rest<TP, 256, 8, 8, 4>(a, b, t);
   }
 };
 template <> struct PSeq<384> {
   static constexpr int R0 = 8, P = 4;
+  template <int TP>
   static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
-    return run_rest<384, 8, 8, 2, 3>(a, b, t);
+    return run_rest<TP, 384, 8, 8, 2, 3>(a, b, t);
   }
 };
 template <> struct PSeq<512> {
   static constexpr int R0 = 8, P = 3;
+  template <int TP>
   static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
-    return run_rest<512, 8, 8, 8>(a, b, t);
+    return run_rest<TP, 512, 8, 8, 8>(a, b, t);
   }
 };
 template <> struct PSeq<720> {
   static constexpr int R0 = 8, P = 5;
+  template <int TP>
   static __device__ __forceinline__ const float2* rest(float2* a, float2* b, const float2* t) {
-    return run_rest<720, 8, 2, 3, 3, 5>(a, b, t);
+    return run_rest<TP, 720, 8, 2, 3, 3, 5>(a, b, t);
   }
 };
 
@@ -184,9 +201,6 @@ template <> struct PSeq<720> {
 // the 1/2) and store rows re = l and im = nb + l of every frequency.  A thread
 // takes two adjacent columns (four points): 16-byte shared loads, and one
 // 16-byte (FP32) or 8-byte (BF16) store per output plane and frequency.
-constexpr int kOutCp = PC / 2;                 // column pairs per tile
-constexpr int kOutFStep = PTHREADS / kOutCp;   // frequencies between a thread's consecutive ones
-
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -194,10 +208,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 __device__ __forceinline__ float bf16_lo_f(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-template <int OUTK, int N>
+template <int OUTK, int TP, int N>
 __device__ __forceinline__ void output_phase(const float2* __restrict__ src, const PipeArgs& a, int l,
                                              int64_t lm0, const float (&sw)[4], void* __restrict__ qout,
                                              void* __restrict__ qlo) {
+  constexpr int kOutCp = Geo<TP>::OUTCP, kOutFStep = Geo<TP>::OUTFSTEP;
   const int cp = threadIdx.x % kOutCp;
   const int f0 = threadIdx.x / kOutCp;
   // FP32 planes are planar [nf][2 nb][chunk]; BF16 planes are blocked by 64
@@ -247,24 +262,24 @@ __device__ __forceinline__ void output_phase(const float2* __restrict__ src, con
 }
 
 // Shared-memory layout (bytes from the 1024-aligned base).
-template <typename Tin, int N>
+template <typename Tin, int TP, int N>
 struct PipeLayout {
   static constexpr size_t hdr = 0;
   static constexpr size_t ring = 128;
-  static constexpr size_t buf0 = ring + (size_t)N * PTP * sizeof(Tin);
-  static constexpr size_t buf1 = buf0 + (size_t)N * PC * sizeof(float2);
-  static constexpr size_t tw = buf1 + (size_t)N * PC * sizeof(float2);
+  static constexpr size_t buf0 = ring + (size_t)N * TP * sizeof(Tin);
+  static constexpr size_t buf1 = buf0 + (size_t)N * (TP / 2) * sizeof(float2);
+  static constexpr size_t tw = buf1 + (size_t)N * (TP / 2) * sizeof(float2);
   static constexpr size_t win = tw + (size_t)N * sizeof(float2);
   static constexpr size_t end = win + (size_t)N * sizeof(float);
   static constexpr size_t dyn = end + 1024;                    // alignment slack
 };
 
-// two CTAs per SM up to nfft = 512 (shared memory allows it); larger
-// transforms get the whole register file
-template <int N> constexpr int pipe_min_blocks() { return N <= 512 ? 2 : 1; }
+// 16-point tiles: two CTAs per SM up to nfft = 512 (shared memory allows it);
+// otherwise one CTA gets the whole register file
+template <int TP, int N> constexpr int pipe_min_blocks() { return TP == 16 && N <= 512 ? 2 : 1; }
 
-template <typename Tin, int OUTK, int N>
-__global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(const __grid_constant__ CUtensorMap xmap,
+template <typename Tin, int OUTK, int TP, int N>
+__global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_fft_pipe(const __grid_constant__ CUtensorMap xmap,
                                                           const float* __restrict__ win,
                                                           const float2* __restrict__ tw_g,
                                                           const float* __restrict__ sqrtW,
@@ -272,8 +287,9 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
                                                           void* __restrict__ qlo, PipeArgs a,
                                                           unsigned* __restrict__ gflags) {
   using namespace tc;
-  using L = PipeLayout<Tin, N>;
+  using L = PipeLayout<Tin, TP, N>;
   using S = PSeq<N>;
+  constexpr int PTP = Geo<TP>::PTP, PC = Geo<TP>::PC, PTHREADS = Geo<TP>::THREADS;
   extern __shared__ unsigned char smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   PipeHdr* hdr = reinterpret_cast<PipeHdr*>(sm + L::hdr);
@@ -330,7 +346,7 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
       if (a.subtract_mean && lm + 1 < a.mcount) {
         const double d = mu[gm0 + 2 * col + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
       }
-      const int cp = tid % kOutCp;
+      const int cp = tid % Geo<TP>::OUTCP;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         sw[q] = (lm0 + 4 * cp + q < a.mcount) ? 0.5f * sqrtW[gm0 + 4 * cp + q] : 0.f;
@@ -341,7 +357,7 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
       ++phase;
       float2* bA = par ? buf1 : buf0;
       float2* bB = par ? buf0 : buf1;
-      pass_first<Tin, N, S::R0>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1);
+      pass_first<Tin, TP, N, S::R0>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1);
       __syncthreads();
       if (hdr->abort) break;
       // the ring rows of this block are consumed: request the next rows
@@ -352,8 +368,8 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
           issue(t + t_step, 0, N);
         }
       }
-      const float2* spec = S::rest(bA, bB, tw);
-      output_phase<OUTK, N>(spec, a, l, lm0, sw, qout, qlo);
+      const float2* spec = S::template rest<TP>(bA, bB, tw);
+      output_phase<OUTK, TP, N>(spec, a, l, lm0, sw, qout, qlo);
       rb += a.step;
       if (rb >= N) rb -= N;
       par ^= (S::P & 1);
@@ -364,18 +380,19 @@ __global__ void __launch_bounds__(PTHREADS, pipe_min_blocks<N>()) k_fft_pipe(con
   if (tid == 0 && !last_ok) mbar_drain(bar, (phase - 1) & 1, gflags);
 }
 
-template <typename Tin, int OUTK, int N>
+template <typename Tin, int OUTK, int TP, int N>
 cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
+  constexpr int PTHREADS = Geo<TP>::THREADS;
   PipeArgs a;
   a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
   const int64_t mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
-  a.ntiles = mpad / PTP;
+  a.ntiles = mpad / TP;
   a.step = p.step; a.nb = p.nb; a.nf = p.nf;
   a.boxr = p.ring_boxr;
   a.subtract_mean = p.desc.subtract_mean;
-  const size_t smem = PipeLayout<Tin, N>::dyn;
-  auto kern = k_fft_pipe<Tin, OUTK, N>;
+  const size_t smem = PipeLayout<Tin, TP, N>::dyn;
+  auto kern = k_fft_pipe<Tin, OUTK, TP, N>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
@@ -391,11 +408,22 @@ cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
 template <typename Tin, int OUTK>
 cudaError_t launch_pipe_t(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
+  if constexpr (sizeof(Tin) <= 4) {
+    if (p.pipe_tp == 32) {
+      switch (p.nfft) {
+        case 256: return launch_pipe_n<Tin, OUTK, 32, 256>(p, xmap, m0, mcount, s);
+        case 384: return launch_pipe_n<Tin, OUTK, 32, 384>(p, xmap, m0, mcount, s);
+        case 512: return launch_pipe_n<Tin, OUTK, 32, 512>(p, xmap, m0, mcount, s);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
+  if (p.pipe_tp != 16) return cudaErrorInvalidValue;
   switch (p.nfft) {
-    case 256: return launch_pipe_n<Tin, OUTK, 256>(p, xmap, m0, mcount, s);
-    case 384: return launch_pipe_n<Tin, OUTK, 384>(p, xmap, m0, mcount, s);
-    case 512: return launch_pipe_n<Tin, OUTK, 512>(p, xmap, m0, mcount, s);
-    default: return launch_pipe_n<Tin, OUTK, 720>(p, xmap, m0, mcount, s);
+    case 256: return launch_pipe_n<Tin, OUTK, 16, 256>(p, xmap, m0, mcount, s);
+    case 384: return launch_pipe_n<Tin, OUTK, 16, 384>(p, xmap, m0, mcount, s);
+    case 512: return launch_pipe_n<Tin, OUTK, 16, 512>(p, xmap, m0, mcount, s);
+    default: return launch_pipe_n<Tin, OUTK, 16, 720>(p, xmap, m0, mcount, s);
   }
 }
 
@@ -407,24 +435,42 @@ cudaError_t launch_pipe_in(const spod_plan_s& p, const CUtensorMap& xmap, int64_
   return launch_pipe_t<Tin, OUT_NATIVE>(p, xmap, m0, mcount, s);
 }
 
-template <typename Tin>
+template <typename Tin, int TP>
 size_t pipe_smem_t(int nfft) {
   switch (nfft) {
-    case 256: return PipeLayout<Tin, 256>::dyn;
-    case 384: return PipeLayout<Tin, 384>::dyn;
-    case 512: return PipeLayout<Tin, 512>::dyn;
-    case 720: return PipeLayout<Tin, 720>::dyn;
+    case 256: return PipeLayout<Tin, TP, 256>::dyn;
+    case 384: return PipeLayout<Tin, TP, 384>::dyn;
+    case 512: return PipeLayout<Tin, TP, 512>::dyn;
+    case 720:
+      if constexpr (TP == 16) return PipeLayout<Tin, TP, 720>::dyn;
+      return 0;
     default: return 0;
   }
+}
+template <typename Tin>
+size_t pipe_smem_tp(int nfft, int tp) {
+  if (tp == 32) {
+    if constexpr (sizeof(Tin) <= 4) return pipe_smem_t<Tin, 32>(nfft);
+    return 0;
+  }
+  return tp == 16 ? pipe_smem_t<Tin, 16>(nfft) : 0;
 }
 
 }  // namespace
 
-// Dynamic shared memory of the pipelined kernel, 0 when nfft has no compiled sequence.
-size_t fft_pipe_smem_bytes(const spod_plan_s& p) {
-  if (p.desc.in_dtype == SPOD_F64) return pipe_smem_t<double>(p.nfft);
-  if (p.desc.in_dtype == SPOD_F32) return pipe_smem_t<float>(p.nfft);
-  return pipe_smem_t<__nv_bfloat16>(p.nfft);
+// Dynamic shared memory of the pipelined kernel with tp-point tiles, 0 when
+// nfft (or the input type) has no compiled form for that tile.
+size_t fft_pipe_smem_bytes(const spod_plan_s& p, int tp) {
+  if (p.desc.in_dtype == SPOD_F64) return pipe_smem_tp<double>(p.nfft, tp);
+  if (p.desc.in_dtype == SPOD_F32) return pipe_smem_tp<float>(p.nfft, tp);
+  return pipe_smem_tp<__nv_bfloat16>(p.nfft, tp);
+}
+
+// Tile width of the pipelined kernel: 32 points when that form exists and
+// fits in shared memory, else 16.
+int fft_pipe_tile(const spod_plan_s& p, int smem_optin) {
+  const size_t s32 = fft_pipe_smem_bytes(p, 32);
+  return s32 > 0 && s32 <= (size_t)smem_optin ? 32 : 16;
 }
 
 bool fft_pipe_usable(const spod_plan_s& p, int smem_optin) {
@@ -432,7 +478,7 @@ bool fft_pipe_usable(const spod_plan_s& p, int smem_optin) {
   const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
   if ((p.M * (int64_t)el) % 16 != 0) return false;          // TMA row stride
   if (p.nfft % p.ring_boxr != 0 || p.step % p.ring_boxr != 0) return false;
-  const size_t smem = fft_pipe_smem_bytes(p);
+  const size_t smem = fft_pipe_smem_bytes(p, p.pipe_tp);
   return smem > 0 && smem <= (size_t)smem_optin;
 }
 

@@ -130,7 +130,7 @@ void* driver_encode_fn() {
   return fn;
 }
 
-// TMA map of X for the ring FFT: dims {M, nt}, box {16 points, ring_boxr rows}.
+// TMA map of X for the ring FFTs: dims {M, nt}, box {tile points, ring_boxr rows}.
 spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
   if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available");
@@ -140,7 +140,7 @@ spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) 
                                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const cuuint64_t dims[2] = {(cuuint64_t)p->M, (cuuint64_t)p->nt};
   const cuuint64_t strides[1] = {(cuuint64_t)p->M * el};
-  const cuuint32_t box[2] = {16, (cuuint32_t)p->ring_boxr};
+  const cuuint32_t box[2] = {(cuuint32_t)(p->pipe_ok ? p->pipe_tp : 16), (cuuint32_t)p->ring_boxr};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, dt, 2, const_cast<void*>(d_X), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -435,6 +435,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   {
     cudaDeviceProp prop2;
     const bool q = p->encode_fn && cudaGetDeviceProperties(&prop2, p->device) == cudaSuccess;
+    if (q) p->pipe_tp = fft_pipe_tile(*p, (int)prop2.sharedMemPerBlockOptin);
     p->pipe_ok = q && fft_pipe_usable(*p, (int)prop2.sharedMemPerBlockOptin);
     p->ring_ok = p->pipe_ok || (q && fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin));
   }

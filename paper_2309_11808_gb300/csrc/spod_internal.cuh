@@ -76,6 +76,7 @@ struct spod_plan_s {
   int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
   bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
   bool pipe_ok = false;       // the pipelined kernel (compiled nfft) is used
+  int pipe_tp = 16;           // its tile width in points (16 or 32; also the X map's box width)
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   int num_sms = 0;
 
@@ -170,8 +171,9 @@ size_t fft_ring_smem_bytes(const spod_plan_s& p);
 size_t fft_ring_stage_offset(const spod_plan_s& p);
 size_t fft_ring_plane_elems(const spod_plan_s& p);
 bool fft_ring_usable(const spod_plan_s& p, int smem_optin);
-size_t fft_pipe_smem_bytes(const spod_plan_s& p);
+size_t fft_pipe_smem_bytes(const spod_plan_s& p, int tp);
 bool fft_pipe_usable(const spod_plan_s& p, int smem_optin);
+int fft_pipe_tile(const spod_plan_s& p, int smem_optin);
 cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                                   cudaStream_t s);
 cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
