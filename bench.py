@@ -205,6 +205,12 @@ def main():
             "phase_rooflines": per_phase,
             "gpu_launches": int(sum(phase_launch.values())), "clocks": clk,
             "snapshots_per_s": round(world * NT / (ms_step * 1e-3), 1)}
+    # fit alone (mean, FFT, Gram, reduction, eigen-solve: the phase events of
+    # spod_fit, which runs its phases back to back on one stream)
+    fit_ms = sum(phase_ms[k] for k in ("mean", "fft", "gram", "reduce", "eig")) / args.steps
+    line["fit_only"] = {"ms_per_step": round(fit_ms, 4),
+                        "value": round(world * bytes_step / (fit_ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+                        "snapshots_per_s": round(world * NT / (fit_ms * 1e-3), 1)}
 
     # ---- the plain FP32 GPU form on the same input (the comparison the metric names)
     if args.precision != "fp32" and not args.no_compare:
