@@ -232,7 +232,7 @@ def main():
         line["e2e"] = e2e_leg(sp, X, nmodes, args, world)
     # ---- CPU oracle on a bounded sample
     if not args.no_cpu and rank == 0 and world == 1:
-        P = 12288                   # ~10 s of oracle work on the host cores
+        P = 24576                   # ~10 s of oracle work on the host cores
         cols, idx = sample_columns(X, P)
         secs = oracle_sample(cols, wl.W.numpy()[idx], nmodes)
         line["cpu_baseline"] = {"value": round(NT * cols.shape[1] * elem / secs / 1e9, 5), "unit": "GB/s",
