@@ -186,9 +186,21 @@ spod_status spod_backward(spod_plan_t plan, const double* d_dLdlambda, const voi
  * nmodes modes (0 = none) and copies eigenvalues (h_lambda[nf][nb], may be
  * NULL) and modes (h_Phi, layout as spod_modes, may be NULL when nmodes = 0)
  * back.  Device staging buffers are owned by the plan and kept for reuse.
- * Pinned host memory gives the fastest copies.  Synchronises the stream. */
-spod_status spod_run_host(spod_plan_t plan, const void* h_X, int nmodes, void* h_Phi,
-                          double* h_lambda, void* stream);
+ * The modes are computed in frequency ranges and each range is copied back
+ * (Phi is frequency-major, so a range is contiguous) while the next one is
+ * computed, on a plan-owned copy stream.  Pinned host memory gives the
+ * fastest copies.  Synchronises the stream.  No counterpart in the paper. */
+spod_status spod_run_host(spod_plan_t plan, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
+                          void* stream);
+
+/* spod_run_host over n datasets of the plan's shape (h_X[i], h_Phi[i],
+ * h_lambda[i]; h_lambda may be NULL, or hold NULL entries), processed in
+ * order with two staging pairs used in turn: dataset i + 1's X is copied up
+ * on one copy stream while dataset i's modes are copied down on another (the
+ * host link carries both directions at once).  Results equal n spod_run_host
+ * calls.  SPOD_EINVAL for n < 1 or a NULL buffer; synchronises the stream. */
+spod_status spod_run_host_many(spod_plan_t plan, int n, const void* const* h_X, int nmodes, void* const* h_Phi,
+                               double* const* h_lambda, void* stream);
 
 /* Wait for the plan's work on `stream` and report device-side conditions. */
 spod_status spod_sync(spod_plan_t plan, void* stream);

@@ -24,9 +24,9 @@ STATUS_NAMES = {0: "SPOD_OK", 1: "SPOD_EINVAL", 2: "SPOD_ENOMEM", 3: "SPOD_ECUDA
 # every symbol include/spod.h declares
 EXPORTED = ["spod_desc_init", "spod_plan_create", "spod_plan_destroy", "spod_plan_get_info", "spod_fit",
             "spod_get_eigs", "spod_get_gram", "spod_get_freqs", "spod_modes", "spod_backward",
-            "spod_run_host", "spod_sync", "spod_fit_batch", "spod_profile_enable", "spod_profile_read",
-            "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning", "spod_plan_autotune",
-            "spod_last_error", "spod_version"]
+            "spod_run_host", "spod_run_host_many", "spod_sync", "spod_fit_batch", "spod_profile_enable",
+            "spod_profile_read", "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning",
+            "spod_plan_autotune", "spod_last_error", "spod_version"]
 
 PHASES = ["mean", "fft", "gram", "reduce", "eig", "modes", "backward"]
 
@@ -79,6 +79,7 @@ def lib() -> C.CDLL:
         L.spod_modes.argtypes = [P, P, C.c_int, P, P]
         L.spod_backward.argtypes = [P, P, P, P, P]
         L.spod_run_host.argtypes = [P, P, C.c_int, P, P, P]
+        L.spod_run_host_many.argtypes = [P, C.c_int, C.POINTER(P), C.c_int, C.POINTER(P), C.POINTER(P), P]
         L.spod_sync.argtypes = [P, P]
         L.spod_fit_batch.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, P]
         L.spod_profile_enable.argtypes = [P, C.c_int]
@@ -171,6 +172,15 @@ def spod_backward(plan: int, dLdlam, X, dX, stream=None) -> None:
 def spod_run_host(plan: int, hX, nmodes: int, hPhi, hlam, stream=None) -> None:
     check(lib().spod_run_host(plan, _ptr(hX), int(nmodes), _ptr(hPhi), _ptr(hlam), _stream(stream)),
           "spod_run_host")
+
+
+def spod_run_host_many(plan: int, hXs, nmodes: int, hPhis, hlams=None, stream=None) -> None:
+    n = len(hXs)
+    arr_x = (C.c_void_p * n)(*[_ptr(x) for x in hXs])
+    arr_p = (C.c_void_p * n)(*[_ptr(x) for x in hPhis]) if hPhis is not None else None
+    arr_l = (C.c_void_p * n)(*[_ptr(x) for x in hlams]) if hlams is not None else None
+    check(lib().spod_run_host_many(plan, n, arr_x, int(nmodes), arr_p, arr_l, _stream(stream)),
+          "spod_run_host_many")
 
 
 def spod_sync(plan: int, stream=None) -> None:

@@ -215,9 +215,9 @@ template <typename R, int KG>
 __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, int64_t rs, int nb, int nmodes,
                                                     int nmp, int64_t mcount, int64_t m0, int64_t M,
                                                     const R* __restrict__ bmat, const R* __restrict__ scale,
-                                                    R* __restrict__ phi) {
+                                                    R* __restrict__ phi, int f0) {
   using V2 = typename Cplx<R>::T;
-  const int f = blockIdx.y;
+  const int f = f0 + blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V2* sB = reinterpret_cast<V2*>(smem_raw);                       // [nb][nmp]
   const V2* Bf = reinterpret_cast<const V2*>(bmat) + (size_t)f * nb * nmodes;
@@ -315,7 +315,7 @@ cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s)
 
 template <typename R>
 static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, int* nlaunch, bool adjoint) {
+                                  cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1) {
   constexpr int KG = sizeof(R) == 8 ? 8 : 16;
   const int nmp = (nmodes + KG - 1) / KG * KG;
   const size_t smem = sizeof(typename Cplx<R>::T) * (size_t)p.nb * nmp;
@@ -323,10 +323,11 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   constexpr int threads = 128;
-  dim3 grid((unsigned)((mcount + 2 * threads - 1) / (2 * threads)), (unsigned)p.nf);
+  dim3 grid((unsigned)((mcount + 2 * threads - 1) / (2 * threads)), (unsigned)(f1 - f0));
   kern<<<grid, threads, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, nmodes, nmp, mcount, m0,
                                    p.M, static_cast<const R*>(p.d_bmat),
-                                   static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW), static_cast<R*>(d_Phi));
+                                   static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW), static_cast<R*>(d_Phi),
+                                   f0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nlaunch;
@@ -334,9 +335,11 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
 }
 
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                               cudaStream_t s, int* nlaunch, bool adjoint) {
-  return p.f64 ? launch_modes_t<double>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint)
-               : launch_modes_t<float>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint);
+                               cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1) {
+  if (f1 < 0) f1 = p.nf;
+  if (f0 < 0 || f1 > p.nf || f0 >= f1) return cudaErrorInvalidValue;
+  return p.f64 ? launch_modes_t<double>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint, f0, f1)
+               : launch_modes_t<float>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint, f0, f1);
 }
 
 }  // namespace spod

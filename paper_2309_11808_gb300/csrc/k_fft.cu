@@ -25,9 +25,10 @@ using namespace fft;
 // ---------------------------------------------------------------- mean
 template <typename Tin>
 __global__ void __launch_bounds__(256) k_mean_partial(const Tin* __restrict__ X, int64_t M, int64_t nt,
-                                                      int64_t tper, double* __restrict__ part) {
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
+                                                      int64_t tper, int64_t m0, int64_t m1,
+                                                      double* __restrict__ part) {
+  const int64_t m = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= m1) return;
   const int64_t t0 = (int64_t)blockIdx.y * tper;
   const int64_t t1 = min(nt, t0 + tper);
   double acc = 0.0;
@@ -48,10 +49,10 @@ __global__ void __launch_bounds__(256) k_mean_partial(const Tin* __restrict__ X,
   part[(int64_t)blockIdx.y * M + m] = acc;
 }
 
-__global__ void k_mean_finish(const double* __restrict__ part, int splits, int64_t M, double inv_nt,
-                              double* __restrict__ mu) {
-  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
+__global__ void k_mean_finish(const double* __restrict__ part, int splits, int64_t M, int64_t m0, int64_t m1,
+                              double inv_nt, double* __restrict__ mu) {
+  const int64_t m = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= m1) return;
   double s = 0.0;
   for (int i = 0; i < splits; ++i) s += part[(int64_t)i * M + m];
   mu[m] = s * inv_nt;
@@ -196,14 +197,15 @@ cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int6
 }
 
 template <typename Tin>
-cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, cudaStream_t s) {
+cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
   const int64_t tper = (p.nt + p.mean_splits - 1) / p.mean_splits;
-  dim3 grid((unsigned)((p.M + 255) / 256), (unsigned)p.mean_splits);
-  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), p.M, p.nt, tper, p.d_mupart);
+  dim3 grid((unsigned)((mcount + 255) / 256), (unsigned)p.mean_splits);
+  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), p.M, p.nt, tper, m0, m0 + mcount,
+                                           p.d_mupart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_mean_finish<<<(unsigned)((p.M + 255) / 256), 256, 0, s>>>(p.d_mupart, p.mean_splits, p.M,
-                                                               1.0 / (double)p.nt, p.d_mu);
+  k_mean_finish<<<(unsigned)((mcount + 255) / 256), 256, 0, s>>>(p.d_mupart, p.mean_splits, p.M, m0, m0 + mcount,
+                                                                  1.0 / (double)p.nt, p.d_mu);
   return cudaGetLastError();
 }
 
@@ -215,11 +217,12 @@ size_t fft_smem_bytes(const spod_plan_s& p) {
   return vb * ((size_t)p.nfft * C * 2 + (size_t)p.nfft);
 }
 
-cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, cudaStream_t s) {
+cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
+  if (mcount <= 0) return cudaSuccess;
   switch (p.desc.in_dtype) {
-    case SPOD_F64: return launch_mean_t<double>(p, d_X, s);
-    case SPOD_F32: return launch_mean_t<float>(p, d_X, s);
-    default: return launch_mean_t<__nv_bfloat16>(p, d_X, s);
+    case SPOD_F64: return launch_mean_t<double>(p, d_X, m0, mcount, s);
+    case SPOD_F32: return launch_mean_t<float>(p, d_X, m0, mcount, s);
+    default: return launch_mean_t<__nv_bfloat16>(p, d_X, m0, mcount, s);
   }
 }
 

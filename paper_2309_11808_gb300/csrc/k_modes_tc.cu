@@ -40,7 +40,8 @@ struct ModesTcArgs {
   int nb, nmodes, np, nn, nf;             // np = K (2 nb padded to 16), nn = N (2 nmodes padded to 16)
   int64_t mcount, m0, M;
   int64_t ntp;                             // 128-point tiles per frequency
-  int64_t nitems;                          // nf * ntp
+  int64_t nitems;                          // (f1 - f0) * ntp
+  int f0;                                  // first frequency of the call's range
   uint32_t box_bytes;                      // one Qhat TMA box: np rows x 128 bytes
   uint32_t img_bytes;                      // one B image (hi or lo)
   int nst;                                 // pipeline stages (2 .. kMaxStages)
@@ -109,9 +110,10 @@ __global__ void k_mode_image(const float* __restrict__ bmat, int nb, int nm, int
 struct Cursor {
   int f, tp;          // frequency, 128-point tile within it
   int s, ph;          // stage, parity of the ring pass (i / nst) & 1
-  __device__ __forceinline__ void init(int64_t item0, int ntp) {
-    f = (int)(item0 / ntp);
-    tp = (int)(item0 - (int64_t)f * ntp);
+  __device__ __forceinline__ void init(int64_t item0, int ntp, int f0) {
+    const int fr = (int)(item0 / ntp);
+    tp = (int)(item0 - (int64_t)fr * ntp);
+    f = f0 + fr;
     s = 0;
     ph = 0;
   }
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     int issued = 0, seg = 0, segs_loaded = 0;
     int fcur = -1;
     Cursor cu;
-    cu.init(i0, ntp);
+    cu.init(i0, ntp, a.f0);
     for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
       const int f = cu.f, tp = cu.tp;
       if (f != fcur) {
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     int seg = 0;
     int fcur = -1;
     Cursor cu;
-    cu.init(i0, ntp);
+    cu.init(i0, ntp, a.f0);
     for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
       const int f = cu.f;
       if (f != fcur) {
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     const int k0 = half * (hcols / 2);              // first mode of this warp
     const int nm = a.nmodes;
     Cursor cu;
-    cu.init(i0, ntp);
+    cu.init(i0, ntp, a.f0);
     for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
       const int f = cu.f, tp = cu.tp;
       const int acc = i & 1;
@@ -321,7 +323,9 @@ cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s) 
 }
 
 cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, bool adjoint) {
+                                  cudaStream_t s, bool adjoint, int f0, int f1) {
+  if (f1 < 0) f1 = p.nf;
+  if (f0 < 0 || f1 > p.nf || f0 >= f1) return cudaErrorInvalidValue;
   const float* scale = static_cast<const float*>(adjoint ? p.d_sqrtW : p.d_rsqrtW);
   ModesTcArgs a;
   a.nb = p.nb;
@@ -333,7 +337,8 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
   a.m0 = m0;
   a.M = p.M;
   a.ntp = (mcount + 127) / 128;
-  a.nitems = a.ntp * p.nf;
+  a.nitems = a.ntp * (f1 - f0);
+  a.f0 = f0;
   a.box_bytes = (uint32_t)a.np * 128u;
   a.img_bytes = modes_img_bytes(a.np, a.nn);
   const int sms = p.num_sms > 0 ? p.num_sms : 148;

@@ -512,6 +512,12 @@ spod_status spod_plan_destroy(spod_plan_t p) {
     if (p->d_radj) cudaFree(p->d_radj);
     for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : p->ev_free) cudaEventDestroy(e);
+    if (p->d_xstage2) cudaFree(p->d_xstage2);
+    if (p->d_lamstage) cudaFree(p->d_lamstage);
+    if (p->d_phistage2) cudaFree(p->d_phistage2);
+    for (auto e : p->host_ev) cudaEventDestroy(e);
+    if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
+    if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
   }
   delete p;
   return SPOD_OK;
@@ -539,21 +545,14 @@ static spod_status check_ptr(const void* ptr, const char* what) {
   return SPOD_OK;
 }
 
-spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
-  if (spod_status st = check_plan(p)) return st;
-  if (spod_status st = check_ptr(d_X, "d_X")) return st;
-  DeviceGuard g(p->device);
-  if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plan's device");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// The fit over spatial chunks of at most w points (w <= chunk_points): per
+// chunk the time mean of its columns, the FFT into Qhat and the Gram partial
+// sums; then the reduction and the eigen-solve.
+static spod_status fit_impl(spod_plan_t p, const void* d_X, cudaStream_t s, int64_t w) {
   p->fitted = false;
   p->qhat_valid = false;
   SPOD_CUDA(cudaMemsetAsync(p->d_flags, 0, 4 * sizeof(unsigned), s), "clear flags");
-  if (p->desc.subtract_mean) {
-    Phase ph(p, SPOD_PHASE_MEAN, s, 2);
-    SPOD_CUDA(launch_mean(*p, d_X, s), "mean kernel");
-  } else {
-    SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M, s), "zero mean");
-  }
+  if (!p->desc.subtract_mean) SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M, s), "zero mean");
   alignas(64) CUtensorMap xmap;
   const CUtensorMap* xm = nullptr;
   if (p->ring_ok) {
@@ -561,8 +560,12 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
     xm = &xmap;
   }
   int64_t nchunks = 0;
-  for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points, ++nchunks) {
-    const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
+  for (int64_t m0 = 0; m0 < p->M; m0 += w, ++nchunks) {
+    const int64_t mc = std::min<int64_t>(w, p->M - m0);
+    if (p->desc.subtract_mean) {
+      Phase ph(p, SPOD_PHASE_MEAN, s, 2);
+      SPOD_CUDA(launch_mean(*p, d_X, m0, mc, s), "mean kernel");
+    }
     {
       Phase ph(p, SPOD_PHASE_FFT, s, 1);
       if (spod_status st = run_fft_chunk(p, d_X, xm, m0, mc, s)) return st;
@@ -584,6 +587,14 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
   p->qhat_valid = nchunks == 1;
   p->last_stream = s;
   return SPOD_OK;
+}
+
+spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plan's device");
+  return fit_impl(p, d_X, static_cast<cudaStream_t>(stream), p->chunk_points);
 }
 
 spod_status spod_sync(spod_plan_t p, void* stream) {
@@ -629,16 +640,12 @@ spod_status spod_get_freqs(spod_plan_t p, double* freqs) {
   return SPOD_OK;
 }
 
-spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, void* stream) {
-  if (spod_status st = check_plan(p)) return st;
-  if (!p->fitted) return fail(SPOD_ESTATE, "spod_modes before spod_fit");
-  if (nmodes < 1 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 1 <= nmodes <= nb");
-  if (spod_status st = check_ptr(d_Phi, "d_Phi")) return st;
-  if (!p->qhat_valid) {
-    if (spod_status st = check_ptr(d_X, "d_X")) return st;
-  }
-  DeviceGuard g(p->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// The modes: over spatial chunks of the plan (Qhat recomputed per chunk)
+// unless the fit left all of Qhat in place; then, with nrange > 0, over
+// nrange frequency ranges, recording done[r] after range r (Phi is
+// frequency-major, so a range is one contiguous block of d_Phi).
+static spod_status modes_impl(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, cudaStream_t s,
+                              int nrange, const cudaEvent_t* done) {
   {
     Phase ph(p, SPOD_PHASE_MODES, s, 1);
     SPOD_CUDA(launch_mode_coeffs(*p, nmodes, s), "mode coefficient kernel");
@@ -648,12 +655,17 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
     }
   }
   if (p->qhat_valid) {
-    Phase ph(p, SPOD_PHASE_MODES, s, 0);
-    if (p->tensor) {
-      SPOD_CUDA(launch_modes_tc_chunk(*p, 0, p->M, nmodes, d_Phi, s), "tensor-core modes kernel");
-      ph.n = 1;
-    } else {
-      SPOD_CUDA(launch_modes_chunk(*p, 0, p->M, nmodes, d_Phi, s, &ph.n), "modes kernel");
+    const int nr = std::max(1, std::min(nrange, p->nf));
+    for (int r = 0; r < nr; ++r) {
+      const int f0 = (int)((int64_t)p->nf * r / nr), f1 = (int)((int64_t)p->nf * (r + 1) / nr);
+      Phase ph(p, SPOD_PHASE_MODES, s, 0);
+      if (p->tensor) {
+        SPOD_CUDA(launch_modes_tc_chunk(*p, 0, p->M, nmodes, d_Phi, s, false, f0, f1), "tensor-core modes kernel");
+        ph.n = 1;
+      } else {
+        SPOD_CUDA(launch_modes_chunk(*p, 0, p->M, nmodes, d_Phi, s, &ph.n, false, f0, f1), "modes kernel");
+      }
+      if (done) SPOD_CUDA(cudaEventRecord(done[r], s), "range done");
     }
   } else {
     alignas(64) CUtensorMap xmap;
@@ -676,9 +688,22 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
         SPOD_CUDA(launch_modes_chunk(*p, m0, mc, nmodes, d_Phi, s, &ph.n), "modes kernel");
       }
     }
+    for (int r = 0; done && r < nrange; ++r) SPOD_CUDA(cudaEventRecord(done[r], s), "range done");
   }
   p->last_stream = s;
   return SPOD_OK;
+}
+
+spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!p->fitted) return fail(SPOD_ESTATE, "spod_modes before spod_fit");
+  if (nmodes < 1 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 1 <= nmodes <= nb");
+  if (spod_status st = check_ptr(d_Phi, "d_Phi")) return st;
+  if (!p->qhat_valid) {
+    if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  }
+  DeviceGuard g(p->device);
+  return modes_impl(p, d_X, nmodes, d_Phi, static_cast<cudaStream_t>(stream), 1, nullptr);
 }
 
 spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* d_X, void* d_dX, void* stream) {
@@ -736,6 +761,112 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
   return SPOD_OK;
 }
 
+// Datasets from and to host memory, one after another through the plan.
+// The host link (~200 GB/s each way, ~340 GB/s both ways at once) is the
+// bound, so the copies run on two plan-owned streams beside the compute
+// stream: dataset i + 1's X goes up while dataset i's modes come down, from
+// two staging pairs used in turn; each dataset's modes are computed in
+// kRanges frequency ranges, and a range goes down while the next one is
+// computed.
+constexpr int kRanges = 8;
+
+static spod_status grow(void** buf, size_t* have, size_t need, const char* what) {
+  if (*have >= need) return SPOD_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  if (cudaMalloc(buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPOD_ENOMEM, what);
+  }
+  *have = need;
+  return SPOD_OK;
+}
+
+static spod_status run_host_impl(spod_plan_t p, int n, const void* const* h_X, int nmodes, void* const* h_Phi,
+                                 double* const* h_lambda, cudaStream_t s) {
+  const size_t el = elem_bytes(p->desc.in_dtype);
+  const size_t xb = (size_t)p->nt * p->M * el;
+  const size_t eb = p->f64 ? 16 : 8;            // one complex element of Phi
+  const size_t fb = (size_t)nmodes * p->M * eb; // Phi bytes of one frequency
+  const size_t pb = (size_t)p->nf * fb;
+  const int nbuf = n > 1 ? 2 : 1;
+  SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");   // staging may be reallocated
+  // staging pair 0 (kept across calls), pair 1 only for several datasets
+  if (spod_status st = grow(&p->d_xstage, &p->xstage_bytes, xb, "X staging")) return st;
+  if (nmodes > 0) {
+    if (spod_status st = grow(&p->d_phistage, &p->phistage_bytes, pb, "Phi staging")) return st;
+  }
+  const size_t lb = sizeof(double) * (size_t)p->nf * p->nb;
+  if (h_lambda) {
+    if (spod_status st = grow(&p->d_lamstage, &p->lamstage_bytes, lb * n, "eigenvalue staging")) return st;
+  }
+  if (nbuf == 2) {
+    if (spod_status st = grow(&p->d_xstage2, &p->xstage2_bytes, xb, "X staging")) return st;
+    if (nmodes > 0) {
+      if (spod_status st = grow(&p->d_phistage2, &p->phistage2_bytes, pb, "Phi staging")) return st;
+    }
+  }
+  if (!p->h2d_stream) SPOD_CUDA(cudaStreamCreateWithFlags(&p->h2d_stream, cudaStreamNonBlocking), "copy stream");
+  if (!p->d2h_stream) SPOD_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking), "copy stream");
+  // events: x_ready[2], x_free[2], phi_free[2], start, range_done[2][kRanges]
+  const size_t nev = 7 + 2 * kRanges;
+  while (p->host_ev.size() < nev) {
+    cudaEvent_t e;
+    SPOD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    p->host_ev.push_back(e);
+  }
+  cudaEvent_t* x_ready = &p->host_ev[0];
+  cudaEvent_t* x_free = &p->host_ev[2];
+  cudaEvent_t* phi_free = &p->host_ev[4];
+  cudaEvent_t start = p->host_ev[6];
+  cudaEvent_t* range_done = &p->host_ev[7];
+  void* xs[2] = {p->d_xstage, p->d_xstage2};
+  void* ps[2] = {p->d_phistage, p->d_phistage2};
+  cudaStream_t up = p->h2d_stream, down = p->d2h_stream;
+  SPOD_CUDA(cudaEventRecord(start, s), "event");
+  SPOD_CUDA(cudaStreamWaitEvent(up, start, 0), "wait");
+  SPOD_CUDA(cudaStreamWaitEvent(down, start, 0), "wait");
+  for (int i = 0; i < n; ++i) {
+    const int b = i % nbuf;
+    // X of dataset i into staging b once dataset i - 2 no longer reads it
+    if (i >= nbuf) SPOD_CUDA(cudaStreamWaitEvent(up, x_free[b], 0), "wait");
+    SPOD_CUDA(cudaMemcpyAsync(xs[b], h_X[i], xb, cudaMemcpyHostToDevice, up), "copy X to device");
+    SPOD_CUDA(cudaEventRecord(x_ready[b], up), "event");
+    SPOD_CUDA(cudaStreamWaitEvent(s, x_ready[b], 0), "wait");
+    if (spod_status st = fit_impl(p, xs[b], s, p->chunk_points)) return st;
+    // eigenvalues to device staging (a pageable host copy here would stall the pipeline)
+    if (h_lambda && h_lambda[i])
+      SPOD_CUDA(cudaMemcpyAsync(static_cast<char*>(p->d_lamstage) + lb * i, p->d_lam, lb, cudaMemcpyDeviceToDevice, s),
+                "stage lambda");
+    if (nmodes > 0) {
+      // Phi staging b once dataset i - 2's modes have gone down
+      if (i >= nbuf) SPOD_CUDA(cudaStreamWaitEvent(s, phi_free[b], 0), "wait");
+      if (spod_status st = modes_impl(p, xs[b], nmodes, ps[b], s, kRanges, range_done + b * kRanges)) return st;
+      for (int r = 0; r < kRanges; ++r) {
+        const int nr = std::min(kRanges, p->nf);
+        if (r >= nr) break;
+        const int64_t f0 = (int64_t)p->nf * r / nr, f1 = (int64_t)p->nf * (r + 1) / nr;
+        SPOD_CUDA(cudaStreamWaitEvent(down, range_done[b * kRanges + r], 0), "wait");
+        SPOD_CUDA(cudaMemcpyAsync(static_cast<char*>(h_Phi[i]) + f0 * fb, static_cast<const char*>(ps[b]) + f0 * fb,
+                                  (f1 - f0) * fb, cudaMemcpyDeviceToHost, down), "copy Phi to host");
+      }
+      SPOD_CUDA(cudaEventRecord(phi_free[b], down), "event");
+    }
+    SPOD_CUDA(cudaEventRecord(x_free[b], s), "event");
+  }
+  SPOD_CUDA(cudaEventRecord(start, up), "event");
+  SPOD_CUDA(cudaStreamWaitEvent(s, start, 0), "join");
+  SPOD_CUDA(cudaEventRecord(start, down), "event");
+  SPOD_CUDA(cudaStreamWaitEvent(s, start, 0), "join");
+  for (int i = 0; h_lambda && i < n; ++i)
+    if (h_lambda[i])
+      SPOD_CUDA(cudaMemcpyAsync(h_lambda[i], static_cast<const char*>(p->d_lamstage) + lb * i, lb,
+                                cudaMemcpyDeviceToHost, s), "copy lambda to host");
+  SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  return read_flags(p);
+}
+
 spod_status spod_run_host(spod_plan_t p, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
                           void* stream) {
   if (spod_status st = check_plan(p)) return st;
@@ -743,34 +874,20 @@ spod_status spod_run_host(spod_plan_t p, const void* h_X, int nmodes, void* h_Ph
   if (nmodes < 0 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 0 <= nmodes <= nb");
   if (nmodes > 0 && !h_Phi) return fail(SPOD_EINVAL, "h_Phi is NULL");
   DeviceGuard g(p->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t xb = (size_t)p->nt * p->M * elem_bytes(p->desc.in_dtype);
-  if (p->xstage_bytes < xb) {
-    if (p->d_xstage) cudaFree(p->d_xstage);
-    p->d_xstage = nullptr;
-    p->xstage_bytes = 0;
-    if (cudaMalloc(&p->d_xstage, xb) != cudaSuccess) { cudaGetLastError(); return fail(SPOD_ENOMEM, "X staging"); }
-    p->xstage_bytes = xb;
+  return run_host_impl(p, 1, &h_X, nmodes, &h_Phi, &h_lambda, static_cast<cudaStream_t>(stream));
+}
+
+spod_status spod_run_host_many(spod_plan_t p, int n, const void* const* h_X, int nmodes, void* const* h_Phi,
+                               double* const* h_lambda, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (n < 1 || !h_X) return fail(SPOD_EINVAL, "need n >= 1 and h_X");
+  if (nmodes < 0 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 0 <= nmodes <= nb");
+  for (int i = 0; i < n; ++i) {
+    if (!h_X[i]) return fail(SPOD_EINVAL, "h_X[i] is NULL");
+    if (nmodes > 0 && (!h_Phi || !h_Phi[i])) return fail(SPOD_EINVAL, "h_Phi[i] is NULL");
   }
-  const size_t pb = (size_t)p->nf * nmodes * p->M * 2 * (p->f64 ? 8 : 4);
-  if (nmodes > 0 && p->phistage_bytes < pb) {
-    if (p->d_phistage) cudaFree(p->d_phistage);
-    p->d_phistage = nullptr;
-    p->phistage_bytes = 0;
-    if (cudaMalloc(&p->d_phistage, pb) != cudaSuccess) { cudaGetLastError(); return fail(SPOD_ENOMEM, "Phi staging"); }
-    p->phistage_bytes = pb;
-  }
-  SPOD_CUDA(cudaMemcpyAsync(p->d_xstage, h_X, xb, cudaMemcpyHostToDevice, s), "copy X to device");
-  if (spod_status st = spod_fit(p, p->d_xstage, stream)) return st;
-  if (nmodes > 0) {
-    if (spod_status st = spod_modes(p, p->d_xstage, nmodes, p->d_phistage, stream)) return st;
-    SPOD_CUDA(cudaMemcpyAsync(h_Phi, p->d_phistage, pb, cudaMemcpyDeviceToHost, s), "copy Phi to host");
-  }
-  if (h_lambda)
-    SPOD_CUDA(cudaMemcpyAsync(h_lambda, p->d_lam, sizeof(double) * (size_t)p->nf * p->nb, cudaMemcpyDeviceToHost, s),
-              "copy lambda to host");
-  SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
-  return read_flags(p);
+  DeviceGuard g(p->device);
+  return run_host_impl(p, n, h_X, nmodes, h_Phi, h_lambda, static_cast<cudaStream_t>(stream));
 }
 
 spod_status spod_plan_get_tuning(spod_plan_t p, spod_tuning* t) {

@@ -123,6 +123,16 @@ struct spod_plan_s {
   size_t xstage_bytes = 0;
   void* d_phistage = nullptr;
   size_t phistage_bytes = 0;
+  // spod_run_host(_many): second staging pair, copy streams (host to device,
+  // device to host) and the events that hand buffers between the streams
+  void* d_xstage2 = nullptr;
+  size_t xstage2_bytes = 0;
+  void* d_phistage2 = nullptr;
+  size_t phistage2_bytes = 0;
+  void* d_lamstage = nullptr;              // eigenvalues of each dataset of a run_host call
+  size_t lamstage_bytes = 0;
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  std::vector<cudaEvent_t> host_ev;
   double* d_gradlam = nullptr;
 
   // per-phase timing and launch counts
@@ -136,15 +146,18 @@ struct spod_plan_s {
 namespace spod {
 
 // Launchers (each returns the first CUDA error it meets).
-cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, cudaStream_t s);
+// Time mean of the columns [m0, m0 + mcount) of X.
+cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s);
 cudaError_t launch_fft_chunk(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount,
                              cudaStream_t s);
 cudaError_t launch_gram_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
 cudaError_t launch_gram_reduce(const spod_plan_s& p, cudaStream_t s);
 cudaError_t launch_eig(const spod_plan_s& p, cudaStream_t s);
 cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s);
+// Modes of the points [m0, m0 + mcount) at the frequencies [f0, f1) (f1 < 0: all).
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes,
-                               void* d_Phi, cudaStream_t s, int* nlaunch, bool adjoint = false);
+                               void* d_Phi, cudaStream_t s, int* nlaunch, bool adjoint = false, int f0 = 0,
+                               int f1 = -1);
 cudaError_t launch_adj_gmat(const spod_plan_s& p, const double* d_g, cudaStream_t s);
 cudaError_t launch_adjoint_chunk(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t m0, int64_t mcount,
                                  void* d_dX, cudaStream_t s);
@@ -152,7 +165,7 @@ size_t adjoint_smem_bytes(const spod_plan_s& p);
 
 cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
 cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, bool adjoint = false);
+                                  cudaStream_t s, bool adjoint = false, int f0 = 0, int f1 = -1);
 size_t gram_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_image_bytes(const spod_plan_s& p);

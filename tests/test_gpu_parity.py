@@ -213,8 +213,30 @@ def test_run_host_matches_device_path():
     hlam = np.empty_like(lam)
     hPhi = np.empty((sp.nf, 3, sp.M), dtype=np.complex64)
     _lib.spod_run_host(sp.handle, hX, 3, hPhi, hlam)
+    # the host path runs the same fit and modes (copies beside them)
     assert np.array_equal(hlam, lam)
     assert np.array_equal(hPhi, Phi)
+
+
+@cuda
+def test_run_host_many_equals_single_calls():
+    wls = [jet_like(nx=16, nr=8, nvars=2, nt=600, nfft=64, seed=s) for s in (5, 6, 7)]
+    sp = SPOD(wls[0].npoints, 2, 600, 64, 32, weights=wls[0].W)
+    hX = [w.X.numpy().copy() for w in wls]
+    ref = []
+    for x in hX:
+        lam, Phi = np.empty((sp.nf, sp.nb)), np.empty((sp.nf, 4, sp.M), dtype=np.complex64)
+        _lib.spod_run_host(sp.handle, x, 4, Phi, lam)
+        ref.append((lam, Phi))
+    lams = [np.empty((sp.nf, sp.nb)) for _ in hX]
+    Phis = [np.empty((sp.nf, 4, sp.M), dtype=np.complex64) for _ in hX]
+    _lib.spod_run_host_many(sp.handle, hX, 4, Phis, lams)
+    for (lam, Phi), l2, P2 in zip(ref, lams, Phis):
+        assert np.array_equal(lam, l2) and np.array_equal(Phi, P2)
+    with pytest.raises(SpodError) as e:
+        _lib.spod_run_host_many(sp.handle, hX, 4, [Phis[0], None, Phis[2]], lams)
+    assert e.value.status == _lib.SPOD_EINVAL
+    sp.close()
 
 
 @cuda
