@@ -17,6 +17,8 @@ decompositions in the PySPOD package" (arXiv 2309.11808), Sec. 2.2
 * method-of-snapshots eigenproblem Q_k^* W Q_k Psi = Psi Lambda (Eq. spod-discrete-snapshots)
 * modes Phi_k = Q_k Psi_k Lambda_k^{-1/2} (scaled, see below)   (Eq. spod-discrete-snapshots)
 * one-sided spectrum for real data                              (Eq. discrete_modes)
+* complex data (the paper allows complex Q, Eq. data-matrix): every bin
+  f = 0 .. N_f - 1 is kept, since there is no conjugate symmetry
 
 Readings where the paper is silent or at odds with itself (all listed in the
 design notes of the repository):
@@ -72,14 +74,19 @@ def n_blocks(nt: int, nfft: int, noverlap: int) -> int:
     return (nt - noverlap) // step
 
 
-def n_freqs(nfft: int) -> int:
-    """One-sided frequency count for real data: floor(nfft/2) + 1."""
-    return nfft // 2 + 1
+def n_freqs(nfft: int, two_sided: bool = False) -> int:
+    """Frequency count: floor(nfft/2) + 1 for real data (one-sided, Sec. 2.2),
+    nfft for complex data (all bins; the paper allows complex Q, Eq. data-matrix)."""
+    return nfft if two_sided else nfft // 2 + 1
 
 
-def freqs(nfft: int, dt: float) -> np.ndarray:
-    """Frequency of bin f: f / (nfft * dt)."""
-    return np.arange(n_freqs(nfft)) / (nfft * dt)
+def freqs(nfft: int, dt: float, two_sided: bool = False) -> np.ndarray:
+    """Frequency of bin f: f / (nfft * dt); two-sided bins f >= nfft/2 rounded
+    up are the negative frequencies (f - nfft) / (nfft * dt)."""
+    f = np.arange(n_freqs(nfft, two_sided))
+    if two_sided:
+        f = np.where(f < (nfft + 1) // 2, f, f - nfft)
+    return f / (nfft * dt)
 
 
 # --------------------------------------------------------------------------
@@ -106,20 +113,26 @@ def window(kind: str, nfft: int, user: np.ndarray | None = None) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Steps of Sec. 2.2
 # --------------------------------------------------------------------------
+def _as_data(X: np.ndarray) -> np.ndarray:
+    """X in FP64, complex128 when it is complex."""
+    return np.asarray(X, dtype=np.complex128 if np.iscomplexobj(X) else np.float64)
+
+
 def time_mean(X: np.ndarray) -> np.ndarray:
     """Temporal mean of every row of Q over all nt snapshots (Sec. 2.2).
 
-    X is laid out [nt][M] (time-major).  FP64 pairwise summation.
+    X is laid out [nt][M] (time-major).  FP64 pairwise summation (complex data:
+    of the real and imaginary parts).
     """
-    return np.asarray(X, dtype=np.float64).mean(axis=0)
+    return _as_data(X).mean(axis=0)
 
 
-def dft_matrix(nfft: int) -> np.ndarray:
-    """E[f, n] = exp(-2 pi i ((f*n) mod nfft) / nfft), f one-sided.
+def dft_matrix(nfft: int, two_sided: bool = False) -> np.ndarray:
+    """E[f, n] = exp(-2 pi i ((f*n) mod nfft) / nfft), f one-sided (or all bins).
 
     The angle is reduced exactly in integers before the cos/sin calls.
     """
-    f = np.arange(n_freqs(nfft), dtype=np.int64)[:, None]
+    f = np.arange(n_freqs(nfft, two_sided), dtype=np.int64)[:, None]
     n = np.arange(nfft, dtype=np.int64)[None, :]
     ang = 2.0 * np.pi * ((f * n) % nfft).astype(np.float64) / nfft
     return np.cos(ang) - 1j * np.sin(ang)
@@ -130,19 +143,21 @@ def block_dft(X: np.ndarray, nfft: int, noverlap: int, w: np.ndarray,
     """Windowed DFT of every Welch block (Eqs. blocks, blocks-ft, blocks-k).
 
     Returns Qhat[f][l][m] = c * sum_n w_n (X[l*step+n, m] - mu_m) e^{-2 pi i f n/nfft}
-    with c = 1 / sum_n w_n, for the one-sided f = 0 .. nfft//2.
+    with c = 1 / sum_n w_n, for the one-sided f = 0 .. nfft//2 of real data, or
+    for every bin f = 0 .. nfft-1 of complex data (no conjugate symmetry).
 
     method="direct": multiplication by the explicit DFT matrix (the definition).
-    method="fft": numpy.fft.rfft as a library step (used for large inputs; it is
-    checked against "direct" by the tests).
+    method="fft": numpy.fft.rfft (complex data: numpy.fft.fft) as a library
+    step (used for large inputs; it is checked against "direct" by the tests).
     """
-    X = np.asarray(X, dtype=np.float64)
+    X = _as_data(X)
+    two = np.iscomplexobj(X)
     nt, M = X.shape
     nb = n_blocks(nt, nfft, noverlap)
     step = nfft - noverlap
-    nf = n_freqs(nfft)
+    nf = n_freqs(nfft, two)
     c = 1.0 / w.sum()
-    E = dft_matrix(nfft) if method == "direct" else None
+    E = dft_matrix(nfft, two) if method == "direct" else None
     out = np.empty((nf, nb, M), dtype=np.complex128)
     for l in range(nb):
         xb = X[l * step: l * step + nfft]
@@ -152,7 +167,7 @@ def block_dft(X: np.ndarray, nfft: int, noverlap: int, w: np.ndarray,
         if method == "direct":
             out[:, l, :] = c * (E @ xw)
         elif method == "fft":
-            out[:, l, :] = c * np.fft.rfft(xw, axis=0)
+            out[:, l, :] = c * (np.fft.fft(xw, axis=0) if two else np.fft.rfft(xw, axis=0))
         else:
             raise ValueError(method)
     return out
@@ -306,6 +321,7 @@ class Desc:
     weights: np.ndarray | None = None      # [M], > 0
     norm: str = NORM_NB
     subtract_mean: bool = True
+    complex_input: bool = False            # two-sided spectrum, nf = nfft
 
     @property
     def nb(self) -> int:
@@ -313,7 +329,7 @@ class Desc:
 
     @property
     def nf(self) -> int:
-        return n_freqs(self.nfft)
+        return n_freqs(self.nfft, self.complex_input)
 
     def w(self) -> np.ndarray:
         return window(self.window, self.nfft, self.user_window)
@@ -338,9 +354,11 @@ class Fit:
 
 def spod_fit(X: np.ndarray, d: Desc, dft: str = "direct") -> Fit:
     """Mean, blocks, window, DFT, Gram and eigen-decomposition (Sec. 2.2)."""
-    X = np.asarray(X, dtype=np.float64)
+    X = _as_data(X)
     if X.shape != (d.nt, d.M):
         raise ValueError("X must be [nt][M]")
+    if np.iscomplexobj(X) != d.complex_input:
+        raise ValueError("complex X needs Desc(complex_input=True), real X the default")
     mu = time_mean(X) if d.subtract_mean else None
     Qhat = block_dft(X, d.nfft, d.noverlap, d.w(), mu, method=dft)
     Mf = gram(Qhat, d.W(), d.norm)
@@ -364,6 +382,8 @@ def spod_grad(X: np.ndarray, d: Desc, dLdlam: np.ndarray, fit: Fit | None = None
       dL/dX[t, m] = dL/dxt[t, m] - (1/nt) sum_t' dL/dxt[t', m].
     """
     X = np.asarray(X, dtype=np.float64)
+    if d.complex_input:
+        raise ValueError("the gradient is defined for real data only")
     if fit is None:
         fit = spod_fit(X, d, dft=dft)
     nf, nb, M = fit.Qhat.shape
@@ -394,11 +414,12 @@ def loss_from_fit(fit: Fit, dLdlam: np.ndarray) -> float:
 
 
 def parseval_rhs(X: np.ndarray, d: Desc) -> float:
-    """(c^2 nfft / den) sum_l sum_n w_n^2 sum_m W_m xt[l*step+n, m]^2.
+    """(c^2 nfft / den) sum_l sum_n w_n^2 sum_m W_m |xt[l*step+n, m]|^2.
 
     Equals sum_f g_f tr(M_f) with g_f = 1 for f = 0 and f = nfft/2 (even nfft)
-    and 2 otherwise (Parseval for each block's DFT of a real sequence)."""
-    X = np.asarray(X, dtype=np.float64)
+    and 2 otherwise (Parseval for each block's DFT of a real sequence); for
+    complex data every g_f = 1 over all nfft bins."""
+    X = _as_data(X)
     w = d.w()
     c = 1.0 / w.sum()
     step = d.nfft - d.noverlap
@@ -407,7 +428,7 @@ def parseval_rhs(X: np.ndarray, d: Desc) -> float:
     tot = 0.0
     for l in range(d.nb):
         blk = xt[l * step: l * step + d.nfft]
-        tot += float(((w ** 2)[:, None] * blk ** 2 * W[None, :]).sum())
+        tot += float(((w ** 2)[:, None] * np.abs(blk) ** 2 * W[None, :]).sum())
     return c * c * d.nfft / gram_denominator(d.nb, d.norm) * tot
 
 

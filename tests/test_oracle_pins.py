@@ -373,3 +373,60 @@ def test_gram_at_freqs_closed_form_and_full_gram():
     Gn = O.gram_at_freqs(d, fsel, lambda a, b: Xn[:, a:b], chunk=77)
     full = O.gram(O.block_dft(Xn, nfft, nfft // 2, d.w(), O.time_mean(Xn)), d.W())
     np.testing.assert_allclose(Gn, full[fsel], rtol=0, atol=1e-13 * np.abs(full).max())
+
+
+# ---------------------------------------------------------------- complex data
+# Complex Q (allowed by Eq. data-matrix): all nfft bins, no conjugate symmetry.
+def test_complex_direct_dft_matches_fft_and_two_sided_parseval():
+    rs = np.random.RandomState(21)
+    nt, M, nfft, nov = 300, 7, 30, 10
+    X = rs.randn(nt, M) + 1j * rs.randn(nt, M) + (0.5 - 0.3j)
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, weights=0.5 + rs.rand(M), complex_input=True)
+    q1 = O.block_dft(X, nfft, nov, d.w(), O.time_mean(X), method="direct")
+    q2 = O.block_dft(X, nfft, nov, d.w(), O.time_mean(X), method="fft")
+    assert q1.shape == (nfft, d.nb, M)
+    np.testing.assert_allclose(q1, q2, rtol=0, atol=1e-13 * np.abs(q1).max())
+    fit = O.spod_fit(X, d)
+    tr = np.real(np.trace(fit.M, axis1=1, axis2=2)).sum()        # every bin once
+    np.testing.assert_allclose(tr, O.parseval_rhs(X, d), rtol=1e-12)
+    # the mean of the complex data is removed from both parts
+    np.testing.assert_allclose(O.time_mean(X), X.mean(axis=0), rtol=1e-14)
+
+
+def test_real_data_as_complex_reproduces_the_one_sided_fit():
+    rs = np.random.RandomState(22)
+    nt, M, nfft, nov = 400, 9, 32, 16
+    X = rs.randn(nt, M) + 2.0
+    W = 0.5 + rs.rand(M)
+    dr = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, weights=W)
+    dc = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, weights=W, complex_input=True)
+    fr = O.spod_fit(X, dr)
+    fc = O.spod_fit(X.astype(np.complex128), dc)
+    nf1 = nfft // 2 + 1
+    np.testing.assert_allclose(fc.lam[:nf1], fr.lam, rtol=1e-11, atol=1e-13 * fr.lam.max())
+    # conjugate symmetry of real data: bin nfft - f carries the conjugate spectrum
+    for f in range(1, nfft // 2):
+        np.testing.assert_allclose(fc.lam[nfft - f], fc.lam[f], rtol=1e-11, atol=1e-13 * fr.lam.max())
+        np.testing.assert_allclose(fc.Qhat[nfft - f], np.conj(fc.Qhat[f]), rtol=0, atol=1e-13)
+    assert np.allclose(O.freqs(nfft, 0.1, True)[nfft - 1], -1.0 / (nfft * 0.1))
+
+
+def test_planted_complex_exponential_sits_in_one_bin():
+    # x[t, m] = a phi_m exp(+2 pi i k t / nfft), phi W-orthonormal, periodic
+    # Hamming (its DFT lives on bins 0, +-1): lambda_1 = a^2 at bin k, a^2
+    # (0.23/0.54)^2 at bins k +- 1, and nothing at the mirrored bin nfft - k
+    rs = np.random.RandomState(23)
+    nt, M, nfft, nov, k, a = 2048, 12, 64, 32, 9, 1.7
+    W = 0.5 + rs.rand(M)
+    phi = rs.randn(M) + 1j * rs.randn(M)
+    phi /= np.sqrt(np.sum(W * np.abs(phi) ** 2))
+    t = np.arange(nt)[:, None]
+    X = a * phi[None, :] * np.exp(2j * np.pi * k * t / nfft)
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, window=O.WIN_HAMMING_PERIODIC, weights=W,
+               subtract_mean=False, complex_input=True)
+    fit = O.spod_fit(X, d, dft="fft")
+    np.testing.assert_allclose(fit.lam[k, 0], a * a, rtol=1e-12)
+    for kk in (k - 1, k + 1):
+        np.testing.assert_allclose(fit.lam[kk, 0], a * a * (0.23 / 0.54) ** 2, rtol=1e-12)
+    assert fit.lam[nfft - k].max() <= 1e-24 * a * a
+    assert fit.lam[k, 1:].max() <= 1e-12 * a * a                  # rank one
