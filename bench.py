@@ -48,15 +48,20 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a reduced grid for quick checks (not a bench value)")
     ap.add_argument("--grid", default=None, help="NXxNR grid for profiling runs (not a bench value)")
+    ap.add_argument("--complex", action="store_true",
+                    help="complex input of the same shape (the jet field + i x a second seed's field, "
+                         "two-sided spectrum); a separate measurement, not the headline line")
     return ap.parse_args()
 
 
 def workload_config(args, nb, nf, nmodes):
-    return {"workload": f"jet-shaped {NX}x{NR}x{NVARS}, nt={NT}, nfft={NFFT}, 50% overlap",
+    cx = getattr(args, "complex", False)
+    return {"workload": f"jet-shaped {NX}x{NR}x{NVARS}, nt={NT}, nfft={NFFT}, 50% overlap"
+                        + (", complex (two-sided)" if cx else ""),
             "npoints": NX * NR, "nvars": NVARS, "M": NX * NR * NVARS, "nt": NT, "nfft": NFFT,
-            "noverlap": NOVERLAP, "nb": nb, "nf": nf, "nmodes": nmodes, "in_dtype": "f32",
+            "noverlap": NOVERLAP, "nb": nb, "nf": nf, "nmodes": nmodes, "in_dtype": "c64" if cx else "f32",
             "precision": args.precision, "window": "hamming", "weights": "r-weighted",
-            "l2": "inputs larger than L2 (15.7 GB per step)"}
+            "l2": f"inputs larger than L2 ({NT * NX * NR * NVARS * (8 if cx else 4) / 1e9:.1f} GB per step)"}
 
 
 # --------------------------------------------------------------- clocks
@@ -169,9 +174,16 @@ def main():
     if args.grid:
         nx, nr = (int(v) for v in args.grid.lower().split("x"))
     wl = jet_like(nx=nx, nr=nr, nvars=NVARS, nt=NT, nfft=NFFT, seed=rank, dtype=torch.float32, device=dev)
+    if args.complex:
+        im = jet_like(nx=nx, nr=nr, nvars=NVARS, nt=NT, nfft=NFFT, seed=rank + 1000, dtype=torch.float32,
+                      device=dev).X
+        wl.X = torch.complex(wl.X, im)
+        del im
+        torch.cuda.empty_cache()
+        args.no_e2e = args.no_cpu = args.no_compare = True
     X = wl.X
     M = X.shape[1]
-    elem = 4
+    elem = X.element_size()
     bytes_step = NT * M * elem
 
     r = timed_run(args.precision, wl, args.steps, max(3, args.warmup), world, dev, clocks=True)
@@ -188,7 +200,7 @@ def main():
         pass
     # one step launches each phase's kernels once (modes: the small coefficient
     # kernel + the mode GEMM), so the per-step phase time is the launch time
-    per_phase = {k: kernel_roofline(k, phase_ms[k] / args.steps, M, nb, nf, nmodes, peaks, args.precision)
+    per_phase = {k: kernel_roofline(k, phase_ms[k] / args.steps, M, nb, nf, nmodes, peaks, args.precision, elem)
                  for k in phase_ms if phase_launch.get(k, 0) > 0}
     dom = max(per_phase, key=lambda k: phase_ms[k])
     roof = per_phase[dom]
@@ -268,9 +280,8 @@ def max_over_ranks(x: float, dev) -> float:
 
 
 def make_plan(precision, wl):
-    import torch
     from paper_2309_11808_gb300 import SPOD
-    return SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=torch.float32, precision=precision, weights=wl.W)
+    return SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=wl.X.dtype, precision=precision, weights=wl.W)
 
 
 def timed_run(precision, wl, steps, warmup, world, dev, clocks):
@@ -344,7 +355,7 @@ def qhat_bytes_per_point(nb, nf, precision):
     return nf * 2 * nb * per
 
 
-def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
+def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, elem=4):
     """Roofline of one launch of a phase's kernel.
 
     Bytes are the compulsory traffic of the kernel in this pipeline: the FFT
@@ -358,19 +369,21 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
     kern = KERNELS.get(phase, phase)
     if isinstance(kern, dict):
         kern = kern[precision]
+    if phase == "fft" and elem == 8:
+        kern = "k_fft_pipe (complex input)"
     s = 8 if precision == "fp64" else 4
     q = qhat_bytes_per_point(nb, nf, precision) * M
     phi = nf * nmodes * M * (16 if precision == "fp64" else 8)
     if phase == "mean":
-        byts = NT * M * s
+        byts = NT * M * (8 if precision == "fp64" else elem)
     elif phase == "fft":
-        byts = NT * M * 4 + q
+        byts = NT * M * elem + q
     elif phase == "gram":
         if precision in ("fp32", "fp64"):
             flops = 4.0 * nf * nb * (nb + 1) * M            # Hermitian half of Q^H W Q, 8 flops per complex MAC
             ach = flops / t / 1e12
             return {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(FP32_PEAK, 1),
-                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": TRAFFIC.get((phase, precision)),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": TRAFFIC.get((phase, precision)) if elem == 4 else None,
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "ms": round(per_launch_ms, 4)}
         byts = q
     elif phase == "modes":
@@ -378,7 +391,7 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
             flops = 8.0 * nf * nb * nmodes * M
             ach = flops / t / 1e12
             return {"bound": "alu", "kernel": kern, "achieved": round(ach, 3), "peak": round(FP32_PEAK, 1),
-                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": TRAFFIC.get((phase, precision)),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK, 4), "traffic": TRAFFIC.get((phase, precision)) if elem == 4 else None,
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "ms": round(per_launch_ms, 4)}
         byts = q + phi
     elif phase == "eig":
@@ -392,7 +405,7 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision):
         byts = nf * nb * nb * 16
     ach = byts / t / 1e9
     return {"bound": "hbm", "kernel": kern, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get((phase, precision)), "peak_source": src + " (burst)",
+            "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get((phase, precision)) if elem == 4 else None, "peak_source": src + " (burst)",
             "bytes_per_launch": int(byts), "ms": round(per_launch_ms, 4)}
 
 

@@ -63,7 +63,12 @@ typedef enum {
   SPOD_EUNSUPPORTED = 8     /* valid request this build does not implement */
 } spod_status;
 
-typedef enum { SPOD_F64 = 0, SPOD_F32 = 1, SPOD_BF16 = 2 } spod_dtype;
+/* Element type of X.  SPOD_C64 / SPOD_C128: complex data (interleaved real,
+ * imaginary; the paper allows a complex data matrix, Eq. data-matrix): the
+ * spectrum is two-sided, nf = nfft bins f = 0 .. nfft-1 (f >= ceil(nfft/2)
+ * are the negative frequencies f - nfft), the time mean is complex, and
+ * spod_backward returns SPOD_EUNSUPPORTED. */
+typedef enum { SPOD_F64 = 0, SPOD_F32 = 1, SPOD_BF16 = 2, SPOD_C64 = 3, SPOD_C128 = 4 } spod_dtype;
 
 /* Arithmetic of the bulk FFT / Gram / mode work.  The time mean is always
  * accumulated in FP64 and the eigen-decomposition always runs in FP64.
@@ -112,8 +117,10 @@ typedef struct {
   spod_precision precision;
   spod_norm norm;
   int subtract_mean;         /* 1 (default): subtract the temporal mean; 0: use X as is */
-  int64_t chunk_points;      /* spatial points per FFT->Gram pass; 0 = automatic.  Bounds
-                                the device workspace (Qhat of one chunk). */
+  int64_t chunk_points;      /* spatial points per FFT->Gram pass; 0 = automatic: the whole
+                                grid when its Qhat fits in the larger of 40 GiB and 35 % of
+                                the device memory free at plan creation, else chunks of that
+                                size.  Bounds the device workspace (Qhat of one chunk). */
 } spod_plan_desc;
 
 typedef struct {
@@ -161,7 +168,8 @@ spod_status spod_get_eigs(spod_plan_t plan, double* lambda, double* psi, int on_
  * FP64, kappa applied) to host memory; synchronising.  SPOD_ESTATE before a fit. */
 spod_status spod_get_gram(spod_plan_t plan, double* gram);
 
-/* Frequencies f / (nfft * dt), f = 0 .. nf-1, into host memory. */
+/* Frequencies f / (nfft * dt), f = 0 .. nf-1, into host memory (complex
+ * input: bins f >= ceil(nfft/2) give (f - nfft) / (nfft * dt)). */
 spod_status spod_get_freqs(spod_plan_t plan, double* freqs);
 
 /* SPOD modes of the last fit (Eq. spod-discrete-snapshots): recomputes Qhat

@@ -11,13 +11,14 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (SPOD_F32, SPOD_F64, SPOD_BF16, SPOD_PREC_BF16, SPOD_PREC_BF16X3, SPOD_PREC_FP32,  # noqa: F401
-                   SPOD_PREC_FP64, SPOD_NORM_NB, SPOD_NORM_NB_MINUS_1, SPOD_WIN_HAMMING,
+from ._lib import (SPOD_F32, SPOD_F64, SPOD_BF16, SPOD_C64, SPOD_C128,  # noqa: F401
+                   SPOD_PREC_BF16, SPOD_PREC_BF16X3, SPOD_PREC_FP32, SPOD_PREC_FP64, SPOD_NORM_NB, SPOD_NORM_NB_MINUS_1, SPOD_WIN_HAMMING,
                    SPOD_WIN_HAMMING_PERIODIC, SPOD_WIN_HANN, SPOD_WIN_RECT, SPOD_WIN_USER, SpodError)
 
 __all__ = ["SPOD", "SpodError", "make_desc"]
 
-_DTYPES = {torch.float64: SPOD_F64, torch.float32: SPOD_F32, torch.bfloat16: SPOD_BF16}
+_DTYPES = {torch.float64: SPOD_F64, torch.float32: SPOD_F32, torch.bfloat16: SPOD_BF16,
+           torch.complex64: SPOD_C64, torch.complex128: SPOD_C128}
 _PRECS = {"fp64": SPOD_PREC_FP64, "fp32": SPOD_PREC_FP32, "bf16": SPOD_PREC_BF16, "bf16x3": SPOD_PREC_BF16X3}
 _WINS = {"hamming": SPOD_WIN_HAMMING, "hamming_periodic": SPOD_WIN_HAMMING_PERIODIC, "hann": SPOD_WIN_HANN,
          "rect": SPOD_WIN_RECT, "user": SPOD_WIN_USER}

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_PKG, "libspod.so")
 # enums (values as in include/spod.h)
 SPOD_OK, SPOD_EINVAL, SPOD_ENOMEM, SPOD_ECUDA, SPOD_ESTATE = 0, 1, 2, 3, 4
 SPOD_ENANINPUT, SPOD_ENOTCONVERGED, SPOD_ETIMEOUT, SPOD_EUNSUPPORTED = 5, 6, 7, 8
-SPOD_F64, SPOD_F32, SPOD_BF16 = 0, 1, 2
+SPOD_F64, SPOD_F32, SPOD_BF16, SPOD_C64, SPOD_C128 = 0, 1, 2, 3, 4
 SPOD_PREC_FP64, SPOD_PREC_FP32, SPOD_PREC_BF16, SPOD_PREC_BF16X3 = 0, 1, 2, 3
 SPOD_WIN_HAMMING, SPOD_WIN_HAMMING_PERIODIC, SPOD_WIN_HANN, SPOD_WIN_RECT, SPOD_WIN_USER = 0, 1, 2, 3, 4
 SPOD_NORM_NB, SPOD_NORM_NB_MINUS_1 = 0, 1

@@ -58,8 +58,12 @@ __global__ void k_mean_finish(const double* __restrict__ part, int splits, int64
   mu[m] = s * inv_nt;
 }
 
-// One CTA (256 threads) per (Welch block l, tile of TP points).
-template <typename Tin, typename R, int TP, int OUTK>
+// One CTA (256 threads) per (Welch block l, tile of TP points).  Real data:
+// two points share each of the TP/2 complex columns and are separated after
+// the transform.  Complex data (CPLX; X holds interleaved real, imaginary
+// components of type Tin): one point per column, TP/2 points per tile, and
+// every one of the nfft bins is kept.
+template <typename Tin, typename R, int TP, int OUTK, bool CPLX = false>
 __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R* __restrict__ win,
                                              const typename C2<R>::T* __restrict__ tw_g,
                                              const R* __restrict__ sqrtW, const double* __restrict__ mu,
@@ -75,7 +79,8 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
   const int64_t item = blockIdx.x;
   const int l = (int)(item % a.nb);
   const int64_t tile = item / a.nb;
-  const int64_t lm0 = tile * TP;          // local (chunk) point index
+  constexpr int PPT = CPLX ? TP / 2 : TP; // points per tile
+  const int64_t lm0 = tile * PPT;         // local (chunk) point index
   const int64_t gm0 = a.m0 + lm0;         // global point index
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = tw_g[i];
@@ -83,21 +88,25 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
   // ---- load block l: thread owns column pair j, rows n = n0, n0 + 256/C, ...
   // (the mean is read once per column and kept as a rounded pair hi + lo)
   {
+    // the column's two real values: points m, m + 1 (real data) or the real
+    // and imaginary parts of point m (complex data), both at component index xi
     const int j = threadIdx.x % C;
     const int n0 = threadIdx.x / C;
-    const int64_t m = gm0 + 2 * j;
+    const int64_t m = gm0 + (CPLX ? j : 2 * j);
+    const int64_t xi = CPLX ? 2 * m : m;
     const int64_t mend = a.m0 + a.mcount;
-    const bool ok0 = m < mend, ok1 = m + 1 < mend;
+    const bool ok0 = m < mend, ok1 = CPLX ? ok0 : m + 1 < mend;
     R mhi0 = 0, mlo0 = 0, mhi1 = 0, mlo1 = 0;
     if (a.subtract_mean) {
-      if (ok0) { const double d = mu[m]; mhi0 = (R)d; mlo0 = (R)(d - (double)mhi0); }
-      if (ok1) { const double d = mu[m + 1]; mhi1 = (R)d; mlo1 = (R)(d - (double)mhi1); }
+      if (ok0) { const double d = mu[xi]; mhi0 = (R)d; mlo0 = (R)(d - (double)mhi0); }
+      if (ok1) { const double d = mu[xi + 1]; mhi1 = (R)d; mlo1 = (R)(d - (double)mhi1); }
     }
-    const Tin* base = X + (int64_t)l * a.step * a.M + m;
+    const int64_t rowlen = CPLX ? 2 * a.M : a.M;   // components per snapshot
+    const Tin* base = X + (int64_t)l * a.step * rowlen + xi;
     constexpr int NSTEP = 256 / C;
 #pragma unroll 4
     for (int n = n0; n < N; n += NSTEP) {
-      const Tin* row = base + (int64_t)n * a.M;
+      const Tin* row = base + (int64_t)n * rowlen;
       R x0 = ok0 ? (R)to_f64<Tin>(row[0]) : (R)0;
       R x1 = ok1 ? (R)to_f64<Tin>(row[1]) : (R)0;
       x0 = ok0 ? (x0 - mhi0) - mlo0 : (R)0;
@@ -130,22 +139,28 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
   // ---- separate the two real spectra, fold sqrt(W), store planar re/im rows;
   // points past mcount (up to the 64-point padding) are written as zeros
   const int64_t rs = a.chunk;
-  for (int idx = threadIdx.x; idx < a.nf * TP; idx += blockDim.x) {
-    const int f = idx / TP, p = idx - f * TP;
+  for (int idx = threadIdx.x; idx < a.nf * PPT; idx += blockDim.x) {
+    const int f = idx / PPT, p = idx - f * PPT;
     const int64_t lm = lm0 + p;
     if (lm >= a.mpad) continue;
     R re = 0, im = 0;
     if (lm < a.mcount) {
-      const int col = p >> 1;
-      const V zf = buf[f * C + col];
-      const int fn = (f == 0) ? 0 : N - f;
-      const V zc = buf[fn * C + col];
-      if ((p & 1) == 0) {          // (Z[f] + conj Z[N-f]) / 2
-        re = (R)0.5 * (zf.x + zc.x);
-        im = (R)0.5 * (zf.y - zc.y);
-      } else {                     // (Z[f] - conj Z[N-f]) / (2i)
-        re = (R)0.5 * (zf.y + zc.y);
-        im = (R)-0.5 * (zf.x - zc.x);
+      if constexpr (CPLX) {          // column p is point p: Z[f] as it is
+        const V z = buf[f * C + p];
+        re = z.x;
+        im = z.y;
+      } else {
+        const int col = p >> 1;
+        const V zf = buf[f * C + col];
+        const int fn = (f == 0) ? 0 : N - f;
+        const V zc = buf[fn * C + col];
+        if ((p & 1) == 0) {          // (Z[f] + conj Z[N-f]) / 2
+          re = (R)0.5 * (zf.x + zc.x);
+          im = (R)0.5 * (zf.y - zc.y);
+        } else {                     // (Z[f] - conj Z[N-f]) / (2i)
+          re = (R)0.5 * (zf.y + zc.y);
+          im = (R)-0.5 * (zf.x - zc.x);
+        }
       }
       const R sw = sqrtW[gm0 + p];
       re *= sw;
@@ -173,9 +188,10 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
   }
 }
 
-template <typename Tin, typename R, int OUTK>
+template <typename Tin, typename R, int OUTK, bool CPLX = false>
 cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
   constexpr int TP = sizeof(R) == 8 ? 8 : 16;
+  constexpr int PPT = CPLX ? TP / 2 : TP;
   FftArgs a;
   a.M = p.M; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
   a.mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
@@ -183,10 +199,10 @@ cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int6
   a.subtract_mean = p.desc.subtract_mean;
   a.fp = p.fft;
   const size_t smem = fft_smem_bytes(p);
-  auto kern = k_fft<Tin, R, TP, OUTK>;
+  auto kern = k_fft<Tin, R, TP, OUTK, CPLX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (a.mpad + TP - 1) / TP;
+  const int64_t ntiles = (a.mpad + PPT - 1) / PPT;
   const int64_t grid = ntiles * p.nb;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   kern<<<(unsigned)grid, 256, smem, s>>>(
@@ -197,15 +213,17 @@ cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int6
 }
 
 template <typename Tin>
-cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
+// Mean of the real columns [m0, m0 + mcount) of a [nt][Mcols] array.
+cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, int64_t Mcols, int64_t m0, int64_t mcount,
+                          cudaStream_t s) {
   const int64_t tper = (p.nt + p.mean_splits - 1) / p.mean_splits;
   dim3 grid((unsigned)((mcount + 255) / 256), (unsigned)p.mean_splits);
-  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), p.M, p.nt, tper, m0, m0 + mcount,
+  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), Mcols, p.nt, tper, m0, m0 + mcount,
                                            p.d_mupart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_mean_finish<<<(unsigned)((mcount + 255) / 256), 256, 0, s>>>(p.d_mupart, p.mean_splits, p.M, m0, m0 + mcount,
-                                                                  1.0 / (double)p.nt, p.d_mu);
+  k_mean_finish<<<(unsigned)((mcount + 255) / 256), 256, 0, s>>>(p.d_mupart, p.mean_splits, Mcols, m0,
+                                                                  m0 + mcount, 1.0 / (double)p.nt, p.d_mu);
   return cudaGetLastError();
 }
 
@@ -220,25 +238,32 @@ size_t fft_smem_bytes(const spod_plan_s& p) {
 cudaError_t launch_mean(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
   if (mcount <= 0) return cudaSuccess;
   switch (p.desc.in_dtype) {
-    case SPOD_F64: return launch_mean_t<double>(p, d_X, m0, mcount, s);
-    case SPOD_F32: return launch_mean_t<float>(p, d_X, m0, mcount, s);
-    default: return launch_mean_t<__nv_bfloat16>(p, d_X, m0, mcount, s);
+    case SPOD_F64: return launch_mean_t<double>(p, d_X, p.M, m0, mcount, s);
+    case SPOD_F32: return launch_mean_t<float>(p, d_X, p.M, m0, mcount, s);
+    // complex data: the real and imaginary parts are 2M interleaved real columns
+    case SPOD_C64: return launch_mean_t<float>(p, d_X, 2 * p.M, 2 * m0, 2 * mcount, s);
+    case SPOD_C128: return launch_mean_t<double>(p, d_X, 2 * p.M, 2 * m0, 2 * mcount, s);
+    default: return launch_mean_t<__nv_bfloat16>(p, d_X, p.M, m0, mcount, s);
   }
 }
 
-template <typename Tin>
+template <typename Tin, bool CPLX = false>
 static cudaError_t launch_fft_in(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount, cudaStream_t s) {
-  if (p.f64) return launch_fft_t<Tin, double, OUT_NATIVE>(p, d_X, m0, mcount, s);
-  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_fft_t<Tin, float, OUT_BF16X3>(p, d_X, m0, mcount, s);
-  if (p.desc.precision == SPOD_PREC_BF16) return launch_fft_t<Tin, float, OUT_BF16>(p, d_X, m0, mcount, s);
-  return launch_fft_t<Tin, float, OUT_NATIVE>(p, d_X, m0, mcount, s);
+  if (p.f64) return launch_fft_t<Tin, double, OUT_NATIVE, CPLX>(p, d_X, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_fft_t<Tin, float, OUT_BF16X3, CPLX>(p, d_X, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16) return launch_fft_t<Tin, float, OUT_BF16, CPLX>(p, d_X, m0, mcount, s);
+  return launch_fft_t<Tin, float, OUT_NATIVE, CPLX>(p, d_X, m0, mcount, s);
 }
 
 cudaError_t launch_fft_chunk(const spod_plan_s& p, const void* d_X, int64_t m0, int64_t mcount,
                              cudaStream_t s) {
-  if (p.desc.in_dtype == SPOD_F64) return launch_fft_in<double>(p, d_X, m0, mcount, s);
-  if (p.desc.in_dtype == SPOD_F32) return launch_fft_in<float>(p, d_X, m0, mcount, s);
-  return launch_fft_in<__nv_bfloat16>(p, d_X, m0, mcount, s);
+  switch (p.desc.in_dtype) {
+    case SPOD_F64: return launch_fft_in<double>(p, d_X, m0, mcount, s);
+    case SPOD_F32: return launch_fft_in<float>(p, d_X, m0, mcount, s);
+    case SPOD_C64: return launch_fft_in<float, true>(p, d_X, m0, mcount, s);
+    case SPOD_C128: return launch_fft_in<double, true>(p, d_X, m0, mcount, s);
+    default: return launch_fft_in<__nv_bfloat16>(p, d_X, m0, mcount, s);
+  }
 }
 
 bool make_fft_plan(int n, FftPlan* fp) {

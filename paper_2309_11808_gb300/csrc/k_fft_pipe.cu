@@ -1,6 +1,11 @@
 // Persistent block DFT (Eqs. blocks, blocks-ft, blocks-k) for the nfft values
 // with a compiled radix sequence (256, 384, 512, 720).
 //
+// Complex data (CPLX) runs through the same ring and passes as an array of
+// 2M interleaved real components: a column of the transform then holds one
+// complex point (its real and imaginary parts) instead of two real points,
+// and the output phase keeps all nfft bins with no separation.
+//
 // Persistent CTAs walk tiles of TP spatial points (TP = 32: one 512-thread CTA
 // per SM; TP = 16: two 256-thread CTAs per SM, for nfft = 720 and FP64 input,
 // whose rings do not fit twice); each CTA transforms the Welch blocks
@@ -208,6 +213,50 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 __device__ __forceinline__ float bf16_lo_f(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
+// Complex data: column c is point c of the tile (lp0 = its first point);
+// a thread takes two adjacent columns of bins f0, f0 + 64, ... over all N
+// bins and stores them with sqrt(W) (sw, no 1/2) as two-point rows.
+template <int OUTK, int TP, int N>
+__device__ __forceinline__ void output_phase_cplx(const float2* __restrict__ src, const PipeArgs& a, int l,
+                                                  int64_t lp0, const float (&sw)[4], void* __restrict__ qout,
+                                                  void* __restrict__ qlo) {
+  constexpr int kOutCp = Geo<TP>::OUTCP, kOutFStep = Geo<TP>::OUTFSTEP;
+  const int cp = threadIdx.x % kOutCp;
+  const int f0 = threadIdx.x / kOutCp;
+  constexpr bool BLK = OUTK != OUT_NATIVE;
+  const int64_t rs = BLK ? (int64_t)kQBlock : a.chunk;
+  const int64_t rowstride = (int64_t)2 * a.nb * rs;
+  const int64_t imoff = (int64_t)a.nb * rs;
+  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lp0 + 2 * cp)
+                  : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lp0 + 2 * cp;
+  const float4* src4 = reinterpret_cast<const float4*>(src);
+  constexpr int kIters = (N + kOutFStep - 1) / kOutFStep;
+#pragma unroll
+  for (int it = 0; it < kIters; ++it) {
+    const int f = f0 + it * kOutFStep;
+    if (f >= N) break;
+    if (it > 0) o += kOutFStep * rowstride;
+    const float4 z = src4[f * kOutCp + cp];                       // points 2cp, 2cp+1 at bin f
+    const float r0 = z.x * sw[0], i0 = z.y * sw[0];
+    const float r1 = z.z * sw[1], i1 = z.w * sw[1];
+    if constexpr (OUTK == OUT_NATIVE) {
+      float* q = static_cast<float*>(qout);
+      *reinterpret_cast<float2*>(q + o) = make_float2(r0, r1);
+      *reinterpret_cast<float2*>(q + o + imoff) = make_float2(i0, i1);
+    } else {
+      __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
+      const uint32_t hr = pack_bf16x2(r0, r1), hi = pack_bf16x2(i0, i1);
+      *reinterpret_cast<uint32_t*>(qh + o) = hr;
+      *reinterpret_cast<uint32_t*>(qh + o + imoff) = hi;
+      if constexpr (OUTK == OUT_BF16X3) {
+        __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qlo);
+        *reinterpret_cast<uint32_t*>(ql + o) = pack_bf16x2(r0 - bf16_lo_f(hr), r1 - bf16_hi_f(hr));
+        *reinterpret_cast<uint32_t*>(ql + o + imoff) = pack_bf16x2(i0 - bf16_lo_f(hi), i1 - bf16_hi_f(hi));
+      }
+    }
+  }
+}
+
 template <int OUTK, int TP, int N>
 __device__ __forceinline__ void output_phase(const float2* __restrict__ src, const PipeArgs& a, int l,
                                              int64_t lm0, const float (&sw)[4], void* __restrict__ qout,
@@ -278,7 +327,7 @@ struct PipeLayout {
 // otherwise one CTA gets the whole register file
 template <int TP, int N> constexpr int pipe_min_blocks() { return TP == 16 && N <= 512 ? 2 : 1; }
 
-template <typename Tin, int OUTK, int TP, int N>
+template <typename Tin, int OUTK, int TP, int N, bool CPLX>
 __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_fft_pipe(const __grid_constant__ CUtensorMap xmap,
                                                           const float* __restrict__ win,
                                                           const float2* __restrict__ tw_g,
@@ -337,7 +386,8 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
     const int64_t lm0 = t * PTP;
     const int64_t gm0 = a.m0 + lm0;
     float mhi0 = 0.f, mlo0 = 0.f, mhi1 = 0.f, mlo1 = 0.f;
-    float sw[4];                     // 0.5 sqrt(W) of the output phase's four points (zero past mcount)
+    float sw[4];                     // 0.5 sqrt(W) of the output phase's four points (zero past mcount);
+                                     // complex data: sqrt(W) of its two points
     {
       const int64_t lm = lm0 + 2 * col;
       if (a.subtract_mean && lm < a.mcount) {
@@ -347,9 +397,15 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
         const double d = mu[gm0 + 2 * col + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
       }
       const int cp = tid % Geo<TP>::OUTCP;
+      if constexpr (CPLX) {          // components -> points
+        const int64_t lp = lm0 / 2 + 2 * cp, gp = gm0 / 2 + 2 * cp;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        sw[q] = (lm0 + 4 * cp + q < a.mcount) ? 0.5f * sqrtW[gm0 + 4 * cp + q] : 0.f;
+        for (int q = 0; q < 4; ++q) sw[q] = (q < 2 && 2 * (lp + q) < a.mcount) ? sqrtW[gp + q] : 0.f;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          sw[q] = (lm0 + 4 * cp + q < a.mcount) ? 0.5f * sqrtW[gm0 + 4 * cp + q] : 0.f;
+      }
     }
     int rb = 0;                      // ring slot of the block's first row
     for (int l = 0; l < a.nb; ++l) {
@@ -369,7 +425,8 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
         }
       }
       const float2* spec = S::template rest<TP>(bA, bB, tw);
-      output_phase<OUTK, TP, N>(spec, a, l, lm0, sw, qout, qlo);
+      if constexpr (CPLX) output_phase_cplx<OUTK, TP, N>(spec, a, l, lm0 / 2, sw, qout, qlo);
+      else output_phase<OUTK, TP, N>(spec, a, l, lm0, sw, qout, qlo);
       rb += a.step;
       if (rb >= N) rb -= N;
       par ^= (S::P & 1);
@@ -380,19 +437,22 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
   if (tid == 0 && !last_ok) mbar_drain(bar, (phase - 1) & 1, gflags);
 }
 
-template <typename Tin, int OUTK, int TP, int N>
+// Complex data (CPLX): m0 and mcount count points; the ring, the mean and the
+// tiles work on the 2M interleaved components.
+template <typename Tin, int OUTK, int TP, int N, bool CPLX>
 cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
   constexpr int PTHREADS = Geo<TP>::THREADS;
+  constexpr int64_t K = CPLX ? 2 : 1;          // components per point
   PipeArgs a;
-  a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
-  const int64_t mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
+  a.m0 = K * m0; a.mcount = K * mcount; a.chunk = p.chunk_points;
+  const int64_t mpad = K * std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
   a.ntiles = mpad / TP;
   a.step = p.step; a.nb = p.nb; a.nf = p.nf;
   a.boxr = p.ring_boxr;
   a.subtract_mean = p.desc.subtract_mean;
   const size_t smem = PipeLayout<Tin, TP, N>::dyn;
-  auto kern = k_fft_pipe<Tin, OUTK, TP, N>;
+  auto kern = k_fft_pipe<Tin, OUTK, TP, N, CPLX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
@@ -405,34 +465,34 @@ cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
   return cudaGetLastError();
 }
 
-template <typename Tin, int OUTK>
+template <typename Tin, int OUTK, bool CPLX>
 cudaError_t launch_pipe_t(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
   if constexpr (sizeof(Tin) <= 4) {
     if (p.pipe_tp == 32) {
       switch (p.nfft) {
-        case 256: return launch_pipe_n<Tin, OUTK, 32, 256>(p, xmap, m0, mcount, s);
-        case 384: return launch_pipe_n<Tin, OUTK, 32, 384>(p, xmap, m0, mcount, s);
-        case 512: return launch_pipe_n<Tin, OUTK, 32, 512>(p, xmap, m0, mcount, s);
+        case 256: return launch_pipe_n<Tin, OUTK, 32, 256, CPLX>(p, xmap, m0, mcount, s);
+        case 384: return launch_pipe_n<Tin, OUTK, 32, 384, CPLX>(p, xmap, m0, mcount, s);
+        case 512: return launch_pipe_n<Tin, OUTK, 32, 512, CPLX>(p, xmap, m0, mcount, s);
         default: return cudaErrorInvalidValue;
       }
     }
   }
   if (p.pipe_tp != 16) return cudaErrorInvalidValue;
   switch (p.nfft) {
-    case 256: return launch_pipe_n<Tin, OUTK, 16, 256>(p, xmap, m0, mcount, s);
-    case 384: return launch_pipe_n<Tin, OUTK, 16, 384>(p, xmap, m0, mcount, s);
-    case 512: return launch_pipe_n<Tin, OUTK, 16, 512>(p, xmap, m0, mcount, s);
-    default: return launch_pipe_n<Tin, OUTK, 16, 720>(p, xmap, m0, mcount, s);
+    case 256: return launch_pipe_n<Tin, OUTK, 16, 256, CPLX>(p, xmap, m0, mcount, s);
+    case 384: return launch_pipe_n<Tin, OUTK, 16, 384, CPLX>(p, xmap, m0, mcount, s);
+    case 512: return launch_pipe_n<Tin, OUTK, 16, 512, CPLX>(p, xmap, m0, mcount, s);
+    default: return launch_pipe_n<Tin, OUTK, 16, 720, CPLX>(p, xmap, m0, mcount, s);
   }
 }
 
-template <typename Tin>
+template <typename Tin, bool CPLX = false>
 cudaError_t launch_pipe_in(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                            cudaStream_t s) {
-  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_pipe_t<Tin, OUT_BF16X3>(p, xmap, m0, mcount, s);
-  if (p.desc.precision == SPOD_PREC_BF16) return launch_pipe_t<Tin, OUT_BF16>(p, xmap, m0, mcount, s);
-  return launch_pipe_t<Tin, OUT_NATIVE>(p, xmap, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_pipe_t<Tin, OUT_BF16X3, CPLX>(p, xmap, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16) return launch_pipe_t<Tin, OUT_BF16, CPLX>(p, xmap, m0, mcount, s);
+  return launch_pipe_t<Tin, OUT_NATIVE, CPLX>(p, xmap, m0, mcount, s);
 }
 
 template <typename Tin, int TP>
@@ -461,9 +521,11 @@ size_t pipe_smem_tp(int nfft, int tp) {
 // Dynamic shared memory of the pipelined kernel with tp-point tiles, 0 when
 // nfft (or the input type) has no compiled form for that tile.
 size_t fft_pipe_smem_bytes(const spod_plan_s& p, int tp) {
-  if (p.desc.in_dtype == SPOD_F64) return pipe_smem_tp<double>(p.nfft, tp);
-  if (p.desc.in_dtype == SPOD_F32) return pipe_smem_tp<float>(p.nfft, tp);
-  return pipe_smem_tp<__nv_bfloat16>(p.nfft, tp);
+  switch (p.desc.in_dtype) {
+    case SPOD_F64: case SPOD_C128: return pipe_smem_tp<double>(p.nfft, tp);
+    case SPOD_F32: case SPOD_C64: return pipe_smem_tp<float>(p.nfft, tp);
+    default: return pipe_smem_tp<__nv_bfloat16>(p.nfft, tp);
+  }
 }
 
 // Tile width of the pipelined kernel: 32 points when that form exists and
@@ -475,7 +537,10 @@ int fft_pipe_tile(const spod_plan_s& p, int smem_optin) {
 
 bool fft_pipe_usable(const spod_plan_s& p, int smem_optin) {
   if (p.f64 || p.ring_boxr <= 0) return false;
-  const size_t el = p.desc.in_dtype == SPOD_F64 ? 8 : (p.desc.in_dtype == SPOD_F32 ? 4 : 2);
+  const size_t el = p.desc.in_dtype == SPOD_F64 || p.desc.in_dtype == SPOD_C64 ? 8
+                   : p.desc.in_dtype == SPOD_C128                              ? 16
+                   : p.desc.in_dtype == SPOD_F32                               ? 4
+                                                                               : 2;
   if ((p.M * (int64_t)el) % 16 != 0) return false;          // TMA row stride
   if (p.nfft % p.ring_boxr != 0 || p.step % p.ring_boxr != 0) return false;
   const size_t smem = fft_pipe_smem_bytes(p, p.pipe_tp);
@@ -484,9 +549,13 @@ bool fft_pipe_usable(const spod_plan_s& p, int smem_optin) {
 
 cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                                   cudaStream_t s) {
-  if (p.desc.in_dtype == SPOD_F64) return launch_pipe_in<double>(p, xmap, m0, mcount, s);
-  if (p.desc.in_dtype == SPOD_F32) return launch_pipe_in<float>(p, xmap, m0, mcount, s);
-  return launch_pipe_in<__nv_bfloat16>(p, xmap, m0, mcount, s);
+  switch (p.desc.in_dtype) {
+    case SPOD_F64: return launch_pipe_in<double>(p, xmap, m0, mcount, s);
+    case SPOD_F32: return launch_pipe_in<float>(p, xmap, m0, mcount, s);
+    case SPOD_C64: return launch_pipe_in<float, true>(p, xmap, m0, mcount, s);
+    case SPOD_C128: return launch_pipe_in<double, true>(p, xmap, m0, mcount, s);
+    default: return launch_pipe_in<__nv_bfloat16>(p, xmap, m0, mcount, s);
+  }
 }
 
 }  // namespace spod

@@ -68,7 +68,16 @@ std::vector<double> make_window(const spod_plan_desc& d) {
   return w;
 }
 
-size_t elem_bytes(spod_dtype t) { return t == SPOD_F64 ? 8 : (t == SPOD_F32 ? 4 : 2); }
+size_t elem_bytes(spod_dtype t) {
+  switch (t) {
+    case SPOD_F64: return 8;
+    case SPOD_F32: return 4;
+    case SPOD_BF16: return 2;
+    case SPOD_C64: return 8;
+    default: return 16;
+  }
+}
+bool is_complex(spod_dtype t) { return t == SPOD_C64 || t == SPOD_C128; }
 
 spod_status check_plan(spod_plan_t p) {
   if (!p) return fail(SPOD_EINVAL, "plan is NULL");
@@ -134,12 +143,15 @@ void* driver_encode_fn() {
 spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) {
   auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p->encode_fn);
   if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available");
-  const size_t el = elem_bytes(p->desc.in_dtype);
-  const CUtensorMapDataType dt = p->desc.in_dtype == SPOD_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                 : p->desc.in_dtype == SPOD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const cuuint64_t dims[2] = {(cuuint64_t)p->M, (cuuint64_t)p->nt};
-  const cuuint64_t strides[1] = {(cuuint64_t)p->M * el};
+  // complex data: a [nt][2M] array of interleaved real components
+  const spod_dtype t = p->desc.in_dtype;
+  const int64_t cols = p->cplx ? 2 * p->M : p->M;
+  const size_t el = p->cplx ? elem_bytes(t) / 2 : elem_bytes(t);
+  const CUtensorMapDataType dt = t == SPOD_F64 || t == SPOD_C128 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : t == SPOD_F32 || t == SPOD_C64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)p->nt};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * el};
   const cuuint32_t box[2] = {(cuuint32_t)(p->pipe_ok ? p->pipe_tp : 16), (cuuint32_t)p->ring_boxr};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, dt, 2, const_cast<void*>(d_X), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -264,7 +276,8 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   if (d->nfft < 2) return fail(SPOD_EINVAL, "nfft must be >= 2");
   if (d->noverlap < 0 || d->noverlap >= d->nfft) return fail(SPOD_EINVAL, "need 0 <= noverlap < nfft");
   if (d->nt < d->nfft) return fail(SPOD_EINVAL, "need nfft <= nt");
-  if (d->in_dtype != SPOD_F64 && d->in_dtype != SPOD_F32 && d->in_dtype != SPOD_BF16)
+  if (d->in_dtype != SPOD_F64 && d->in_dtype != SPOD_F32 && d->in_dtype != SPOD_BF16 && d->in_dtype != SPOD_C64 &&
+      d->in_dtype != SPOD_C128)
     return fail(SPOD_EINVAL, "unknown in_dtype");
   if (d->precision < SPOD_PREC_FP64 || d->precision > SPOD_PREC_BF16X3) return fail(SPOD_EINVAL, "unknown precision");
   if (d->norm != SPOD_NORM_NB && d->norm != SPOD_NORM_NB_MINUS_1) return fail(SPOD_EINVAL, "unknown norm");
@@ -287,7 +300,8 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->noverlap = d->noverlap;
   p->step = d->nfft - d->noverlap;
   p->nb = (int)((d->nt - d->noverlap) / p->step);
-  p->nf = d->nfft / 2 + 1;
+  p->cplx = is_complex(d->in_dtype);
+  p->nf = p->cplx ? d->nfft : d->nfft / 2 + 1;     // two-sided for complex data
   p->f64 = d->precision == SPOD_PREC_FP64;
   p->tensor = d->precision == SPOD_PREC_BF16 || d->precision == SPOD_PREC_BF16X3;
   auto bail = [&](spod_status st, const std::string& m) {
@@ -332,7 +346,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     int boxr = 0;
     for (int dv = std::min(g, 256); dv >= 1; --dv)
       if (g % dv == 0) { boxr = dv; break; }
-    const size_t rowb = 16 * elem_bytes(d->in_dtype);
+    const size_t rowb = 16 * (is_complex(d->in_dtype) ? elem_bytes(d->in_dtype) / 2 : elem_bytes(d->in_dtype));
     p->ring_boxr = ((size_t)boxr * rowb) % 128 == 0 ? boxr : 0;
   }
   if (fft_smem_bytes(*p) > (size_t)prop.sharedMemPerBlockOptin)
@@ -353,7 +367,11 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t per_point = (size_t)p->nf * 2 * p->nb * qelem * nq;
   int64_t chunk = d->chunk_points;
   if (chunk == 0) {
-    const size_t budget = (size_t)40 << 30;   // whole-array Qhat up to 40 GiB, else spatial chunks
+    // whole-array Qhat up to the larger of 40 GiB and 35 % of the device memory
+    // free now (the modes then reuse it), else spatial chunks
+    size_t budget = (size_t)40 << 30, free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::max(budget, free_b / 100 * 35);
+    else cudaGetLastError();
     chunk = (int64_t)std::min<size_t>((size_t)M, std::max<size_t>(budget / per_point, tile));
   }
   chunk = std::min<int64_t>(chunk, M);
@@ -361,7 +379,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->chunk_points = chunk;
   p->Mpad = ((M + tile - 1) / tile) * tile;
   {
-    const int64_t ctas = (M + 255) / 256;
+    const int64_t ctas = ((p->cplx ? 2 * M : M) + 255) / 256;
     int64_t sp = (1216 + ctas - 1) / ctas;
     sp = std::max<int64_t>(1, std::min<int64_t>(sp, p->nt / 16 > 0 ? p->nt / 16 : 1));
     p->mean_splits = (int)std::min<int64_t>(sp, 4096);
@@ -380,8 +398,9 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   size_t off = 0;
   auto carve = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const size_t o_flags = carve(4 * sizeof(unsigned));
-  const size_t o_mu = carve(sizeof(double) * M);
-  const size_t o_mupart = carve(sizeof(double) * M * p->mean_splits);
+  const int64_t Mr = p->cplx ? 2 * M : M;          // real columns of X (complex: re, im interleaved)
+  const size_t o_mu = carve(sizeof(double) * Mr);
+  const size_t o_mupart = carve(sizeof(double) * Mr * p->mean_splits);
   const size_t o_win = carve(R * p->nfft);
   const size_t o_tw = carve(2 * R * p->nfft);
   const size_t o_sqrtW = carve(R * p->Mpad);
@@ -436,8 +455,10 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     cudaDeviceProp prop2;
     const bool q = p->encode_fn && cudaGetDeviceProperties(&prop2, p->device) == cudaSuccess;
     if (q) p->pipe_tp = fft_pipe_tile(*p, (int)prop2.sharedMemPerBlockOptin);
+    // the runtime-radix ring kernel handles real data only; complex data takes
+    // the pipelined kernel (compiled nfft) or the per-block one
     p->pipe_ok = q && fft_pipe_usable(*p, (int)prop2.sharedMemPerBlockOptin);
-    p->ring_ok = p->pipe_ok || (q && fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin));
+    p->ring_ok = p->pipe_ok || (!p->cplx && q && fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin));
   }
   if (p->tensor) {
     if (spod_status st = make_qhat_maps(p)) {
@@ -552,7 +573,8 @@ static spod_status fit_impl(spod_plan_t p, const void* d_X, cudaStream_t s, int6
   p->fitted = false;
   p->qhat_valid = false;
   SPOD_CUDA(cudaMemsetAsync(p->d_flags, 0, 4 * sizeof(unsigned), s), "clear flags");
-  if (!p->desc.subtract_mean) SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M, s), "zero mean");
+  if (!p->desc.subtract_mean)
+    SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M * (p->cplx ? 2 : 1), s), "zero mean");
   alignas(64) CUtensorMap xmap;
   const CUtensorMap* xm = nullptr;
   if (p->ring_ok) {
@@ -636,7 +658,10 @@ spod_status spod_get_gram(spod_plan_t p, double* gram) {
 spod_status spod_get_freqs(spod_plan_t p, double* freqs) {
   if (spod_status st = check_plan(p)) return st;
   if (!freqs) return fail(SPOD_EINVAL, "freqs is NULL");
-  for (int f = 0; f < p->nf; ++f) freqs[f] = (double)f / ((double)p->nfft * p->desc.dt);
+  for (int f = 0; f < p->nf; ++f) {
+    const int fs = (p->cplx && f >= (p->nfft + 1) / 2) ? f - p->nfft : f;
+    freqs[f] = (double)fs / ((double)p->nfft * p->desc.dt);
+  }
   return SPOD_OK;
 }
 
@@ -708,6 +733,7 @@ spod_status spod_modes(spod_plan_t p, const void* d_X, int nmodes, void* d_Phi, 
 
 spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* d_X, void* d_dX, void* stream) {
   if (spod_status st = check_plan(p)) return st;
+  if (p->cplx) return fail(SPOD_EUNSUPPORTED, "spod_backward supports real data only");
   if (!p->fitted) return fail(SPOD_ESTATE, "spod_backward before spod_fit");
   if (!d_dLdlambda || reinterpret_cast<uintptr_t>(d_dLdlambda) % 8) return fail(SPOD_EINVAL, "d_dLdlambda NULL or misaligned");
   if (spod_status st = check_ptr(d_dX, "d_dX")) return st;

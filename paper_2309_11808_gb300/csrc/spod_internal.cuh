@@ -75,6 +75,7 @@ struct spod_plan_s {
   int modes_ctas = 0;         // tensor-core modes: CTAs per frequency (0 = automatic)
   int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
   bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
+  bool cplx = false;          // complex input: two-sided spectrum, complex mean
   bool pipe_ok = false;       // the pipelined kernel (compiled nfft) is used
   int pipe_tp = 16;           // its tile width in points (16 or 32; also the X map's box width)
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled

@@ -71,7 +71,11 @@ def lam_gate_report(lam, ref, k=5, cond=10.0):
     return float(rel[well].max()), normwise, float(rel[keep].max())
 
 
-def mode_err(Phi, ref_fit, d, W, nmodes, gap=1e-2):
+def mode_err(Phi, ref_fit, d, W, nmodes, gap=1e-2, cond=None):
+    """Worst 1 - |<phi, phi_ref>_W| over modes whose relative eigen-gap is >= gap
+    (and, with cond, whose lambda_1 / lambda_k <= cond: a Gram perturbation dM
+    turns psi_k by about ||dM|| / (gap * lambda_k), so modes far below lambda_1
+    are Weyl-limited like their eigenvalues)."""
     Pref = O.spod_modes(ref_fit, d, nmodes)
     lam = ref_fit.lam
     Wv = np.ones(d.M) if W is None else np.asarray(W, dtype=np.float64)
@@ -79,7 +83,7 @@ def mode_err(Phi, ref_fit, d, W, nmodes, gap=1e-2):
     for f in range(lam.shape[0]):
         for k in range(nmodes):
             lk = lam[f, k]
-            if lk <= 1e-8 * lam[f, 0]:
+            if lk <= 1e-8 * lam[f, 0] or (cond is not None and lk * cond < lam[f, 0]):
                 continue
             nb = []
             if k > 0:
@@ -362,3 +366,93 @@ def test_tensor_path_chunked_matches_single_pass(nfft):
     assert (np.abs(la - lb).max(axis=1) / la[:, 0]).max() <= 2e-6
     well = la * 10.0 >= la[:, :1]
     assert (np.abs(la - lb) / la)[well].max() <= 1e-5
+
+
+# ---------------------------------------------------------------- complex data
+@cuda
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_complex_input_two_sided(prec):
+    g = torch.Generator().manual_seed(31)
+    npts, nvars, nt, nfft, nov = 300, 2, 700, 48, 24
+    M = npts * nvars
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    # planted complex exponentials at a positive and a negative bin plus noise
+    t = torch.arange(nt, dtype=torch.float64)[:, None]
+    ph1 = torch.randn(M, generator=g, dtype=torch.float64) + 1j * torch.randn(M, generator=g, dtype=torch.float64)
+    ph2 = torch.randn(M, generator=g, dtype=torch.float64) + 1j * torch.randn(M, generator=g, dtype=torch.float64)
+    X = (2.0 * ph1[None] * torch.exp(2j * np.pi * 5 * t / nfft) + ph2[None] * torch.exp(-2j * np.pi * 11 * t / nfft)
+         + 0.3 * (torch.randn(nt, M, generator=g, dtype=torch.float64)
+                  + 1j * torch.randn(nt, M, generator=g, dtype=torch.float64)) + (1.0 - 0.5j))
+    W = (0.5 + torch.rand(M, generator=g, dtype=torch.float64)).numpy()
+    sp = SPOD(npts, nvars, nt, nfft, nov, dtype=cdt, precision=prec, weights=W)
+    assert sp.nf == nfft
+    Xd = X.to(cdt).to(DEV).contiguous()
+    sp.fit(Xd)
+    lam = sp.eigs()
+    Phi = sp.modes(Xd, 3).cpu().numpy()
+    freqs = sp.freqs() if hasattr(sp, "freqs") else None
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, weights=W, complex_input=True)
+    ref = O.spod_fit(X.to(cdt).to(torch.complex128).numpy(), d)
+    tol = 1e-10 if prec == "fp64" else (1e-4 if prec == "fp32" else 1e-5)
+    if prec == "bf16x3":
+        rel, normwise, _ = lam_gate_report(lam, ref.lam, 5)
+        assert rel <= tol and normwise <= tol
+    else:
+        assert lam_rel_err(lam, ref.lam, None if prec == "fp64" else 5) <= tol
+    assert mode_err(Phi, ref, d, W, 3) <= (1e-8 if prec == "fp64" else 1e-4)
+    # the planted bins: +5 and the negative bin -11 (index nfft - 11) lead
+    assert lam[5, 0] > 10 * lam[nfft - 5, 0] and lam[nfft - 11, 0] > 10 * lam[11, 0]
+    if freqs is not None:
+        assert np.isclose(freqs[nfft - 11], -11.0 / nfft)
+    with pytest.raises(SpodError) as e:
+        dX = torch.empty(nt, M, dtype=dt, device=DEV)
+        _lib.spod_backward(sp.handle, torch.zeros(sp.nf, sp.nb, dtype=torch.float64, device=DEV), Xd, dX)
+    assert e.value.status == _lib.SPOD_EUNSUPPORTED
+    sp.close()
+
+
+@cuda
+def test_real_data_as_complex_on_the_device():
+    wl = jet_like(nx=16, nr=8, nvars=1, nt=600, nfft=64, seed=8, dtype=torch.float64)
+    spr = SPOD(wl.npoints, 1, 600, 64, 32, dtype=torch.float64, precision="fp64", weights=wl.W)
+    spc = SPOD(wl.npoints, 1, 600, 64, 32, dtype=torch.complex128, precision="fp64", weights=wl.W)
+    Xr = wl.X.to(DEV)
+    spr.fit(Xr)
+    spc.fit(Xr.to(torch.complex128).contiguous())
+    lr, lc = spr.eigs(), spc.eigs()
+    np.testing.assert_allclose(lc[:33], lr, rtol=1e-10, atol=1e-13 * lr.max())
+    np.testing.assert_allclose(lc[64 - 20], lc[20], rtol=1e-10, atol=1e-13 * lr.max())
+    spr.close()
+    spc.close()
+
+
+@cuda
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("nfft", [256, 384])
+def test_complex_input_pipelined_fft(prec, nfft):
+    # compiled nfft: complex data through the TMA-ring pipelined FFT (32-point
+    # component tiles), ragged M, against the two-sided FP64 oracle
+    g = torch.Generator().manual_seed(nfft)
+    npts, nt = 203, 3 * nfft
+    t = torch.arange(nt, dtype=torch.float64)[:, None]
+    ph = torch.randn(npts, generator=g, dtype=torch.float64) + 1j * torch.randn(npts, generator=g, dtype=torch.float64)
+    X = (ph[None] * torch.exp(-2j * np.pi * 17 * t / nfft)
+         + 0.5 * (torch.randn(nt, npts, generator=g, dtype=torch.float64)
+                  + 1j * torch.randn(nt, npts, generator=g, dtype=torch.float64)) + 0.7j)
+    W = (0.5 + torch.rand(npts, generator=g, dtype=torch.float64)).numpy()
+    sp = SPOD(npts, 1, nt, nfft, nfft // 2, dtype=torch.complex64, precision=prec, weights=W)
+    Xd = X.to(torch.complex64).to(DEV).contiguous()
+    sp.fit(Xd)
+    lam = sp.eigs()
+    Phi = sp.modes(Xd, 2).cpu().numpy()
+    d = O.Desc(nt=nt, M=npts, nfft=nfft, noverlap=nfft // 2, weights=W, complex_input=True)
+    ref = O.spod_fit(X.to(torch.complex64).to(torch.complex128).numpy(), d, dft="fft")
+    # the planted bin has lambda_1 / lambda_5 in the hundreds: gated as the
+    # design notes state (relative where lambda_1 / lambda_j <= 10, normwise)
+    rel, normwise, _ = lam_gate_report(lam, ref.lam, 5)
+    tol = 1e-5 if prec == "bf16x3" else 1e-4
+    assert rel <= tol and normwise <= tol
+    assert mode_err(Phi, ref, d, W, 2, cond=10.0) <= 1e-4
+    assert lam[nfft - 17, 0] > 10 * lam[17, 0]
+    sp.close()
