@@ -499,3 +499,52 @@ def gram_at_freqs(d: Desc, fsel, get_chunk, chunk: int) -> np.ndarray:
         Qw = np.conj(Q) * W[None, None, m0:m1]
         acc += np.matmul(Qw, np.transpose(Q, (0, 2, 1)))
     return acc / gram_denominator(d.nb, d.norm)
+
+
+# --------------------------------------------------------------------------
+# Expansion coefficients and reconstruction (SPOD for data compression,
+# Eqs. coeffs and SPODrec)
+# --------------------------------------------------------------------------
+def is_self_conjugate_bin(f: int, nfft: int) -> bool:
+    """DC and (even nfft) Nyquist: the one-sided bins of real data whose DFT is real."""
+    return f == 0 or (nfft % 2 == 0 and f == nfft // 2)
+
+
+def coeff_basis(Phi: np.ndarray, fsel, nmodes_r: int, nfft: int) -> tuple[np.ndarray, list]:
+    """Columns of Phi_r for real data: the leading nmodes_r modes of every
+    selected one-sided bin and, for the bins other than DC and Nyquist, their
+    complex conjugates (the modes of the negative frequency -f, so that the
+    two-sided set is closed under conjugation and the reconstruction of real
+    data is real).  Returns P [M][K] and the (bin, mode, conjugated) labels."""
+    cols, labels = [], []
+    for f in fsel:
+        for k in range(nmodes_r):
+            cols.append(Phi[f, k])
+            labels.append((f, k, False))
+            if not is_self_conjugate_bin(f, nfft):
+                cols.append(np.conj(Phi[f, k]))
+                labels.append((f, k, True))
+    return np.stack(cols, axis=1), labels
+
+
+def expansion_coefficients(X: np.ndarray, d: Desc, Phi: np.ndarray, fsel, nmodes_r: int,
+                           mu: np.ndarray | None = None):
+    """A = (Phi_r^* W Phi_r)^{-1} Phi_r^* W Q  (Eq. coeffs), Q = X^T - mu (M x nt).
+
+    Returns (A [K][nt] complex, P [M][K], labels).  The solve is a plain dense
+    one of the Hermitian positive definite K x K system."""
+    X = np.asarray(X, dtype=np.float64)
+    if mu is None:
+        mu = time_mean(X) if d.subtract_mean else np.zeros(d.M)
+    P, labels = coeff_basis(Phi, fsel, nmodes_r, d.nfft)
+    W = d.W()
+    PW = np.conj(P).T * W[None, :]                  # Phi_r^* W  [K][M]
+    G = PW @ P
+    A = np.linalg.solve(G, PW @ (X - mu[None, :]).T)
+    return A, P, labels
+
+
+def reconstruct(A: np.ndarray, P: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """Q~ = Phi_r A_r  (Eq. SPODrec), as data [nt][M]: Re(P A)^T + mu (the
+    imaginary part vanishes for a conjugation-closed set of modes)."""
+    return (P @ A).real.T + mu[None, :]

@@ -430,3 +430,51 @@ def test_planted_complex_exponential_sits_in_one_bin():
         np.testing.assert_allclose(fit.lam[kk, 0], a * a * (0.23 / 0.54) ** 2, rtol=1e-12)
     assert fit.lam[nfft - k].max() <= 1e-24 * a * a
     assert fit.lam[k, 1:].max() <= 1e-12 * a * a                  # rank one
+
+
+# ---------------------------------------------------------------- expansion coefficients
+def _coeff_case(M=6, nt=256, nfft=8, nov=4, seed=41):
+    rs = np.random.RandomState(seed)
+    X = rs.randn(nt, M) + 0.5
+    W = 0.5 + rs.rand(M)
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, weights=W)
+    fit = O.spod_fit(X, d)
+    return X, d, fit
+
+
+def test_expansion_full_span_reconstructs_the_data():
+    # 6 points, nfft = 8: the leading mode of bins 0 and 4 (DC, Nyquist: real)
+    # and of bins 1, 2 with their conjugates give six columns spanning C^6, so
+    # the oblique projection is the identity
+    X, d, fit = _coeff_case()
+    Phi = O.spod_modes(fit, d, 1)
+    A, P, labels = O.expansion_coefficients(X, d, Phi, [0, 1, 2, 4], 1)
+    assert P.shape == (6, 6) and np.linalg.cond(P) < 1e6
+    Xr = O.reconstruct(A, P, fit.mu)
+    np.testing.assert_allclose(Xr, X, rtol=0, atol=1e-10 * np.abs(X).max())
+    assert np.abs((P @ A).imag).max() <= 1e-10 * np.abs(X).max()
+
+
+def test_expansion_residual_is_w_orthogonal_and_projection_idempotent():
+    X, d, fit = _coeff_case(M=20, nt=400, nfft=16, nov=8, seed=42)
+    Phi = O.spod_modes(fit, d, 2)
+    A, P, labels = O.expansion_coefficients(X, d, Phi, [0, 2, 5], 2)
+    Xr = O.reconstruct(A, P, fit.mu)
+    R = (X - Xr).T                                               # M x nt residual
+    res = np.conj(P).T @ (d.W()[:, None] * R)
+    assert np.abs(res).max() <= 1e-10 * np.abs(X).max()
+    # projecting the reconstruction again leaves it unchanged
+    A2, _, _ = O.expansion_coefficients(Xr, d, Phi, [0, 2, 5], 2, mu=fit.mu)
+    np.testing.assert_allclose(A2, A, rtol=0, atol=1e-10 * np.abs(A).max())
+    assert len(labels) == 2 * (1 + 2 + 2)
+
+
+def test_expansion_dc_modes_are_w_orthonormal_so_coefficients_are_projections():
+    # DC modes are real and W-orthonormal, and carry no conjugate: G = I and
+    # A = Phi^T W (X - mu)^T
+    X, d, fit = _coeff_case(M=20, nt=400, nfft=16, nov=8, seed=43)
+    Phi = O.spod_modes(fit, d, 3)
+    A, P, _ = O.expansion_coefficients(X, d, Phi, [0], 3)
+    assert np.abs(P.imag).max() <= 1e-12
+    direct = (P.real.T * d.W()[None, :]) @ (X - fit.mu[None, :]).T
+    np.testing.assert_allclose(A.real, direct, rtol=0, atol=1e-10 * np.abs(direct).max())
