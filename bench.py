@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--small", action="store_true", help="a reduced grid for quick checks (not a bench value)")
     ap.add_argument("--grid", default=None, help="NXxNR grid for profiling runs (not a bench value)")
+    ap.add_argument("--coeffs", action="store_true",
+                    help="time the expansion coefficients + reconstruction (Eqs. coeffs, SPODrec) on a "
+                         "256x128x2, nt=4096, nfft=256 grid; a separate measurement, not the headline line")
     ap.add_argument("--complex", action="store_true",
                     help="complex input of the same shape (the jet field + i x a second seed's field, "
                          "two-sided spectrum); a separate measurement, not the headline line")
@@ -162,6 +165,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.impl == "reference":
         return reference_leg(args, world, rank)
+    if args.coeffs:
+        return coeffs_leg(args, rank)
 
     import __graft_entry__ as g
     from paper_2309_11808_gb300 import _lib
@@ -443,6 +448,58 @@ def step_roofline(ms_step, M, nb, nf, nmodes, peaks, precision):
     return {"t_roof_ms": round(t_roof * 1e3, 3), "frac": round(t_roof * 1e3 / ms_step, 4),
             "t_hbm_ms": round(t_hbm * 1e3, 3), "t_gemm_ms": round(t_gemm * 1e3, 3), "t_fft_ms": round(t_fft * 1e3, 3),
             "bytes": int(B), "note": "B = X read once + Phi written; a Qhat round trip counts against the step"}
+
+
+def coeffs_leg(args, rank):
+    """Expansion coefficients of the leading 2 modes at 16 bins (with their
+    conjugates: K = 62 real basis vectors) and the reconstruction, timed with
+    CUDA events after a fit + modes of the same grid."""
+    import torch
+    import __graft_entry__ as g
+    from paper_2309_11808_gb300 import SPOD, _lib
+    from workloads import jet_like
+    g.build()
+    dev = torch.device("cuda", 0)
+    nx, nr, nv, nt, nfft = 256, 128, 2, 4096, 256
+    wl = jet_like(nx=nx, nr=nr, nvars=nv, nt=nt, nfft=nfft, seed=rank, dtype=torch.float32, device=dev)
+    sp = SPOD(wl.npoints, nv, nt, nfft, nfft // 2, dtype=torch.float32, precision=args.precision, weights=wl.W)
+    X = wl.X
+    M = X.shape[1]
+    sp.fit(X)
+    nmodes, nr_, fsel = 4, 2, list(range(0, 128, 8)) + [128]
+    fsel = fsel[:16]
+    Phi = sp.modes(X, nmodes)
+    A = torch.empty((len(fsel), nr_, nt), dtype=torch.complex128, device=dev)
+    Xr = torch.empty_like(X)
+    st = torch.cuda.current_stream()
+
+    def call():
+        _lib.spod_coeffs(sp.handle, X, Phi, nmodes, nr_, fsel, A, st)
+        _lib.spod_reconstruct(sp.handle, Phi, nmodes, nr_, fsel, A, Xr, st)
+    for _ in range(max(3, args.warmup)):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        call()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    K = sum(nr_ * (1 if f in (0, nfft // 2) else 2) for f in fsel)
+    flops = 2.0 * K * nt * M * 2 + 2.0 * K * K * M            # the two GEMMs and the basis Gram
+    rel = float((Xr - X).float().pow(2).sum() / (X - X.mean(0)).float().pow(2).sum())
+    line = {"metric": "SPOD expansion coefficients + reconstruction, ms per call", "value": round(ms, 3),
+            "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": max(3, args.warmup),
+            "config": {"workload": f"jet-shaped {nx}x{nr}x{nv}, nt={nt}, nfft={nfft}", "M": M, "nt": nt,
+                       "modes_per_bin": nr_, "bins": fsel, "real_basis_vectors": K, "fit_precision": args.precision,
+                       "gemm": "cuBLAS FP32 (pedantic)"},
+            "roofline": {"bound": "alu", "achieved": round(flops / (ms * 1e-3) / 1e12, 3), "peak": round(FP32_PEAK, 1),
+                         "unit": "TFLOP/s", "frac": round(flops / (ms * 1e-3) / 1e12 / FP32_PEAK, 4),
+                         "flops": flops},
+            "relative_residual_energy": round(rel, 5)}
+    print(json.dumps(line), flush=True)
+    sp.close()
 
 
 def e2e_leg(sp, X, nmodes, args, world):

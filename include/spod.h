@@ -223,6 +223,32 @@ spod_status spod_sync(spod_plan_t plan, void* stream);
  * are returned, device-side conditions by the next spod_sync of each plan. */
 spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream);
 
+/* Expansion coefficients (Eq. coeffs; SPOD for data compression): the
+ * W-weighted oblique projection of the data onto the leading nmodes_r modes
+ * of the nfreq_r one-sided bins h_freqs[] (host, distinct, 0 .. nf-1) and,
+ * for the bins other than DC and Nyquist, their complex conjugates (the
+ * modes of the negative frequencies; the set is then closed under
+ * conjugation and the reconstruction of real data is real):
+ *   A = (Phi_r^* W Phi_r)^{-1} Phi_r^* W (X^T - mu).
+ * d_X: the data of the last fit (device, [nt][M]); d_Phi: modes of the last
+ * fit from spod_modes with nmodes columns (>= nmodes_r), [nf][nmodes][M].
+ * d_A (device, caller-owned): interleaved complex FP64 [nfreq_r][nmodes_r][nt],
+ * the coefficient of mode k at bin h_freqs[j] (the conjugate bin's is its
+ * conjugate).  Real data with F32 input (FP32 / BF16 / BF16X3 plans) or F64
+ * input (FP64 plans) only, else SPOD_EUNSUPPORTED; at most 4096 real basis
+ * vectors.  A basis that is not linearly independent is reported by the
+ * next spod_sync as SPOD_ENOTCONVERGED.  The two large products run as
+ * cuBLAS GEMMs (FP32 or FP64 as the plan) on `stream`.  No counterpart of
+ * this API shape in the paper. */
+spod_status spod_coeffs(spod_plan_t plan, const void* d_X, const void* d_Phi, int nmodes, int nmodes_r, int nfreq_r,
+                        const int* h_freqs, double* d_A, void* stream);
+
+/* Reconstruction (Eq. SPODrec): d_Xrec[t][m] = mu_m + (Phi_r A_r)[m][t] from the
+ * coefficients of spod_coeffs (same nmodes, nmodes_r, h_freqs), in the data's
+ * type (F32 or F64), [nt][M], caller-owned. */
+spod_status spod_reconstruct(spod_plan_t plan, const void* d_Phi, int nmodes, int nmodes_r, int nfreq_r,
+                             const int* h_freqs, const double* d_A, void* d_Xrec, void* stream);
+
 /* Launch-shape knobs (the autotuner's interface).  They change how work is
  * split across CTAs, never what is computed beyond floating-point grouping.
  * In spod_plan_set_tuning a zero field keeps the plan's current value. */

@@ -537,6 +537,7 @@ spod_status spod_plan_destroy(spod_plan_t p) {
     if (p->d_lamstage) cudaFree(p->d_lamstage);
     if (p->d_phistage2) cudaFree(p->d_phistage2);
     for (auto e : p->host_ev) cudaEventDestroy(e);
+    destroy_blas(*p);
     if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
   }
@@ -914,6 +915,52 @@ spod_status spod_run_host_many(spod_plan_t p, int n, const void* const* h_X, int
   }
   DeviceGuard g(p->device);
   return run_host_impl(p, n, h_X, nmodes, h_Phi, h_lambda, static_cast<cudaStream_t>(stream));
+}
+
+// Validation shared by the expansion-coefficient entries.
+static spod_status check_coeff_args(spod_plan_t p, const void* d_Phi, int nmodes, int nmodes_r, int nfreq_r,
+                                    const int* h_freqs) {
+  if (!p->fitted) return fail(SPOD_ESTATE, "expansion coefficients before spod_fit");
+  if (p->cplx) return fail(SPOD_EUNSUPPORTED, "expansion coefficients support real data only");
+  if (p->f64 ? p->desc.in_dtype != SPOD_F64 : p->desc.in_dtype != SPOD_F32)
+    return fail(SPOD_EUNSUPPORTED, "expansion coefficients need F64 data with FP64 precision or F32 data otherwise");
+  if (spod_status st = check_ptr(d_Phi, "d_Phi")) return st;
+  if (nmodes < 1 || nmodes > p->nb || nmodes_r < 1 || nmodes_r > nmodes)
+    return fail(SPOD_EINVAL, "need 1 <= nmodes_r <= nmodes <= nb");
+  if (nfreq_r < 1 || nfreq_r > p->nf || !h_freqs) return fail(SPOD_EINVAL, "need 1 <= nfreq_r <= nf and h_freqs");
+  std::vector<char> seen(p->nf, 0);
+  for (int j = 0; j < nfreq_r; ++j) {
+    if (h_freqs[j] < 0 || h_freqs[j] >= p->nf) return fail(SPOD_EINVAL, "h_freqs entry outside 0 .. nf-1");
+    if (seen[h_freqs[j]]++) return fail(SPOD_EINVAL, "h_freqs entries must be distinct");
+  }
+  if (coeff_basis_size(*p, nmodes_r, nfreq_r, h_freqs) > 4096)
+    return fail(SPOD_EUNSUPPORTED, "more than 4096 real basis vectors");
+  return SPOD_OK;
+}
+
+spod_status spod_coeffs(spod_plan_t p, const void* d_X, const void* d_Phi, int nmodes, int nmodes_r, int nfreq_r,
+                        const int* h_freqs, double* d_A, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (spod_status st = check_coeff_args(p, d_Phi, nmodes, nmodes_r, nfreq_r, h_freqs)) return st;
+  if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  if (spod_status st = check_ptr(d_A, "d_A")) return st;
+  DeviceGuard g(p->device);
+  SPOD_CUDA(launch_coeffs(*p, d_X, d_Phi, nmodes, nmodes_r, nfreq_r, h_freqs, d_A, static_cast<cudaStream_t>(stream)),
+            "expansion coefficients");
+  return SPOD_OK;
+}
+
+spod_status spod_reconstruct(spod_plan_t p, const void* d_Phi, int nmodes, int nmodes_r, int nfreq_r,
+                             const int* h_freqs, const double* d_A, void* d_Xrec, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (spod_status st = check_coeff_args(p, d_Phi, nmodes, nmodes_r, nfreq_r, h_freqs)) return st;
+  if (spod_status st = check_ptr(d_A, "d_A")) return st;
+  if (spod_status st = check_ptr(d_Xrec, "d_Xrec")) return st;
+  DeviceGuard g(p->device);
+  SPOD_CUDA(launch_reconstruct(*p, d_Phi, nmodes, nmodes_r, nfreq_r, h_freqs, d_A, d_Xrec,
+                               static_cast<cudaStream_t>(stream)),
+            "reconstruction");
+  return SPOD_OK;
 }
 
 spod_status spod_plan_get_tuning(spod_plan_t p, spod_tuning* t) {

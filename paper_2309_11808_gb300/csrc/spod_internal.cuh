@@ -76,6 +76,7 @@ struct spod_plan_s {
   int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
   bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
   bool cplx = false;          // complex input: two-sided spectrum, complex mean
+  void* blas = nullptr;       // cuBLAS handle of the expansion-coefficient GEMMs (created on first use)
   bool pipe_ok = false;       // the pipelined kernel (compiled nfft) is used
   int pipe_tp = 16;           // its tile width in points (16 or 32; also the X map's box width)
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
@@ -196,6 +197,13 @@ size_t eig_smem_bytes(int nb);
 size_t eig_tridiag_smem_bytes(int nb);
 size_t eig_tridiag_gws_doubles(int nb, int nf);
 cudaError_t launch_eig_tridiag(const spod_plan_s& p, cudaStream_t s);
+// expansion coefficients / reconstruction (k_coeffs.cu)
+int coeff_basis_size(const spod_plan_s& p, int nmodes_r, int nsel, const int* h_freqs);
+cudaError_t launch_coeffs(spod_plan_s& p, const void* d_X, const void* d_Phi, int nmodes, int nmodes_r, int nsel,
+                          const int* h_freqs, double* d_A, cudaStream_t s);
+cudaError_t launch_reconstruct(spod_plan_s& p, const void* d_Phi, int nmodes, int nmodes_r, int nsel,
+                               const int* h_freqs, const double* d_A, void* d_Xrec, cudaStream_t s);
+void destroy_blas(spod_plan_s& p);
 
 void set_error(const std::string& msg);
 
