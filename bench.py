@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--complex", action="store_true",
                     help="complex input of the same shape (the jet field + i x a second seed's field, "
                          "two-sided spectrum); a separate measurement, not the headline line")
+    ap.add_argument("--ooc", action="store_true",
+                    help="time the out-of-core run (spod_run_host_ooc: X and Phi in pinned host memory, column "
+                         "tiles over the host link) on the headline grid; a separate measurement")
     return ap.parse_args()
 
 
@@ -167,6 +170,8 @@ def main():
         return reference_leg(args, world, rank)
     if args.coeffs:
         return coeffs_leg(args, rank)
+    if args.ooc:
+        return ooc_leg(args, rank)
 
     import __graft_entry__ as g
     from paper_2309_11808_gb300 import _lib
@@ -500,6 +505,58 @@ def coeffs_leg(args, rank):
             "relative_residual_energy": round(rel, 5)}
     print(json.dumps(line), flush=True)
     sp.close()
+
+
+def ooc_leg(args, rank):
+    """The out-of-core run on the headline grid: X (pinned host) is read in
+    column tiles, the modes of every bin written back in tiles; the plan's Qhat
+    chunk is one tile, so the device holds the plan's workspace and four tile
+    buffers, not X, Qhat or Phi.  Wall-clock per call (the call synchronises)."""
+    import torch
+    import __graft_entry__ as g
+    from paper_2309_11808_gb300 import SPOD, _lib
+    from workloads import jet_like
+    g.build()
+    dev = torch.device("cuda", 0)
+    wl = jet_like(nx=NX, nr=NR, nvars=NVARS, nt=NT, nfft=NFFT, seed=rank, dtype=torch.float32, device=dev)
+    M = wl.X.shape[1]
+    hX = torch.empty(wl.X.shape, dtype=torch.float32, pin_memory=True)
+    hX.copy_(wl.X)
+    W = wl.W.cpu()
+    del wl
+    torch.cuda.empty_cache()
+    lines = []
+    for ntile in (4, 8):
+        tile = (M // ntile + 63) // 64 * 64
+        sp = SPOD(NX * NR, NVARS, NT, NFFT, NOVERLAP, dtype=torch.float32, precision=args.precision, weights=W,
+                  chunk_points=tile)
+        nmodes = sp.nb
+        cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
+        hPhi = torch.empty((sp.nf, nmodes, M), dtype=cdt, pin_memory=True)
+        hlam = torch.empty((sp.nf, sp.nb), dtype=torch.float64, pin_memory=True)
+        for _ in range(max(3, args.warmup)):
+            _lib.spod_run_host_ooc(sp.handle, hX, nmodes, hPhi, hlam, tile)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _lib.spod_run_host_ooc(sp.handle, hX, nmodes, hPhi, hlam, tile)
+        dt = (time.perf_counter() - t0) / args.steps
+        eb = hPhi.element_size()
+        tiles_b = 2 * NT * tile * 4 + 2 * sp.nf * nmodes * tile * eb
+        lines.append({"tile_points": tile, "tiles": (M + tile - 1) // tile, "ms_per_call": round(dt * 1e3, 2),
+                      "GB_per_s": round(NT * M * 4 / dt / 1e9, 2),
+                      "host_link_GB_per_s": round((2 * NT * M * 4 + hPhi.numel() * eb) / dt / 1e9, 1),
+                      "device_bytes": int(sp.info.workspace_bytes + tiles_b),
+                      "X_plus_Phi_bytes": int(NT * M * 4 + hPhi.numel() * eb)})
+        sp.close()
+        del hPhi
+    line = {"metric": "SPOD out-of-core run (fit + all modes, host data), ms per call",
+            "value": min(x["ms_per_call"] for x in lines), "unit": "ms", "higher_is_better": False,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "config": {"workload": f"jet-shaped {NX}x{NR}x{NVARS}, nt={NT}, nfft={NFFT}, 50% overlap",
+                       "precision": args.precision, "X": "pinned host memory", "Phi": "pinned host memory"},
+            "runs": lines}
+    print(json.dumps(line), flush=True)
 
 
 def e2e_leg(sp, X, nmodes, args, world):

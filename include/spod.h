@@ -223,6 +223,20 @@ spod_status spod_sync(spod_plan_t plan, void* stream);
  * are returned, device-side conditions by the next spod_sync of each plan. */
 spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, void* stream);
 
+/* Out-of-core run for data larger than device memory (no counterpart of
+ * this API shape in the paper; its data-size argument is Sec. 3.2): h_X and
+ * h_Phi stay in host memory the device can address -- pinned (cudaHostAlloc or
+ * cudaHostRegister), or any host memory on a device that reads pageable memory
+ * through the host's page tables (cudaDevAttrPageableMemoryAccess); otherwise
+ * SPOD_EINVAL -- and are read and written in column tiles of tile_points points
+ * (0: about M/4, rounded to 64, at most the plan's chunk) by copy kernels
+ * over the host link, overlapped with the fit (mean, FFT, Gram per tile) and
+ * with the modes (each tile's Qhat recomputed).  Device memory: the plan's
+ * workspace plus two X tiles and two Phi tiles.  Results equal spod_fit +
+ * spod_modes to rounding (the Gram is summed tile by tile).  Synchronises. */
+spod_status spod_run_host_ooc(spod_plan_t plan, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
+                              int64_t tile_points, void* stream);
+
 /* Expansion coefficients (Eq. coeffs; SPOD for data compression): the
  * W-weighted oblique projection of the data onto the leading nmodes_r modes
  * of the nfreq_r one-sided bins h_freqs[] (host, distinct, 0 .. nf-1) and,

@@ -26,7 +26,8 @@ EXPORTED = ["spod_desc_init", "spod_plan_create", "spod_plan_destroy", "spod_pla
             "spod_get_eigs", "spod_get_gram", "spod_get_freqs", "spod_modes", "spod_backward",
             "spod_run_host", "spod_run_host_many", "spod_sync", "spod_fit_batch", "spod_profile_enable",
             "spod_profile_read", "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning",
-            "spod_plan_autotune", "spod_coeffs", "spod_reconstruct", "spod_last_error", "spod_version"]
+            "spod_plan_autotune", "spod_coeffs", "spod_reconstruct", "spod_run_host_ooc", "spod_last_error",
+            "spod_version"]
 
 PHASES = ["mean", "fft", "gram", "reduce", "eig", "modes", "backward"]
 
@@ -89,6 +90,7 @@ def lib() -> C.CDLL:
         L.spod_plan_set_tuning.argtypes = [P, C.POINTER(spod_tuning)]
         L.spod_plan_autotune.argtypes = [P, P, P, C.POINTER(spod_tuning)]
         L.spod_coeffs.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), P, P]
+        L.spod_run_host_ooc.argtypes = [P, P, C.c_int, P, P, C.c_int64, P]
         L.spod_reconstruct.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), P, P, P]
         L.spod_last_error.restype = C.c_char_p
         L.spod_version.restype = C.c_char_p
@@ -183,6 +185,11 @@ def spod_run_host_many(plan: int, hXs, nmodes: int, hPhis, hlams=None, stream=No
     arr_l = (C.c_void_p * n)(*[_ptr(x) for x in hlams]) if hlams is not None else None
     check(lib().spod_run_host_many(plan, n, arr_x, int(nmodes), arr_p, arr_l, _stream(stream)),
           "spod_run_host_many")
+
+
+def spod_run_host_ooc(plan: int, hX, nmodes: int, hPhi, hlam, tile_points: int = 0, stream=None) -> None:
+    check(lib().spod_run_host_ooc(plan, _ptr(hX), int(nmodes), _ptr(hPhi), _ptr(hlam), int(tile_points),
+                                  _stream(stream)), "spod_run_host_ooc")
 
 
 def spod_coeffs(plan: int, X, Phi, nmodes: int, nmodes_r: int, freqs, A, stream=None) -> None:

@@ -33,7 +33,8 @@ template <> __device__ __forceinline__ double to_f64<double>(double v) { return 
 
 // ---------------------------------------------------------------- FFT
 struct FftArgs {
-  int64_t M, m0, mcount, chunk;   // chunk = row stride of Qhat (points per chunk)
+  int64_t M, m0, mcount, chunk;   // M = row stride of X in points; chunk = row stride of Qhat
+  int64_t xoff;                   // point of X's first column (tiled data)
   int64_t mpad;                   // points written: mcount rounded up to 64 (zeros past mcount)
   int nfft, step, nb, nf;
   int subtract_mean;

@@ -215,7 +215,7 @@ template <typename R, int KG>
 __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, int64_t rs, int nb, int nmodes,
                                                     int nmp, int64_t mcount, int64_t m0, int64_t M,
                                                     const R* __restrict__ bmat, const R* __restrict__ scale,
-                                                    R* __restrict__ phi, int f0) {
+                                                    R* __restrict__ phi, int f0, int64_t phioff) {
   using V2 = typename Cplx<R>::T;
   const int f = f0 + blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, 
     for (int j = 0; j < KG; ++j) {
       const int k = k0 + j;
       if (k >= nmodes) break;
-      R* o = phi + (((int64_t)f * nmodes + k) * M + m) * 2;
+      R* o = phi + (((int64_t)f * nmodes + k) * M + (m - phioff)) * 2;
       if (two && vec && sizeof(R) == 4) {
         *reinterpret_cast<float4*>(o) = make_float4((float)(ar0[j] * s0), (float)(ai0[j] * s0),
                                                     (float)(ar1[j] * s1), (float)(ai1[j] * s1));
@@ -324,10 +324,11 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
   if (e != cudaSuccess) return e;
   constexpr int threads = 128;
   dim3 grid((unsigned)((mcount + 2 * threads - 1) / (2 * threads)), (unsigned)(f1 - f0));
+  const int64_t ld = (p.phi_ld && !adjoint) ? p.phi_ld : p.M;
   kern<<<grid, threads, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, nmodes, nmp, mcount, m0,
-                                   p.M, static_cast<const R*>(p.d_bmat),
+                                   ld, static_cast<const R*>(p.d_bmat),
                                    static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW), static_cast<R*>(d_Phi),
-                                   f0);
+                                   f0, adjoint ? 0 : p.phi_off);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nlaunch;

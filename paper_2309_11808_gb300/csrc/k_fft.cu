@@ -23,28 +23,31 @@ namespace {
 using namespace fft;
 
 // ---------------------------------------------------------------- mean
+// part[y][m] (row stride M) sums rows [y tper, (y+1) tper) of column m of X,
+// whose rows are xld columns long and start at column xoff.
 template <typename Tin>
-__global__ void __launch_bounds__(256) k_mean_partial(const Tin* __restrict__ X, int64_t M, int64_t nt,
-                                                      int64_t tper, int64_t m0, int64_t m1,
+__global__ void __launch_bounds__(256) k_mean_partial(const Tin* __restrict__ X, int64_t M, int64_t xld, int64_t xoff,
+                                                      int64_t nt, int64_t tper, int64_t m0, int64_t m1,
                                                       double* __restrict__ part) {
   const int64_t m = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= m1) return;
   const int64_t t0 = (int64_t)blockIdx.y * tper;
   const int64_t t1 = min(nt, t0 + tper);
   double acc = 0.0;
-  const Tin* p = X + t0 * M + m;
+  const int64_t Mx = xld;                      // row stride of X
+  const Tin* p = X + t0 * Mx + (m - xoff);
   int64_t t = t0;
   if constexpr (sizeof(Tin) == 8) {
-    for (; t < t1; ++t, p += M) acc += (double)(*p);
+    for (; t < t1; ++t, p += Mx) acc += (double)(*p);
   } else {
     for (; t + 16 <= t1; t += 16) {
       float r = 0.f;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) r += to_f32<Tin>(p[i * M]);
+      for (int i = 0; i < 16; ++i) r += to_f32<Tin>(p[i * Mx]);
       acc += (double)r;
-      p += 16 * M;
+      p += 16 * Mx;
     }
-    for (; t < t1; ++t, p += M) acc += (double)to_f32<Tin>(*p);
+    for (; t < t1; ++t, p += Mx) acc += (double)to_f32<Tin>(*p);
   }
   part[(int64_t)blockIdx.y * M + m] = acc;
 }
@@ -93,7 +96,8 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
     const int j = threadIdx.x % C;
     const int n0 = threadIdx.x / C;
     const int64_t m = gm0 + (CPLX ? j : 2 * j);
-    const int64_t xi = CPLX ? 2 * m : m;
+    const int64_t xi = CPLX ? 2 * m : m;          // mean (global)
+    const int64_t xc = CPLX ? 2 * (m - a.xoff) : m - a.xoff;   // column of X
     const int64_t mend = a.m0 + a.mcount;
     const bool ok0 = m < mend, ok1 = CPLX ? ok0 : m + 1 < mend;
     R mhi0 = 0, mlo0 = 0, mhi1 = 0, mlo1 = 0;
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
       if (ok1) { const double d = mu[xi + 1]; mhi1 = (R)d; mlo1 = (R)(d - (double)mhi1); }
     }
     const int64_t rowlen = CPLX ? 2 * a.M : a.M;   // components per snapshot
-    const Tin* base = X + (int64_t)l * a.step * rowlen + xi;
+    const Tin* base = X + (int64_t)l * a.step * rowlen + xc;
     constexpr int NSTEP = 256 / C;
 #pragma unroll 4
     for (int n = n0; n < N; n += NSTEP) {
@@ -193,7 +197,7 @@ cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int6
   constexpr int TP = sizeof(R) == 8 ? 8 : 16;
   constexpr int PPT = CPLX ? TP / 2 : TP;
   FftArgs a;
-  a.M = p.M; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
+  a.M = p.x_ld ? p.x_ld : p.M; a.xoff = p.x_off; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
   a.mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
   a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;
   a.subtract_mean = p.desc.subtract_mean;
@@ -217,9 +221,11 @@ template <typename Tin>
 cudaError_t launch_mean_t(const spod_plan_s& p, const void* d_X, int64_t Mcols, int64_t m0, int64_t mcount,
                           cudaStream_t s) {
   const int64_t tper = (p.nt + p.mean_splits - 1) / p.mean_splits;
+  const int64_t k = Mcols / p.M;              // 2 for complex data (components)
+  const int64_t xld = k * (p.x_ld ? p.x_ld : p.M), xoff = k * p.x_off;
   dim3 grid((unsigned)((mcount + 255) / 256), (unsigned)p.mean_splits);
-  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), Mcols, p.nt, tper, m0, m0 + mcount,
-                                           p.d_mupart);
+  k_mean_partial<Tin><<<grid, 256, 0, s>>>(static_cast<const Tin*>(d_X), Mcols, xld, xoff, p.nt, tper, m0,
+                                           m0 + mcount, p.d_mupart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_mean_finish<<<(unsigned)((mcount + 255) / 256), 256, 0, s>>>(p.d_mupart, p.mean_splits, Mcols, m0,

@@ -53,6 +53,7 @@ struct Geo {
 
 struct PipeArgs {
   int64_t m0, mcount, chunk, ntiles;
+  int64_t xoff;                      // column of X's first TMA column (tiled data)
   int step, nb, nf, boxr;
   int subtract_mean;
 };
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
   // TMA boxes for time rows [r0, r0 + nrows) of tile t; row r lands in ring slot r mod N
   auto issue = [&](int64_t t, int r0, int nrows) {
     mbar_arrive_expect_tx(bar, (uint32_t)nrows * row_bytes);
-    const int x = (int)(a.m0 + t * PTP);
+    const int x = (int)(a.m0 - a.xoff + t * PTP);
     for (int r = r0; r < r0 + nrows; r += a.boxr) tma_load_2d(smem_u32(ring + (size_t)(r % N) * PTP), &xmap, x, r, bar);
   };
   if (tid == 0) {
@@ -446,6 +447,7 @@ cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
   constexpr int64_t K = CPLX ? 2 : 1;          // components per point
   PipeArgs a;
   a.m0 = K * m0; a.mcount = K * mcount; a.chunk = p.chunk_points;
+  a.xoff = K * p.x_off;
   const int64_t mpad = K * std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
   a.ntiles = mpad / TP;
   a.step = p.step; a.nb = p.nb; a.nf = p.nf;

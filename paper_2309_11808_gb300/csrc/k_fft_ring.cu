@@ -32,6 +32,7 @@ constexpr int RTHREADS = 512;
 
 struct RingArgs {
   int64_t M, m0, mcount, chunk, mpad, ntiles;
+  int64_t xoff;                     // column of X's first TMA column (tiled data)
   int nfft, step, nb, nf, boxr, ring;
   int stg_off;                      // byte offset of the output staging (from the ring start)
   int fbox, nfbox;                  // frequency rows per TMA store box, boxes per plane
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(RTHREADS, 1) k_fft_ring(const __grid_constant_
   // issue the TMA boxes for time rows [r0, r0 + nrows) of tile t into the ring
   auto issue = [&](int64_t t, int r0, int nrows) {
     mbar_arrive_expect_tx(bar, (uint32_t)nrows * row_bytes);
-    const int x = (int)(a.m0 + t * RTP);
+    const int x = (int)(a.m0 - a.xoff + t * RTP);
     for (int r = r0; r < r0 + nrows; r += a.boxr) {
       const int slot = r % a.ring;
       tma_load_2d(smem_u32(ring + (size_t)slot * RTP), &xmap, x, r, bar);
@@ -279,6 +280,7 @@ cudaError_t launch_ring_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
                           cudaStream_t s) {
   RingArgs a;
   a.M = p.M; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
+  a.xoff = p.x_off;
   a.mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
   a.ntiles = a.mpad / RTP;
   a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;

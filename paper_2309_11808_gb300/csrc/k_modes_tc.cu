@@ -38,7 +38,8 @@ constexpr int kThreadsModes = (kEpiWarps + 2) * 32;
 
 struct ModesTcArgs {
   int nb, nmodes, np, nn, nf;             // np = K (2 nb padded to 16), nn = N (2 nmodes padded to 16)
-  int64_t mcount, m0, M;
+  int64_t mcount, m0, M;                  // M: row stride of Phi in points
+  int64_t phioff;                          // point of Phi's first column (tiled output)
   int64_t ntp;                             // 128-point tiles per frequency
   int64_t nitems;                          // (f1 - f0) * ntp
   int f0;                                  // first frequency of the call's range
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
       if (lm < a.mcount) {
         const int64_t m = a.m0 + lm;
         const float rw = scale[m];
-        float2* out = phi + ((int64_t)f * nm + k0) * a.M + m;
+        float2* out = phi + ((int64_t)f * nm + k0) * a.M + (m - a.phioff);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           if (2 * j < hcols && k0 + j < nm) out[(int64_t)j * a.M] = make_float2(v[2 * j] * rw, v[2 * j + 1] * rw);
@@ -335,7 +336,8 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
   a.nf = p.nf;
   a.mcount = mcount;
   a.m0 = m0;
-  a.M = p.M;
+  a.M = (p.phi_ld && !adjoint) ? p.phi_ld : p.M;
+  a.phioff = adjoint ? 0 : p.phi_off;
   a.ntp = (mcount + 127) / 128;
   a.nitems = a.ntp * (f1 - f0);
   a.f0 = f0;

@@ -145,7 +145,8 @@ spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) 
   if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available");
   // complex data: a [nt][2M] array of interleaved real components
   const spod_dtype t = p->desc.in_dtype;
-  const int64_t cols = p->cplx ? 2 * p->M : p->M;
+  const int64_t xld = p->x_ld ? p->x_ld : p->M;     // tiled data: the tile's width
+  const int64_t cols = p->cplx ? 2 * xld : xld;
   const size_t el = p->cplx ? elem_bytes(t) / 2 : elem_bytes(t);
   const CUtensorMapDataType dt = t == SPOD_F64 || t == SPOD_C128 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                  : t == SPOD_F32 || t == SPOD_C64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -915,6 +916,170 @@ spod_status spod_run_host_many(spod_plan_t p, int n, const void* const* h_X, int
   }
   DeviceGuard g(p->device);
   return run_host_impl(p, n, h_X, nmodes, h_Phi, h_lambda, static_cast<cudaStream_t>(stream));
+}
+
+// Out-of-core pipeline: X and Phi stay in pinned host memory; column tiles of
+// w points are gathered over the host link by a copy kernel (on the plan's
+// upload stream) into two device tile buffers used in turn, and the fit runs
+// tile by tile (mean, FFT, Gram of tile c while tile c + 1 arrives); after
+// the eigen-solve the tiles are gathered again, their Qhat recomputed and
+// their modes written into two device Phi tiles, each scattered back to the
+// host while the next one is computed.  Device memory: the plan's workspace
+// and the four tile buffers.
+spod_status spod_run_host_ooc(spod_plan_t p, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
+                              int64_t tile_points, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!h_X) return fail(SPOD_EINVAL, "h_X is NULL");
+  if (nmodes < 0 || nmodes > p->nb) return fail(SPOD_EINVAL, "need 0 <= nmodes <= nb");
+  if (nmodes > 0 && !h_Phi) return fail(SPOD_EINVAL, "h_Phi is NULL");
+  if (tile_points < 0) return fail(SPOD_EINVAL, "tile_points must be >= 0");
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the kernels read and write the host arrays directly: pinned memory through
+  // its device alias, pageable memory only where the device reads it through
+  // the host's page tables
+  int pageable = 0;
+  if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    pageable = 0;
+  }
+  auto device_alias = [&](void* h, void** d) {
+    if (cudaHostGetDevicePointer(d, h, 0) == cudaSuccess) return true;
+    cudaGetLastError();
+    *d = h;
+    return pageable != 0;
+  };
+  void *dXh = nullptr, *dPh = nullptr;
+  if (!device_alias(const_cast<void*>(h_X), &dXh))
+    return fail(SPOD_EINVAL, "h_X must be pinned host memory (cudaHostAlloc / cudaHostRegister)");
+  if (nmodes > 0 && !device_alias(h_Phi, &dPh))
+    return fail(SPOD_EINVAL, "h_Phi must be pinned host memory (cudaHostAlloc / cudaHostRegister)");
+  const int64_t M = p->M, nt = p->nt;
+  int64_t w = tile_points ? tile_points : ((M + 3) / 4 + 63) / 64 * 64;
+  // whole multiples of 64 points (16-byte aligned tile rows), within the plan's Qhat chunk
+  w = std::min<int64_t>(std::max<int64_t>(64, (w + 63) / 64 * 64), p->chunk_points);
+  const int64_t ntile = (M + w - 1) / w;
+  const size_t el = elem_bytes(p->desc.in_dtype);
+  const size_t eb = p->f64 ? 16 : 8;
+  const size_t xtb = (size_t)nt * w * el, ptb = (size_t)p->nf * nmodes * w * eb;
+  if (!p->h2d_stream) SPOD_CUDA(cudaStreamCreateWithFlags(&p->h2d_stream, cudaStreamNonBlocking), "copy stream");
+  if (!p->d2h_stream) SPOD_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking), "copy stream");
+  while (p->host_ev.size() < 16) {
+    cudaEvent_t e;
+    SPOD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    p->host_ev.push_back(e);
+  }
+  cudaEvent_t* ready = &p->host_ev[0];      // [2] X tile arrived
+  cudaEvent_t* xfree = &p->host_ev[2];      // [2] X tile consumed
+  cudaEvent_t* pready = &p->host_ev[4];     // [2] Phi tile written
+  cudaEvent_t* pfree = &p->host_ev[6];      // [2] Phi tile sent
+  cudaEvent_t start = p->host_ev[8];
+  cudaStream_t up = p->h2d_stream, down = p->d2h_stream;
+  void *xt[2] = {nullptr, nullptr}, *pt[2] = {nullptr, nullptr};
+  auto release = [&]() {
+    for (int b = 0; b < 2; ++b) {
+      if (xt[b]) cudaFreeAsync(xt[b], s);
+      if (pt[b]) cudaFreeAsync(pt[b], s);
+    }
+    p->x_ld = p->x_off = p->phi_ld = p->phi_off = 0;
+  };
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMallocAsync(&xt[b], xtb, s) != cudaSuccess || (nmodes > 0 && cudaMallocAsync(&pt[b], ptb, s) != cudaSuccess)) {
+      cudaGetLastError();
+      release();
+      return fail(SPOD_ENOMEM, "out-of-core tile buffers");
+    }
+  }
+  spod_status st = SPOD_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == SPOD_OK) st = cuda_fail(e, what);
+    return st == SPOD_OK;
+  };
+  ck(cudaEventRecord(start, s), "event");
+  ck(cudaStreamWaitEvent(up, start, 0), "wait");
+  ck(cudaStreamWaitEvent(down, start, 0), "wait");
+  auto gather = [&](int64_t c, int b, int use) {
+    const int64_t c0 = c * w, wc = std::min<int64_t>(w, M - c0);
+    if (use >= 2) ck(cudaStreamWaitEvent(up, xfree[b], 0), "wait");
+    // the columns past the last point read as zeros, as TMA's out-of-range fill does for untiled data
+    ck(launch_copy2d(xt[b], w * el, static_cast<const char*>(dXh) + c0 * el, M * el, wc * el, w * el, nt,
+                     p->num_sms, up),
+       "gather X tile");
+    ck(cudaEventRecord(ready[b], up), "event");
+    ck(cudaStreamWaitEvent(s, ready[b], 0), "wait");
+  };
+  // ---- fit
+  p->fitted = false;
+  p->qhat_valid = false;
+  p->x_ld = w;
+  ck(cudaMemsetAsync(p->d_flags, 0, 4 * sizeof(unsigned), s), "clear flags");
+  if (!p->desc.subtract_mean) ck(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * M * (p->cplx ? 2 : 1), s), "zero mean");
+  int use = 0;
+  for (int64_t c = 0; c < ntile && st == SPOD_OK; ++c, ++use) {
+    const int b = use & 1;
+    const int64_t c0 = c * w, wc = std::min<int64_t>(w, M - c0);
+    gather(c, b, use);
+    p->x_off = c0;
+    if (p->desc.subtract_mean) ck(launch_mean(*p, xt[b], c0, wc, s), "mean kernel");
+    alignas(64) CUtensorMap xmap;
+    const CUtensorMap* xm = nullptr;
+    if (p->ring_ok && st == SPOD_OK) {
+      if ((st = make_x_map(p, xt[b], &xmap)) != SPOD_OK) break;
+      xm = &xmap;
+    }
+    if (st == SPOD_OK) st = run_fft_chunk(p, xt[b], xm, c0, wc, s);
+    if (p->tensor) ck(launch_gram_tc_chunk(*p, wc, c == 0, s), "tensor-core gram kernel");
+    else ck(launch_gram_chunk(*p, wc, c == 0, s), "gram kernel");
+    ck(cudaEventRecord(xfree[b], s), "event");
+  }
+  if (p->tensor) ck(launch_gram_tc_finish(*p, s), "gram finish kernel");
+  else ck(launch_gram_reduce(*p, s), "gram reduce kernel");
+  ck(launch_eig_tridiag(*p, s), "eigen-solver kernel");
+  if (st == SPOD_OK) p->fitted = true;
+  if (h_lambda)
+    ck(cudaMemcpyAsync(h_lambda, p->d_lam, sizeof(double) * (size_t)p->nf * p->nb, cudaMemcpyDeviceToHost, s),
+       "copy lambda to host");
+  // ---- modes
+  if (nmodes > 0 && st == SPOD_OK) {
+    ck(launch_mode_coeffs(*p, nmodes, s), "mode coefficient kernel");
+    if (p->tensor) ck(launch_mode_image(*p, nmodes, s), "mode operand image kernel");
+    p->phi_ld = w;
+    for (int64_t c = 0; c < ntile && st == SPOD_OK; ++c, ++use) {
+      const int b = use & 1, pb = (int)(c & 1);
+      const int64_t c0 = c * w, wc = std::min<int64_t>(w, M - c0);
+      gather(c, b, use);
+      p->x_off = c0;
+      alignas(64) CUtensorMap xmap;
+      const CUtensorMap* xm = nullptr;
+      if (p->ring_ok) {
+        if ((st = make_x_map(p, xt[b], &xmap)) != SPOD_OK) break;
+        xm = &xmap;
+      }
+      if ((st = run_fft_chunk(p, xt[b], xm, c0, wc, s)) != SPOD_OK) break;
+      ck(cudaEventRecord(xfree[b], s), "event");
+      if (c >= 2) ck(cudaStreamWaitEvent(s, pfree[pb], 0), "wait");
+      p->phi_off = c0;
+      int nl = 0;
+      if (p->tensor) ck(launch_modes_tc_chunk(*p, c0, wc, nmodes, pt[pb], s), "tensor-core modes kernel");
+      else ck(launch_modes_chunk(*p, c0, wc, nmodes, pt[pb], s, &nl), "modes kernel");
+      ck(cudaEventRecord(pready[pb], s), "event");
+      ck(cudaStreamWaitEvent(down, pready[pb], 0), "wait");
+      ck(launch_copy2d(static_cast<char*>(dPh) + c0 * eb, M * eb, pt[pb], w * eb, wc * eb, wc * eb,
+                       (int64_t)p->nf * nmodes, p->num_sms, down),
+         "scatter Phi tile");
+      ck(cudaEventRecord(pfree[pb], down), "event");
+    }
+  }
+  ck(cudaEventRecord(start, up), "event");
+  ck(cudaStreamWaitEvent(s, start, 0), "join");
+  ck(cudaEventRecord(start, down), "event");
+  ck(cudaStreamWaitEvent(s, start, 0), "join");
+  release();
+  p->qhat_valid = false;
+  p->last_stream = s;
+  if (st != SPOD_OK) return st;
+  SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+  return read_flags(p);
 }
 
 // Validation shared by the expansion-coefficient entries.

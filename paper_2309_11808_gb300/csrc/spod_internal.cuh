@@ -77,6 +77,10 @@ struct spod_plan_s {
   bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
   bool cplx = false;          // complex input: two-sided spectrum, complex mean
   void* blas = nullptr;       // cuBLAS handle of the expansion-coefficient GEMMs (created on first use)
+  // Views for data held in tiles (out-of-core driver): X is read as rows of
+  // x_ld points starting at point x_off, Phi written as rows of phi_ld points
+  // starting at point phi_off (0, 0: the full arrays, row stride M).
+  int64_t x_ld = 0, x_off = 0, phi_ld = 0, phi_off = 0;
   bool pipe_ok = false;       // the pipelined kernel (compiled nfft) is used
   int pipe_tp = 16;           // its tile width in points (16 or 32; also the X map's box width)
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
@@ -204,6 +208,11 @@ cudaError_t launch_coeffs(spod_plan_s& p, const void* d_X, const void* d_Phi, in
 cudaError_t launch_reconstruct(spod_plan_s& p, const void* d_Phi, int nmodes, int nmodes_r, int nsel,
                                const int* h_freqs, const double* d_A, void* d_Xrec, cudaStream_t s);
 void destroy_blas(spod_plan_s& p);
+// strided tile copy (k_tile_copy.cu)
+// rows x width bytes from src (pitch spitch) to dst (pitch dpitch); bytes
+// [width, dwidth) of each destination row are set to zero
+cudaError_t launch_copy2d(void* dst, int64_t dpitch, const void* src, int64_t spitch, int64_t width, int64_t dwidth,
+                          int64_t rows, int num_sms, cudaStream_t s);
 
 void set_error(const std::string& msg);
 
