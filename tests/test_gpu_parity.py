@@ -173,6 +173,62 @@ def test_chunked_pipeline_matches_single_pass():
 
 
 @cuda
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_constant_data_gives_a_zero_spectrum(prec):
+    g = torch.Generator().manual_seed(51)
+    nt, M, nfft = 600, 96, 64
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    sp = SPOD(M, 1, nt, nfft, nfft // 2, dtype=dt, precision=prec)
+    # integer constants: every partial sum of the mean is exact, so a column
+    # minus its mean is zero; Qhat, the Gram and every eigenvalue vanish, the
+    # eigen-solver meets an all-zero matrix, and every mode is returned as zero
+    X = torch.randint(-3, 4, (M,), generator=g).to(dt).expand(nt, M).contiguous()
+    Xd = X.to(DEV)
+    sp.fit(Xd)
+    lam = sp.eigs()
+    Phi = sp.modes(Xd, 3)
+    torch.cuda.synchronize()
+    assert np.all(lam == 0.0)
+    assert int(torch.count_nonzero(Phi)) == 0
+    # general constants: the mean is exact only to the rounding of its sums
+    # (FP32 runs of 16 samples for FP32 input, relative error below 16 u32;
+    # FP64 sums for FP64 input, below nt u64), and a constant residual d_m
+    # gives |qhat_m| <= |d_m| (the window carries c = 1 / sum w), hence
+    # 0 <= lambda <= trace M_f <= sum_m d_m^2
+    c = torch.randn(M, generator=g, dtype=torch.float64) * 5.0
+    X = c.to(dt).expand(nt, M).contiguous()
+    Xd = X.to(DEV)
+    sp.fit(Xd)
+    lam = sp.eigs()
+    Phi = sp.modes(Xd, 3)
+    torch.cuda.synchronize()
+    u = 2.0 ** -24 * 16 if dt == torch.float32 else 2.0 ** -53 * nt
+    bound = float(((u * X[0].double()) ** 2).sum())
+    assert np.all(lam >= -1e-3 * bound) and np.all(lam <= bound), (lam.max(), bound)
+    assert bool(torch.isfinite(torch.view_as_real(Phi)).all())
+    sp.close()
+
+
+@cuda
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rank_deficient_data(prec):
+    # M = 2 points and nb = 30 blocks: at most two nonzero eigenvalues per bin;
+    # the others vanish to the precision of the Gram's arithmetic
+    g = torch.Generator().manual_seed(52)
+    nt, M, nfft = 1000, 2, 64
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    X = torch.randn(nt, M, generator=g, dtype=torch.float64).to(dt)
+    r = run_both(X, M, 1, nfft, nfft // 2, prec, nmodes=2)
+    lam, ref = r["lam"], r["ref"].lam
+    assert lam.shape[1] == 30
+    assert lam_rel_err(lam[:, :2], ref[:, :2]) <= (1e-10 if prec == "fp64" else 1e-4)
+    tail = (1e-12 if prec == "fp64" else 1e-5) * lam[:, :1]
+    assert np.all(np.abs(lam[:, 2:]) <= tail)
+    assert np.all(np.abs(ref[:, 2:]) <= 1e-12 * ref[:, :1])
+    assert mode_err(r["Phi"], r["ref"], r["desc"], np.ones(M), 2) <= (1e-8 if prec == "fp64" else 1e-4)
+
+
+@cuda
 def test_bitwise_reproducible():
     wl = jet_like(nx=16, nr=16, nvars=2, nt=700, nfft=64, seed=1)
     sp = SPOD(wl.npoints, 2, 700, 64, 32, weights=wl.W)
