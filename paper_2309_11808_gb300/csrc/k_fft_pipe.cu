@@ -374,9 +374,18 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
     const int x = (int)(a.m0 - a.xoff + t * PTP);
     for (int r = r0; r < r0 + nrows; r += a.boxr) tma_load_2d(smem_u32(ring + (size_t)(r % N) * PTP), &xmap, x, r, bar);
   };
+  // L2 prefetch of time rows [r0, r0 + nrows) of tile t: the rows of block
+  // l + 2 are requested from HBM while block l + 1's rows travel to the ring,
+  // so the ring's load (one block ahead, all the shared memory allows) finds
+  // them in L2
+  auto prefetch = [&](int64_t t, int r0, int nrows) {
+    const int x = (int)(a.m0 - a.xoff + t * PTP);
+    for (int r = r0; r < r0 + nrows; r += a.boxr) tma_prefetch_2d(&xmap, x, r);
+  };
   if (tid == 0) {
     prefetch_tmap(&xmap);
     issue(t_first, 0, N);
+    if (a.nb > 1) prefetch(t_first, N, a.step);
   }
 
   const int col = tid % PC;
@@ -421,8 +430,10 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
       if (tid == 0) {
         if (l + 1 < a.nb) {
           issue(t, l * a.step + N, a.step);
+          if (l + 2 < a.nb) prefetch(t, (l + 1) * a.step + N, a.step);   // rows of block l + 2 (< nt)
         } else if (t + t_step < a.ntiles) {
           issue(t + t_step, 0, N);
+          if (a.nb > 1) prefetch(t + t_step, N, a.step);
         }
       }
       const float2* spec = S::template rest<TP>(bA, bB, tw);
