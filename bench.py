@@ -424,11 +424,11 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, e
 # points processed (x 32) to the full grid; the summaries are in profiles/.
 # Absent entries: no capture of the current kernel version.
 TRAFFIC = {
-    ("fft", "bf16x3"): int((490.987776 + 909.537536) * 1e6 * 32),    # k_fft_pipe<float, 1, 512>
-    ("gram", "bf16x3"): int((960.324864 + 19.772928) * 1e6 * 32),    # k_gram_tc<1, 40>
-    ("modes", "bf16x3"): int((976.955392 + 907.371776) * 1e6 * 32),  # k_modes_tc<1>
+    ("fft", "bf16x3"): int((491.146752 + 910.630400) * 1e6 * 32),    # k_fft_pipe<float, 1, 32, 512> (L2 prefetch)
+    ("gram", "bf16x3"): int((960.310528 + 19.053056) * 1e6 * 32),    # k_gram_tc<1, 40>
+    ("modes", "bf16x3"): int((976.941568 + 907.403264) * 1e6 * 32),  # k_modes_tc<1> (Phi view)
     ("gram", "fp32"): int((961.233 + 25.105920) * 1e6 * 32),         # k_gram_simt<float>
-    ("modes", "fp32"): int((1016.175 + 920.394496) * 1e6 * 32),      # k_modes_simt<float, 16>
+    # k_modes_simt changed (frequency range, Phi view) after its capture: no entry
 }
 
 
