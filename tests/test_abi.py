@@ -89,3 +89,24 @@ def test_argument_validation_on_host(L):
     # NULL plan handles
     assert L.spod_fit(None, None, None) == _lib.SPOD_EINVAL
     assert L.spod_plan_destroy(None) == _lib.SPOD_OK
+    E = _lib.SPOD_EINVAL
+    info = _lib.spod_plan_info()
+    tun = _lib.spod_tuning()
+    assert L.spod_plan_get_info(None, ctypes.byref(info)) == E
+    assert L.spod_get_eigs(None, None, None, 0) == E
+    assert L.spod_get_gram(None, None) == E
+    assert L.spod_get_freqs(None, None) == E
+    assert L.spod_modes(None, None, 1, None, None) == E
+    assert L.spod_backward(None, None, None, None, None) == E
+    assert L.spod_sync(None, None) == E
+    assert L.spod_run_host(None, None, 0, None, None, None) == E
+    assert L.spod_run_host_many(None, 1, None, 0, None, None, None) == E
+    assert L.spod_run_host_ooc(None, None, 0, None, None, 0, None) == E
+    assert L.spod_coeffs(None, None, None, 1, 1, 0, None, None, None) == E
+    assert L.spod_reconstruct(None, None, 1, 1, 0, None, None, None, None) == E
+    assert L.spod_plan_get_tuning(None, ctypes.byref(tun)) == E
+    assert L.spod_plan_set_tuning(None, ctypes.byref(tun)) == E
+    assert L.spod_plan_autotune(None, None, None, ctypes.byref(tun)) == E
+    assert L.spod_profile_enable(None, 1) == E
+    assert L.spod_profile_read(None, None, None) == E
+    assert L.spod_fit_batch(None, None, 1, None) == E
