@@ -8,6 +8,7 @@ Metric: snapshot-GB/s = nt * M * sizeof(element) / (time per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3]
                     [--impl native|reference] [--no-compare] [--no-e2e] [--no-cpu]
+    python bench.py --complex | --coeffs | --ooc     (separate measurements)
 
 The default precision is bf16x3 (BF16 tensor-core Gram and modes with split
 products); the same input is then also run through the plain FP32 GPU form
