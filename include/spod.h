@@ -13,13 +13,16 @@
  *   property stated right after that equation).
  *
  * Conventions fixed by this library where the paper is silent:
- *   - X is real, laid out time-major: X[t][v][p], t < nt, v < nvars,
- *     p < npoints, row-major; the flattened row index is m = v*npoints + p and
+ *   - X is laid out time-major: X[t][v][p], t < nt, v < nvars, p < npoints,
+ *     row-major; the flattened row index is m = v*npoints + p and
  *     M = nvars*npoints (Eq. data-matrix stores the transpose, Q in R^{M x Nt}).
+ *     X is real (SPOD_F64 / F32 / BF16) or complex (SPOD_C64 / C128,
+ *     interleaved real and imaginary parts).
  *   - step = nfft - noverlap; block l covers t in [l*step, l*step + nfft);
  *     nb = floor((nt - noverlap) / step) (the paper's L); tail samples belong
  *     to no block but do enter the mean.
- *   - nf = floor(nfft/2) + 1 one-sided frequencies (real data, Eq. discrete_modes).
+ *   - nf = floor(nfft/2) + 1 one-sided frequencies for real data (Eq.
+ *     discrete_modes); nf = nfft (two-sided) for complex data.
  *   - qhat[f][l][m] = c * sum_n w_n (X[l*step+n][m] - mu_m) exp(-2 pi i f n / nfft),
  *     c = 1 / sum_n w_n, mu_m the mean over all nt snapshots.
  *   - kappa = 1/nb (SPOD_NORM_NB) or 1/(nb-1) (SPOD_NORM_NB_MINUS_1, the
@@ -231,9 +234,14 @@ spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, vo
  * SPOD_EINVAL -- and are read and written in column tiles of tile_points points
  * (0: about M/4, rounded to 64, at most the plan's chunk) by copy kernels
  * over the host link, overlapped with the fit (mean, FFT, Gram per tile) and
- * with the modes (each tile's Qhat recomputed).  Device memory: the plan's
- * workspace plus two X tiles and two Phi tiles.  Results equal spod_fit +
- * spod_modes to rounding (the Gram is summed tile by tile).  Synchronises. */
+ * with the modes (each tile's Qhat recomputed).  h_X is [nt][M] in the plan's
+ * input type, h_Phi [nf][nmodes][M] as spod_modes writes it (may be NULL when
+ * nmodes = 0), h_lambda [nf][nb] (may be NULL).  Device memory: the plan's
+ * workspace plus two X tiles and two Phi tiles; give the plan chunk_points =
+ * the tile width so that its Qhat is one tile.  Results equal spod_fit +
+ * spod_modes bit for bit when the plan's chunk_points equals the tile width
+ * (the same spatial chunks), else to rounding (the Gram is summed over other
+ * chunks).  Synchronises. */
 spod_status spod_run_host_ooc(spod_plan_t plan, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
                               int64_t tile_points, void* stream);
 
