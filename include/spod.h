@@ -138,18 +138,25 @@ typedef struct {
 } spod_plan_info;
 
 /* Fill *desc with defaults (Hamming, 50 % overlap unset = 0, FP32, NORM_NB,
- * subtract_mean = 1, dt = 1).  Never fails for a non-NULL pointer. */
+ * subtract_mean = 1, dt = 1): the readings this library takes where Sec. 2.2
+ * is silent (window, normalisation).  Never fails for a non-NULL pointer;
+ * SPOD_EINVAL for NULL. */
 spod_status spod_desc_init(spod_plan_desc* desc);
 
 /* Validate desc, copy window and weights, and allocate the plan's device
- * workspace on the current CUDA device.  Errors: SPOD_EINVAL (bad sizes,
+ * workspace on the current CUDA device.  Derived sizes follow Eq. blocks
+ * (nb = floor((nt - noverlap) / step), step = nfft - noverlap) and the
+ * one-sided count after Eq. discrete_modes (nf).  Errors: SPOD_EINVAL (bad sizes,
  * non-positive or non-finite weights, unsupported nfft factorisation ->
  * SPOD_EUNSUPPORTED), SPOD_ENOMEM, SPOD_ECUDA.  *out is NULL on failure. */
 spod_status spod_plan_create(const spod_plan_desc* desc, spod_plan_t* out);
 
-/* Free the plan and its workspace (device-synchronising).  NULL is a no-op. */
+/* Free the plan and its workspace (device-synchronising).  NULL is a no-op.
+ * No counterpart in the paper (resource management). */
 spod_status spod_plan_destroy(spod_plan_t plan);
 
+/* The plan's derived sizes (M, nb and step of Eq. blocks, nf, chunk) and
+ * workspace into *info (host).  SPOD_EINVAL for a NULL plan or info. */
 spod_status spod_plan_get_info(spod_plan_t plan, spod_plan_info* info);
 
 /* Mean, blocks, window, batched FFT, weighted Gram, deterministic reduction and
@@ -158,7 +165,8 @@ spod_status spod_plan_get_info(spod_plan_t plan, spod_plan_info* info);
  * 16-byte aligned.  Results stay in the plan (see spod_get_eigs).  Stream-ordered. */
 spod_status spod_fit(spod_plan_t plan, const void* d_X, void* stream);
 
-/* Copy the eigenvalues lambda[nf][nb] (FP64, descending per frequency) and,
+/* Copy the eigenvalues lambda[nf][nb] of the M_f of Eq.
+ * spod-discrete-snapshots (FP64, descending per frequency) and,
  * when psi != NULL, the eigenvectors psi[nf][nb (entry)][nb (vector)] as
  * interleaved complex FP64 (column k of psi[f] is the k-th eigenvector).
  * on_device = 1: both pointers are device memory, the copy is enqueued on
@@ -167,12 +175,14 @@ spod_status spod_fit(spod_plan_t plan, const void* d_X, void* stream);
  * (SPOD_ENANINPUT, SPOD_ENOTCONVERGED).  SPOD_ESTATE before a fit. */
 spod_status spod_get_eigs(spod_plan_t plan, double* lambda, double* psi, int on_device);
 
-/* Copy the weighted Gram matrices M_f [nf][nb][nb] (interleaved complex
- * FP64, kappa applied) to host memory; synchronising.  SPOD_ESTATE before a fit. */
+/* Copy the weighted Gram matrices M_f [nf][nb][nb] of Eq.
+ * spod-discrete-snapshots (interleaved complex FP64, kappa applied) to host
+ * memory; synchronising.  SPOD_ESTATE before a fit. */
 spod_status spod_get_gram(spod_plan_t plan, double* gram);
 
-/* Frequencies f / (nfft * dt), f = 0 .. nf-1, into host memory (complex
- * input: bins f >= ceil(nfft/2) give (f - nfft) / (nfft * dt)). */
+/* Frequencies of the bins of Eq. blocks-ft, f / (nfft * dt), f = 0 .. nf-1,
+ * into host memory (complex input: bins f >= ceil(nfft/2) give
+ * (f - nfft) / (nfft * dt)).  SPOD_EINVAL for a NULL plan or freqs. */
 spod_status spod_get_freqs(spod_plan_t plan, double* freqs);
 
 /* SPOD modes of the last fit (Eq. spod-discrete-snapshots): recomputes Qhat
@@ -183,7 +193,9 @@ spod_status spod_get_freqs(spod_plan_t plan, double* freqs);
  * complex elements, 16-byte aligned.  SPOD_ESTATE before a fit. */
 spod_status spod_modes(spod_plan_t plan, const void* d_X, int nmodes, void* d_Phi, void* stream);
 
-/* Adjoint of the fit for losses on eigenvalues: given d_dLdlambda[nf][nb]
+/* Adjoint of the fit for losses on eigenvalues (not in the paper: the
+ * derivative of the eigenvalues of Eq. spod-discrete-snapshots with respect
+ * to the data, through Eqs. blocks to blocks-k): given d_dLdlambda[nf][nb]
  * (device FP64) writes dL/dX [nt][M] (device, FP32 for precision
  * FP32/BF16/BF16X3, FP64 for FP64).  Valid for simple eigenvalues: with
  * G_f = sum_k g_fk psi psi^H and R_f = 2 kappa W Qhat_f G_f,
@@ -204,7 +216,8 @@ spod_status spod_backward(spod_plan_t plan, const double* d_dLdlambda, const voi
 spod_status spod_run_host(spod_plan_t plan, const void* h_X, int nmodes, void* h_Phi, double* h_lambda,
                           void* stream);
 
-/* spod_run_host over n datasets of the plan's shape (h_X[i], h_Phi[i],
+/* spod_run_host (the fit and modes of Sec. 2.2; the pipelining has no
+ * counterpart in the paper) over n datasets of the plan's shape (h_X[i], h_Phi[i],
  * h_lambda[i]; h_lambda may be NULL, or hold NULL entries), processed in
  * order with two staging pairs used in turn: dataset i + 1's X is copied up
  * on one copy stream while dataset i's modes are copied down on another (the
@@ -213,7 +226,9 @@ spod_status spod_run_host(spod_plan_t plan, const void* h_X, int nmodes, void* h
 spod_status spod_run_host_many(spod_plan_t plan, int n, const void* const* h_X, int nmodes, void* const* h_Phi,
                                double* const* h_lambda, void* stream);
 
-/* Wait for the plan's work on `stream` and report device-side conditions. */
+/* Wait for the plan's work on `stream` and report device-side conditions
+ * (SPOD_ENANINPUT, SPOD_ENOTCONVERGED, SPOD_ETIMEOUT).  No counterpart in the
+ * paper (stream-ordered execution). */
 spod_status spod_sync(spod_plan_t plan, void* stream);
 
 /* Fit n plans on n inputs with one CUDA-graph launch (datasets of different
@@ -283,8 +298,10 @@ typedef struct {
   int modes_ctas;         /* tensor-core modes: CTAs per frequency (0 = automatic) */
 } spod_tuning;
 
+/* The plan's launch shape into *tuning (host).  No counterpart in the paper. */
 spod_status spod_plan_get_tuning(spod_plan_t plan, spod_tuning* tuning);
-/* SPOD_EINVAL for values outside the stated ranges; takes effect from the next fit/modes call. */
+/* Set the launch shape (no counterpart in the paper).  SPOD_EINVAL for values
+ * outside the stated ranges; takes effect from the next fit/modes call. */
 spod_status spod_plan_set_tuning(spod_plan_t plan, const spod_tuning* tuning);
 
 /* Autotuner: runs spod_fit on d_X (device, as spod_fit) under candidate
@@ -342,10 +359,11 @@ spod_status spod_profile_read(spod_plan_t plan, double* ms, int64_t* launches);
 spod_status spod_eigh_batched_noalloc(const double* d_gram, int nf, int nb, double* d_lambda, double* d_psi,
                                       void* stream);
 
-/* Thread-local message describing the last non-OK status. */
+/* Thread-local message describing the last non-OK status (no counterpart in
+ * the paper).  Never NULL. */
 const char* spod_last_error(void);
 
-/* Library version string. */
+/* Library version string (no counterpart in the paper).  Never NULL. */
 const char* spod_version(void);
 
 #ifdef __cplusplus

@@ -35,6 +35,22 @@ def test_header_declares_the_expected_entry_points():
     assert sorted(_lib.EXPORTED) == names
 
 
+def test_every_declaration_cites_its_passage():
+    # each entry point's comment names the passage that defines it (Sec. / Eq.)
+    # or says that the paper has no counterpart
+    src = open(HEADER).read()
+    decl = re.compile(r"^\s*(?:const\s+)?\w+\s*\*?\s*(spod_\w+)\s*\(", flags=re.M)
+    cite = re.compile(r"Sec\.|Eq\.|Algorithm|[Nn]o counterpart|not in the paper|paper has no counterpart")
+    shared = {"spod_profile_read": "spod_profile_enable"}     # one comment for the pair
+    found = {}
+    for m in decl.finditer(src):
+        c0, c1 = src.rfind("/*", 0, m.start()), src.rfind("*/", 0, m.start())
+        text = src[c0:c1] if c1 > c0 >= 0 and ";" not in src[c1 + 2:m.start()] else ""
+        found[m.group(1)] = bool(cite.search(text))
+    for name, ok in found.items():
+        assert ok or found.get(shared.get(name, ""), False), name
+
+
 def test_library_exports_every_declared_symbol(L):
     for name in declared_functions():
         assert hasattr(L, name), name
