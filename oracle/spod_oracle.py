@@ -81,8 +81,9 @@ def n_freqs(nfft: int, two_sided: bool = False) -> int:
 
 
 def freqs(nfft: int, dt: float, two_sided: bool = False) -> np.ndarray:
-    """Frequency of bin f: f / (nfft * dt); two-sided bins f >= nfft/2 rounded
-    up are the negative frequencies (f - nfft) / (nfft * dt)."""
+    """Frequency of bin f of the block DFT (Eq. blocks-ft): f / (nfft * dt);
+    two-sided bins f >= nfft/2 rounded up are the negative frequencies
+    (f - nfft) / (nfft * dt)."""
     f = np.arange(n_freqs(nfft, two_sided))
     if two_sided:
         f = np.where(f < (nfft + 1) // 2, f, f - nfft)
@@ -93,6 +94,9 @@ def freqs(nfft: int, dt: float, two_sided: bool = False) -> np.ndarray:
 # Window (not specified by the paper; reading: symmetric Hamming)
 # --------------------------------------------------------------------------
 def window(kind: str, nfft: int, user: np.ndarray | None = None) -> np.ndarray:
+    """Window w_n of the windowed block DFT (Eq. blocks-ft).  The paper leaves
+    the window open; the symmetric Hamming table is the default reading, the
+    others are options."""
     n = np.arange(nfft, dtype=np.float64)
     if kind == "user":
         w = np.asarray(user, dtype=np.float64)
@@ -114,7 +118,7 @@ def window(kind: str, nfft: int, user: np.ndarray | None = None) -> np.ndarray:
 # Steps of Sec. 2.2
 # --------------------------------------------------------------------------
 def _as_data(X: np.ndarray) -> np.ndarray:
-    """X in FP64, complex128 when it is complex."""
+    """X in FP64, complex128 when it is complex (Eq. data-matrix admits both)."""
     return np.asarray(X, dtype=np.complex128 if np.iscomplexobj(X) else np.float64)
 
 
@@ -128,7 +132,8 @@ def time_mean(X: np.ndarray) -> np.ndarray:
 
 
 def dft_matrix(nfft: int, two_sided: bool = False) -> np.ndarray:
-    """E[f, n] = exp(-2 pi i ((f*n) mod nfft) / nfft), f one-sided (or all bins).
+    """E[f, n] = exp(-2 pi i ((f*n) mod nfft) / nfft) of Eq. blocks-ft, f one-sided
+    (or all bins).
 
     The angle is reduced exactly in integers before the cos/sin calls.
     """
@@ -187,6 +192,8 @@ def gram(Qhat: np.ndarray, W: np.ndarray, norm: str = NORM_NB) -> np.ndarray:
 
 
 def gram_denominator(nb: int, norm: str) -> float:
+    """1 / kappa of the cross-spectral density: nb (the default reading) or
+    nb - 1 (the factor printed in Eq. csd-discrete)."""
     if norm == NORM_NB:
         return float(nb)
     if norm == NORM_NB_MINUS_1:
@@ -198,7 +205,8 @@ def gram_denominator(nb: int, norm: str) -> float:
 
 def jacobi_eigh(A: np.ndarray, tol: float = JACOBI_TOL,
                 max_sweeps: int = JACOBI_MAX_SWEEPS):
-    """Cyclic complex Jacobi for a batch of Hermitian matrices A[b][n][n].
+    """Cyclic complex Jacobi for a batch of Hermitian matrices A[b][n][n]: the
+    eigen-decomposition of M_f in Eq. spod-discrete-snapshots.
 
     Row-cyclic order (p < q).  Each rotation first turns a_pq real with a
     diagonal phase, then applies the real symmetric Jacobi rotation that
@@ -275,13 +283,15 @@ def jacobi_eigh(A: np.ndarray, tol: float = JACOBI_TOL,
 
 
 def _off_norm(A: np.ndarray, offmask: np.ndarray) -> np.ndarray:
-    """Frobenius norm of the off-diagonal part, summed entry by entry."""
+    """Frobenius norm of the off-diagonal part, summed entry by entry (the
+    stopping test of the eigen-decomposition, Eq. spod-discrete-snapshots)."""
     return np.sqrt((np.abs(A[:, offmask]) ** 2).sum(axis=1))
 
 
 def fix_phase(V: np.ndarray) -> np.ndarray:
-    """Unit 2-norm columns; the largest-|.| entry of each (lowest index on ties)
-    made real and positive."""
+    """Unit 2-norm columns (the eigenvectors of Eq. spod-discrete-snapshots);
+    the largest-|.| entry of each (lowest index on ties) made real and
+    positive, a phase the paper leaves free."""
     V = V / np.sqrt((np.abs(V) ** 2).sum(axis=-2, keepdims=True))
     idx = np.argmax(np.abs(V), axis=-2)                       # [b][k]
     piv = np.take_along_axis(V, idx[..., None, :], axis=-2)    # [b][1][k]
@@ -312,6 +322,8 @@ def modes(Qhat: np.ndarray, lam: np.ndarray, Psi: np.ndarray, nmodes: int,
 # --------------------------------------------------------------------------
 @dataclass
 class Desc:
+    """Sizes and options of one SPOD (Sec. 2.2): nt snapshots of M points,
+    Welch blocks of Eq. blocks, window, weights W, normalisation."""
     nt: int
     M: int
     nfft: int
@@ -342,6 +354,8 @@ class Desc:
 
 @dataclass
 class Fit:
+    """One fit: the mean, Qhat (Eq. blocks-k), M_f, eigenvalues and
+    eigenvectors (Eq. spod-discrete-snapshots), Jacobi sweeps and convergence."""
     mu: np.ndarray
     Qhat: np.ndarray
     M: np.ndarray
@@ -367,12 +381,14 @@ def spod_fit(X: np.ndarray, d: Desc, dft: str = "direct") -> Fit:
 
 
 def spod_modes(fit: Fit, d: Desc, nmodes: int) -> np.ndarray:
+    """The leading nmodes modes of a fit (Eq. spod-discrete-snapshots)."""
     return modes(fit.Qhat, fit.lam, fit.Psi, nmodes, d.norm)
 
 
 def spod_grad(X: np.ndarray, d: Desc, dLdlam: np.ndarray, fit: Fit | None = None,
               dft: str = "direct") -> np.ndarray:
-    """Gradient of L = sum_{f,k} g[f,k] lambda_{k,f} with respect to X.
+    """Gradient of L = sum_{f,k} g[f,k] lambda_{k,f} with respect to X (not in
+    the paper: the adjoint of Eqs. blocks to spod-discrete-snapshots).
 
     For simple eigenvalues d lambda_k = psi_k^H dM_f psi_k.  With
     G_f = sum_k g[f,k] psi_k psi_k^H and R_f = 2 kappa W Qhat_f G_f (M x nb):
@@ -410,11 +426,15 @@ def spod_grad(X: np.ndarray, d: Desc, dLdlam: np.ndarray, fit: Fit | None = None
 
 
 def loss_from_fit(fit: Fit, dLdlam: np.ndarray) -> float:
+    """L = sum g lambda, the eigenvalue loss whose gradient spod_grad gives
+    (not in the paper)."""
     return float((np.asarray(dLdlam) * fit.lam).sum())
 
 
 def parseval_rhs(X: np.ndarray, d: Desc) -> float:
-    """(c^2 nfft / den) sum_l sum_n w_n^2 sum_m W_m |xt[l*step+n, m]|^2.
+    """Parseval's theorem for the block DFT of Eq. blocks-ft summed as in Eq.
+    csd-discrete (a pin, not a step of the method):
+    (c^2 nfft / den) sum_l sum_n w_n^2 sum_m W_m |xt[l*step+n, m]|^2.
 
     Equals sum_f g_f tr(M_f) with g_f = 1 for f = 0 and f = nfft/2 (even nfft)
     and 2 otherwise (Parseval for each block's DFT of a real sequence); for
@@ -433,6 +453,8 @@ def parseval_rhs(X: np.ndarray, d: Desc) -> float:
 
 
 def one_sided_multiplicity(nfft: int) -> np.ndarray:
+    """How often each one-sided bin (after Eq. discrete_modes) stands for itself
+    in the full spectrum of real data: 1 for DC and Nyquist, 2 otherwise."""
     g = np.full(n_freqs(nfft), 2.0)
     g[0] = 1.0
     if nfft % 2 == 0:
@@ -462,7 +484,8 @@ def gram_chunked(X: np.ndarray | None, d: Desc, mu: np.ndarray, chunk: int,
 
 
 def point_qhat(xcol: np.ndarray, d: Desc, mu_m: float) -> np.ndarray:
-    """Qhat[f][l] for one spatial point (direct DFT); xcol is X[:, m]."""
+    """Qhat[f][l] for one spatial point (Eqs. blocks-ft, blocks-k; direct DFT);
+    xcol is X[:, m]."""
     return block_dft(np.asarray(xcol, dtype=np.float64)[:, None], d.nfft, d.noverlap,
                      d.w(), np.array([mu_m]) if d.subtract_mean else None)[:, :, 0]
 
@@ -506,12 +529,13 @@ def gram_at_freqs(d: Desc, fsel, get_chunk, chunk: int) -> np.ndarray:
 # Eqs. coeffs and SPODrec)
 # --------------------------------------------------------------------------
 def is_self_conjugate_bin(f: int, nfft: int) -> bool:
-    """DC and (even nfft) Nyquist: the one-sided bins of real data whose DFT is real."""
+    """DC and (even nfft) Nyquist: the one-sided bins of real data whose DFT is
+    real, which have no separate conjugate bin in Eq. coeffs."""
     return f == 0 or (nfft % 2 == 0 and f == nfft // 2)
 
 
 def coeff_basis(Phi: np.ndarray, fsel, nmodes_r: int, nfft: int) -> tuple[np.ndarray, list]:
-    """Columns of Phi_r for real data: the leading nmodes_r modes of every
+    """Columns of Phi_r of Eq. coeffs for real data: the leading nmodes_r modes of every
     selected one-sided bin and, for the bins other than DC and Nyquist, their
     complex conjugates (the modes of the negative frequency -f, so that the
     two-sided set is closed under conjugation and the reconstruction of real
