@@ -8,7 +8,7 @@ Metric: snapshot-GB/s = nt * M * sizeof(element) / (time per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3]
                     [--impl native|reference] [--no-compare] [--no-e2e] [--no-cpu]
-    python bench.py --complex | --coeffs | --ooc     (separate measurements)
+    python bench.py --complex | --coeffs | --ooc | --backward     (separate measurements)
 
 The default precision is bf16x3 (BF16 tensor-core Gram and modes with split
 products); the same input is then also run through the plain FP32 GPU form
@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--complex", action="store_true",
                     help="complex input of the same shape (the jet field + i x a second seed's field, "
                          "two-sided spectrum); a separate measurement, not the headline line")
+    ap.add_argument("--backward", action="store_true",
+                    help="time spod_backward (the adjoint of the eigenvalues) after a fit on the headline grid; "
+                         "a separate measurement")
     ap.add_argument("--ooc", action="store_true",
                     help="time the out-of-core run (spod_run_host_ooc: X and Phi in pinned host memory, column "
                          "tiles over the host link) on the headline grid; a separate measurement")
@@ -173,6 +176,8 @@ def main():
         return coeffs_leg(args, rank)
     if args.ooc:
         return ooc_leg(args, rank)
+    if args.backward:
+        return backward_leg(args, rank)
 
     import __graft_entry__ as g
     from paper_2309_11808_gb300 import _lib
@@ -504,6 +509,64 @@ def coeffs_leg(args, rank):
                          "unit": "TFLOP/s", "frac": round(flops / (ms * 1e-3) / 1e12 / FP32_PEAK, 4),
                          "flops": flops},
             "relative_residual_energy": round(rel, 5)}
+    print(json.dumps(line), flush=True)
+    sp.close()
+
+
+def backward_leg(args, rank):
+    """spod_backward on the headline grid after one fit (Qhat resident): the
+    G_f kernel, R_f = W Qhat_f G_f on the mode kernels in adjoint mode (Qhat
+    read, R written) and the inverse-DFT overlap-add kernel (R read, dL/dX
+    written).  CUDA events on the launching stream; dL/dlambda = 1 for every
+    eigenvalue (the loss sum_f tr M_f)."""
+    import torch
+    import __graft_entry__ as g
+    from paper_2309_11808_gb300 import SPOD, _lib
+    from workloads import jet_like
+    g.build()
+    dev = torch.device("cuda", 0)
+    wl = jet_like(nx=NX, nr=NR, nvars=NVARS, nt=NT, nfft=NFFT, seed=rank, dtype=torch.float32, device=dev)
+    X = wl.X
+    M = X.shape[1]
+    sp = SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=torch.float32, precision=args.precision, weights=wl.W)
+    sp.fit(X)
+    sp.eigs()                                   # the fit's status before timing
+    nb, nf = sp.nb, sp.nf
+    gl = torch.ones((nf, nb), dtype=torch.float64, device=dev)
+    dX = torch.empty(X.shape, dtype=torch.float64 if args.precision == "fp64" else torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        _lib.spod_backward(sp.handle, gl, X, dX, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        _lib.spod_backward(sp.handle, gl, X, dX, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    _lib.spod_sync(sp.handle, st)
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    eb = 16 if args.precision == "fp64" else 8
+    q = qhat_bytes_per_point(nb, nf, args.precision) * M
+    r = nf * nb * M * eb
+    dx = NT * M * dX.element_size()
+    byts = q + r + r + dx                        # Qhat read, R written and read back, dL/dX written
+    ach = byts / (ms * 1e-3) / 1e9
+    line = {"metric": "SPOD adjoint (spod_backward) ms per call", "value": round(ms, 3), "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "warmup": max(3, args.warmup),
+            "config": {"workload": f"jet-shaped {NX}x{NR}x{NVARS}, nt={NT}, nfft={NFFT}, 50% overlap",
+                       "precision": args.precision, "nb": nb, "nf": nf, "dLdlambda": "ones"},
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach / hbm, 4), "bytes_per_call": int(byts),
+                         "note": "Qhat read + R written + R read + dL/dX written"},
+            "finite": bool(torch.isfinite(dX).all())}
     print(json.dumps(line), flush=True)
     sp.close()
 
