@@ -20,8 +20,7 @@ decompositions in the PySPOD package" (arXiv 2309.11808), Sec. 2.2
 * complex data (the paper allows complex Q, Eq. data-matrix): every bin
   f = 0 .. N_f - 1 is kept, since there is no conjugate symmetry
 
-Readings where the paper is silent or at odds with itself (all listed in the
-design notes of the repository):
+Readings where the paper is silent or at odds with itself:
 
 * Gram normalisation: 1/L by default; 1/(L-1), the "Bessel" factor of
   Eq. csd-discrete, as an option.
@@ -462,34 +461,43 @@ def one_sided_multiplicity(nfft: int) -> np.ndarray:
     return g
 
 
-def gram_chunked(X: np.ndarray | None, d: Desc, mu: np.ndarray, chunk: int,
-                 get_chunk=None, dft: str = "fft") -> np.ndarray:
-    """Gram of Eq. spod-discrete-snapshots accumulated over spatial chunks.
+def qhat_at_freqs(xcols: np.ndarray, d: Desc, fsel, mu: np.ndarray | None = None) -> np.ndarray:
+    """Qhat[f][l][j] (Eqs. blocks-ft, blocks-k) of a few spatial columns at the
+    selected one-sided bins only, from the rows of the DFT matrix for those
+    bins (the plain definition of Eq. blocks-ft restricted to f in ``fsel``).
 
-    For inputs too large to hold as FP64 at once.  ``get_chunk(m0, m1)`` returns
-    X[:, m0:m1] (any real dtype, promoted exactly to FP64).  The chunk partial
-    Grams are summed in chunk order, the same sum as ``gram`` over all points.
-    """
-    W = d.W()
+    ``xcols`` is X[:, cols] (promoted exactly to FP64); ``mu`` their temporal
+    means over all nt snapshots (computed here when None and the descriptor
+    subtracts the mean).  Returns [len(fsel)][nb][ncols] complex."""
+    fsel = np.asarray(fsel, dtype=np.int64)
+    xc = np.asarray(xcols, dtype=np.float64)
+    if xc.ndim == 1:
+        xc = xc[:, None]
+    if d.subtract_mean:
+        xc = xc - (time_mean(xc) if mu is None else np.asarray(mu, dtype=np.float64))[None, :]
     w = d.w()
-    acc = np.zeros((d.nf, d.nb, d.nb), dtype=np.complex128)
-    for m0 in range(0, d.M, chunk):
-        m1 = min(d.M, m0 + chunk)
-        xc = X[:, m0:m1] if get_chunk is None else get_chunk(m0, m1)
-        Qc = block_dft(np.asarray(xc, dtype=np.float64), d.nfft, d.noverlap, w,
-                       mu[m0:m1] if d.subtract_mean else None, method=dft)
-        Qw = np.conj(Qc) * W[None, None, m0:m1]
-        acc += np.matmul(Qw, np.transpose(Qc, (0, 2, 1)))
-    return acc / gram_denominator(d.nb, d.norm)
+    c = 1.0 / w.sum()
+    E = dft_matrix(d.nfft)[fsel]                      # [F][nfft]
+    step = d.nfft - d.noverlap
+    Q = np.empty((len(fsel), d.nb, xc.shape[1]), dtype=np.complex128)
+    for l in range(d.nb):
+        Q[:, l, :] = c * (E @ (w[:, None] * xc[l * step: l * step + d.nfft]))
+    return Q
 
 
-def point_qhat(xcol: np.ndarray, d: Desc, mu_m: float) -> np.ndarray:
-    """Qhat[f][l] for one spatial point (Eqs. blocks-ft, blocks-k; direct DFT);
-    xcol is X[:, m]."""
-    return block_dft(np.asarray(xcol, dtype=np.float64)[:, None], d.nfft, d.noverlap,
-                     d.w(), np.array([mu_m]) if d.subtract_mean else None)[:, :, 0]
-
-
+def modes_at(Q: np.ndarray, lam: np.ndarray, Psi: np.ndarray, nmodes: int, norm: str, nb: int) -> np.ndarray:
+    """Modes of Eq. spod-discrete-snapshots restricted to the columns whose
+    Qhat is given: Phi[f][k][j] = sum_l Q[f][l][j] Psi[f][l][k] / sqrt(den * lambda_k)
+    with den the Gram denominator (the scaling for which Phi^* W Phi = I over
+    the whole grid), zero where lambda_k <= MODE_RANK_TOL * lambda_1.  Q, lam and
+    Psi are those of the same selected bins."""
+    den = gram_denominator(nb, norm)
+    out = np.zeros((Q.shape[0], nmodes, Q.shape[2]), dtype=np.complex128)
+    for i in range(Q.shape[0]):
+        for k in range(nmodes):
+            if lam[i, k] > MODE_RANK_TOL * lam[i, 0] and lam[i, k] > 0:
+                out[i, k] = (Q[i].T @ Psi[i][:, k]) / np.sqrt(den * lam[i, k])
+    return out
 
 
 def gram_at_freqs(d: Desc, fsel, get_chunk, chunk: int) -> np.ndarray:

@@ -375,6 +375,42 @@ def test_gram_at_freqs_closed_form_and_full_gram():
     np.testing.assert_allclose(Gn, full[fsel], rtol=0, atol=1e-13 * np.abs(full).max())
 
 
+def test_qhat_at_freqs_matches_the_fft_transform():
+    # Selected-bin, selected-column Qhat from DFT rows (with each column's own
+    # mean) against numpy's FFT of the whole array (with the array's mean)
+    rng = _rng(31)
+    nt, M, nfft, nov = 700, 37, 96, 40
+    X = rng.standard_normal((nt, M)) + 3.0 * rng.standard_normal(M)[None, :]
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, window=O.WIN_HANN)
+    full = O.block_dft(X, nfft, nov, d.w(), X.mean(axis=0), method="fft")
+    fsel, cols = [0, 1, 7, 33, 48], [0, 5, 6, 36]
+    Q = O.qhat_at_freqs(X[:, cols], d, fsel)
+    np.testing.assert_allclose(Q, full[fsel][:, :, cols], rtol=0, atol=1e-12 * np.abs(full).max())
+    # without the mean, and with the means given
+    d0 = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nov, window=O.WIN_HANN, subtract_mean=False)
+    raw = O.block_dft(X, nfft, nov, d.w(), None, method="fft")
+    np.testing.assert_allclose(O.qhat_at_freqs(X[:, cols], d0, fsel), raw[fsel][:, :, cols], rtol=0,
+                               atol=1e-12 * np.abs(raw).max())
+    mu = X[:, cols].mean(axis=0)
+    np.testing.assert_allclose(O.qhat_at_freqs(X[:, cols], d, fsel, mu=mu), Q, rtol=0, atol=1e-13 * np.abs(Q).max())
+
+
+def test_modes_at_sampled_columns_equal_the_full_modes():
+    # Modes restricted to a few columns and bins equal those columns of the
+    # whole-grid modes (which are pinned by W-orthonormality above)
+    rng = _rng(32)
+    nt, M, nfft = 900, 60, 64
+    W = 0.5 + rng.random(M)
+    X = rng.standard_normal((nt, M))
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=32, weights=W, norm=O.NORM_NB_MINUS_1)
+    fit = O.spod_fit(X, d)
+    Phi = O.spod_modes(fit, d, 6)
+    fsel, cols = [0, 3, 20, 32], [1, 2, 30, 59]
+    Q = O.qhat_at_freqs(X[:, cols], d, fsel)
+    Pm = O.modes_at(Q, fit.lam[fsel], fit.Psi[fsel], 6, d.norm, d.nb)
+    np.testing.assert_allclose(Pm, Phi[fsel][:, :, cols], rtol=0, atol=1e-12 * np.abs(Phi).max())
+
+
 # ---------------------------------------------------------------- complex data
 # Complex Q (allowed by Eq. data-matrix): all nfft bins, no conjugate symmetry.
 def test_complex_direct_dft_matches_fft_and_two_sided_parseval():
