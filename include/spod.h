@@ -165,6 +165,33 @@ spod_status spod_plan_get_info(spod_plan_t plan, spod_plan_info* info);
  * 16-byte aligned.  Results stay in the plan (see spod_get_eigs).  Stream-ordered. */
 spod_status spod_fit(spod_plan_t plan, const void* d_X, void* stream);
 
+/* The paper's spatial decomposition (Sec. 3.1): each process owns a slab of
+ * the points, forms its part of every M_f (Eq. spod-discrete-snapshots is a
+ * sum over points), one reduction sums the parts, every process solves the
+ * same eigenproblems and computes the modes of its own points.  Here a slab is
+ * a plan over a contiguous range of columns of X (its own npoints / weights,
+ * X given as that slab's [nt][slab columns]); the exchange of the parts
+ * between processes or GPUs is the caller's.
+ *
+ * spod_fit_partial: the fit of the plan's points up to the weighted Gram
+ * (mean, blocks, window, DFT, the plan's fixed-order reduction, kappa
+ * applied), without the eigen-solve.  Writes that slab Gram to d_gram (device,
+ * caller-owned, [nf][nb][nb] interleaved complex FP64, 16-byte aligned) and
+ * keeps the slab's Qhat for the modes.  Stream-ordered. */
+spod_status spod_fit_partial(spod_plan_t plan, const void* d_X, double* d_gram, void* stream);
+
+/* spod_fit_from_grams (the reduction and the redundant eigen-solve of Sec. 3.1):
+ * the sum of nparts slab Grams d_grams[nparts][nf][nb][nb]
+ * (device, interleaved complex FP64, 16-byte aligned), taken in part order --
+ * so every process that passes the same gathered parts gets bit-identical
+ * results -- then the eigen-solve.  Afterwards the plan behaves as after
+ * spod_fit of the whole domain: spod_get_eigs gives the global eigenpairs,
+ * spod_modes the modes restricted to this plan's points, spod_backward the
+ * gradient with respect to this plan's columns.  SPOD_ESTATE unless
+ * spod_fit_partial ran on this plan before; SPOD_EINVAL for nparts < 1.
+ * Stream-ordered. */
+spod_status spod_fit_from_grams(spod_plan_t plan, const double* d_grams, int nparts, void* stream);
+
 /* Copy the eigenvalues lambda[nf][nb] of the M_f of Eq.
  * spod-discrete-snapshots (FP64, descending per frequency) and,
  * when psi != NULL, the eigenvectors psi[nf][nb (entry)][nb (vector)] as
@@ -288,20 +315,37 @@ spod_status spod_reconstruct(spod_plan_t plan, const void* d_Phi, int nmodes, in
 
 /* Launch-shape knobs (the autotuner's interface).  They change how work is
  * split across CTAs, never what is computed beyond floating-point grouping.
- * In spod_plan_set_tuning a zero field keeps the plan's current value. */
+ * In spod_plan_set_tuning a zero gram_splits or gram_flush_blocks keeps the
+ * plan's current value; modes_ctas, eig_max_iter and wait_timeout_us are set
+ * as given (0 = their default). */
 typedef struct {
   int gram_splits;        /* FP32/FP64: CTAs per frequency over the points of a chunk; BF16/BF16X3:
                              persistent CTAs of the tensor-core Gram (default one per SM);
                              1..gram_splits_max */
   int gram_splits_max;    /* read-only: bound set by the plan's workspace */
-  int gram_flush_blocks;  /* tensor-core Gram: 64-point blocks per FP32 accumulation group (1..64) */
+  int gram_flush_blocks;  /* tensor-core Gram: 64-point blocks per accumulation run in tensor memory
+                             (1..64, default 1).  The tensor core's FP32 accumulation rounds toward
+                             zero, so a longer run biases the Gram by about run length x 2^-24 */
   int modes_ctas;         /* tensor-core modes: CTAs per frequency (0 = automatic) */
+  int eig_max_iter;       /* eigen-solver: implicit QL iterations allowed per eigenvalue (0 = default 60;
+                             1..1000).  An eigenvalue that needs more is left as it stands and the
+                             next synchronising call returns SPOD_ENOTCONVERGED. */
+  int wait_timeout_us;    /* bound of every device wait (a TMA copy, an MMA, a pipeline stage), in
+                             microseconds (0 = default 2 s; 1..4000000).  A wait that runs out stops
+                             its kernel early (copies and MMAs in flight are let land first), the
+                             call's results are invalid, and the next synchronising call returns
+                             SPOD_ETIMEOUT; the plan stays usable.  Setting it synchronises the device. */
+  int wait_selftest;      /* 1: self-test of the bounded waits -- the tensor-core Gram (BF16 / BF16X3
+                             plans) leaves its first pipeline stage unfilled, so the waits on it run
+                             out after wait_timeout_us and the fit reports SPOD_ETIMEOUT; 0 (default):
+                             off.  No other effect. */
 } spod_tuning;
 
 /* The plan's launch shape into *tuning (host).  No counterpart in the paper. */
 spod_status spod_plan_get_tuning(spod_plan_t plan, spod_tuning* tuning);
-/* Set the launch shape (no counterpart in the paper).  SPOD_EINVAL for values
- * outside the stated ranges; takes effect from the next fit/modes call. */
+/* Set the launch shape and the limits (no counterpart in the paper).
+ * SPOD_EINVAL for values outside the stated ranges; takes effect from the
+ * next fit/modes call. */
 spod_status spod_plan_set_tuning(spod_plan_t plan, const spod_tuning* tuning);
 
 /* Autotuner: runs spod_fit on d_X (device, as spod_fit) under candidate
@@ -334,12 +378,15 @@ typedef enum {
 spod_status spod_profile_enable(spod_plan_t plan, int enable);
 spod_status spod_profile_read(spod_plan_t plan, double* ms, int64_t* launches);
 
-/* Allocation-free batched Hermitian eigen-decomposition (the eigen-solver step
- * of spod_fit on caller-provided matrices).  The paper has no counterpart:
- * this exists for callers that cannot call cudaMalloc -- code running under a
- * host framework that owns all device memory, real-time loops that cannot
- * take the allocator's latency or the device-wide synchronisation of
- * cudaFree, programs that reserve all their memory up front.
+/* Allocation-free batched Hermitian eigen-decomposition of caller-provided
+ * matrices.  The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc -- code running under a host framework that owns
+ * all device memory, real-time loops that cannot take the allocator's latency
+ * or the device-wide synchronisation of cudaFree, programs that reserve all
+ * their memory up front.  It runs a cyclic complex Jacobi solver (one CTA per
+ * matrix; spod_fit uses Householder + implicit QL instead) with the same
+ * conventions as spod_get_eigs, so the results agree with a fit's to
+ * rounding; its cost grows as nb^3 per sweep on the FP64 pipe.
  *   d_gram   : device, [nf][nb][nb] interleaved complex FP64 Hermitian
  *              matrices (16-byte aligned), read only.
  *   d_lambda : device, [nf][nb] FP64 eigenvalues, descending (8-byte aligned).
@@ -348,14 +395,17 @@ spod_status spod_profile_read(spod_plan_t plan, double* ms, int64_t* launches);
  *              real positive (16-byte aligned).
  * Scratch comes from one fixed 32 MiB device array inside the library (held
  * by every GPU that loads it until the process exits): the call needs
- * 256 + (nb > 48 ? nf * 32 * nb * nb : 0) bytes and returns SPOD_EINVAL when
- * that exceeds 32 MiB, or when nf < 1 or nb is outside 1..1024.  No device
- * memory is allocated.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress), so make it before any stream capture.
- * The call is enqueued on `stream` on the current device and then waits for
- * that stream, returning SPOD_ENOTCONVERGED if the solver hit its sweep cap.
- * All calls share the one array: calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialised by the caller. */
+ * 256 + (nb > 48 ? nf * 32 * nb * nb : 0) bytes of it, so nb <= 1023 at
+ * nf = 1, and returns SPOD_EINVAL when that exceeds 32 MiB, or when nf < 1
+ * or nb is outside 1..1024.  No device memory is allocated.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for that device: make that first call before any stream capture
+ * begins, and do not use this entry across a cudaDeviceReset (the kept
+ * address would be stale).  The call enqueues the solver on `stream` on the
+ * current device, then waits for that stream and returns SPOD_ENOTCONVERGED
+ * if the solver hit its sweep cap.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller. */
 spod_status spod_eigh_batched_noalloc(const double* d_gram, int nf, int nb, double* d_lambda, double* d_psi,
                                       void* stream);
 

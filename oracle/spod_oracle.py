@@ -424,6 +424,41 @@ def spod_grad(X: np.ndarray, d: Desc, dLdlam: np.ndarray, fit: Fit | None = None
     return dxt
 
 
+def grad_columns(xcols: np.ndarray, d: Desc, dLdlam: np.ndarray, Psi: np.ndarray, Wcols: np.ndarray,
+                 mu: np.ndarray | None = None) -> np.ndarray:
+    """The gradient of ``spod_grad`` restricted to a few spatial columns.
+
+    Column m of dL/dX depends on the data only through column m itself and
+    the eigenvectors Psi of the whole fit (through G_f): R_f[m, :] =
+    2 kappa W_m Qhat_f[:, m]^T G_f, then the inverse one-sided DFT, window,
+    overlap-add and the mean projection of that column.  ``xcols`` is X[:, cols]
+    (promoted exactly to FP64), ``Wcols`` their weights, ``Psi`` [nf][nb][nb]
+    the whole fit's eigenvectors; ``mu`` the columns' means (computed when
+    None).  Returns dL/dX[:, cols]."""
+    xc = np.asarray(xcols, dtype=np.float64)
+    nf = n_freqs(d.nfft)
+    Q = qhat_at_freqs(xc, d, np.arange(nf), mu)          # [nf][nb][ncols]
+    nb = Q.shape[1]
+    kappa = 1.0 / gram_denominator(nb, d.norm)
+    w = d.w()
+    c = 1.0 / w.sum()
+    step = d.nfft - d.noverlap
+    g = np.asarray(dLdlam, dtype=np.float64)
+    G = np.matmul(Psi * g[:, None, :], np.conj(np.transpose(Psi, (0, 2, 1))))
+    R = 2.0 * kappa * np.asarray(Wcols, dtype=np.float64)[None, :, None] * np.matmul(
+        np.transpose(Q, (0, 2, 1)), G)                     # [nf][ncols][nb]
+    f = np.arange(nf, dtype=np.int64)[None, :]
+    n = np.arange(d.nfft, dtype=np.int64)[:, None]
+    ang = 2.0 * np.pi * ((f * n) % d.nfft).astype(np.float64) / d.nfft
+    Einv = np.cos(ang) + 1j * np.sin(ang)
+    dxt = np.zeros((d.nt, xc.shape[1]))
+    for l in range(nb):
+        dxt[l * step: l * step + d.nfft] += c * w[:, None] * (Einv @ R[:, :, l]).real
+    if d.subtract_mean:
+        dxt = dxt - dxt.mean(axis=0, keepdims=True)
+    return dxt
+
+
 def loss_from_fit(fit: Fit, dLdlam: np.ndarray) -> float:
     """L = sum g lambda, the eigenvalue loss whose gradient spod_grad gives
     (not in the paper)."""

@@ -26,8 +26,8 @@ EXPORTED = ["spod_desc_init", "spod_plan_create", "spod_plan_destroy", "spod_pla
             "spod_get_eigs", "spod_get_gram", "spod_get_freqs", "spod_modes", "spod_backward",
             "spod_run_host", "spod_run_host_many", "spod_sync", "spod_fit_batch", "spod_profile_enable",
             "spod_profile_read", "spod_eigh_batched_noalloc", "spod_plan_get_tuning", "spod_plan_set_tuning",
-            "spod_plan_autotune", "spod_coeffs", "spod_reconstruct", "spod_run_host_ooc", "spod_last_error",
-            "spod_version"]
+            "spod_plan_autotune", "spod_coeffs", "spod_reconstruct", "spod_run_host_ooc", "spod_fit_partial",
+            "spod_fit_from_grams", "spod_last_error", "spod_version"]
 
 PHASES = ["mean", "fft", "gram", "reduce", "eig", "modes", "backward"]
 
@@ -48,7 +48,8 @@ class spod_plan_info(C.Structure):
 
 class spod_tuning(C.Structure):
     _fields_ = [("gram_splits", C.c_int), ("gram_splits_max", C.c_int), ("gram_flush_blocks", C.c_int),
-                ("modes_ctas", C.c_int)]
+                ("modes_ctas", C.c_int), ("eig_max_iter", C.c_int), ("wait_timeout_us", C.c_int),
+                ("wait_selftest", C.c_int)]
 
 
 class SpodError(RuntimeError):
@@ -92,6 +93,8 @@ def lib() -> C.CDLL:
         L.spod_coeffs.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), P, P]
         L.spod_run_host_ooc.argtypes = [P, P, C.c_int, P, P, C.c_int64, P]
         L.spod_reconstruct.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), P, P, P]
+        L.spod_fit_partial.argtypes = [P, P, P, P]
+        L.spod_fit_from_grams.argtypes = [P, P, C.c_int, P]
         L.spod_last_error.restype = C.c_char_p
         L.spod_version.restype = C.c_char_p
         for name in EXPORTED[:-2]:
@@ -151,6 +154,14 @@ def spod_plan_get_info(plan: int) -> spod_plan_info:
 
 def spod_fit(plan: int, X, stream=None) -> None:
     check(lib().spod_fit(plan, _ptr(X), _stream(stream)), "spod_fit")
+
+
+def spod_fit_partial(plan: int, X, gram, stream=None) -> None:
+    check(lib().spod_fit_partial(plan, _ptr(X), _ptr(gram), _stream(stream)), "spod_fit_partial")
+
+
+def spod_fit_from_grams(plan: int, grams, nparts: int, stream=None) -> None:
+    check(lib().spod_fit_from_grams(plan, _ptr(grams), int(nparts), _stream(stream)), "spod_fit_from_grams")
 
 
 def spod_get_eigs(plan: int, lam, psi=None, on_device: bool = False) -> None:
@@ -239,8 +250,10 @@ def spod_plan_get_tuning(plan: int) -> spod_tuning:
     return t
 
 
-def spod_plan_set_tuning(plan: int, gram_splits: int = 0, gram_flush_blocks: int = 0, modes_ctas: int = 0) -> None:
-    t = spod_tuning(int(gram_splits), 0, int(gram_flush_blocks), int(modes_ctas))
+def spod_plan_set_tuning(plan: int, gram_splits: int = 0, gram_flush_blocks: int = 0, modes_ctas: int = 0,
+                         eig_max_iter: int = 0, wait_timeout_us: int = 0, wait_selftest: int = 0) -> None:
+    t = spod_tuning(int(gram_splits), 0, int(gram_flush_blocks), int(modes_ctas), int(eig_max_iter),
+                    int(wait_timeout_us), int(wait_selftest))
     check(lib().spod_plan_set_tuning(plan, C.byref(t)), "spod_plan_set_tuning")
 
 

@@ -54,6 +54,7 @@ __global__ void k_adj_gmat(const double* __restrict__ g, const double* __restric
 
 struct AdjArgs {
   int64_t M, m0, mcount, nt;
+  int64_t roff;                      // point of R's first column
   int nfft, step, nb, nf;
   int subtract_mean;
   double inv_nt;
@@ -79,7 +80,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const typename C2<R>::T* __rest
   R* red = mean + TP;                                       // [256] reduction scratch
 
   const int64_t lm0 = (int64_t)blockIdx.x * TP;
-  const int64_t gm0 = a.m0 + lm0;
+  const int64_t gm0 = a.m0 + lm0;                           // global point (dX)
+  const int64_t rm0 = gm0 - a.roff;                         // column in R
   const int tid = threadIdx.x;
   for (int i = tid; i < N; i += blockDim.x) tw[i] = tw_g[i];
   for (int i = tid; i < a.nf; i += blockDim.x) wc[i] = wc_g[i];
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const typename C2<R>::T* __rest
     if (lm0 + p < a.mcount) {
       for (int e = q; e < a.nb * a.nf; e += Q) {
         const int l = e / a.nf, f = e - l * a.nf;
-        const V r = Rsp[((int64_t)f * a.nb + l) * rs + gm0 + p];
+        const V r = Rsp[((int64_t)f * a.nb + l) * rs + rm0 + p];
         const V w = wc[f];
         acc += r.x * w.x - r.y * w.y;
       }
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const typename C2<R>::T* __rest
       const int fm = (f == 0) ? 0 : N - f;
       V ha = mk<R>(0, 0), hb = mk<R>(0, 0);
       const int64_t pa = lm0 + 2 * j;       // local index (bounds)
-      const int64_t ga = gm0 + 2 * j;       // global index (storage)
+      const int64_t ga = rm0 + 2 * j;       // column in R
       if (f < a.nf) {
         if (pa < a.mcount) ha = Rsp[((int64_t)f * a.nb + l) * rs + ga];
         if (pa + 1 < a.mcount) hb = Rsp[((int64_t)f * a.nb + l) * rs + ga + 1];
@@ -191,11 +193,11 @@ __global__ void __launch_bounds__(256) k_adjoint(const typename C2<R>::T* __rest
 }
 
 template <typename R>
-cudaError_t launch_adjoint_t(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t m0, int64_t mcount,
-                             void* d_dX, cudaStream_t s) {
+cudaError_t launch_adjoint_t(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t roff, int64_t m0,
+                             int64_t mcount, void* d_dX, cudaStream_t s) {
   constexpr int TP = sizeof(R) == 8 ? 8 : 16;
   AdjArgs a;
-  a.M = p.M; a.m0 = m0; a.mcount = mcount; a.nt = p.nt;
+  a.M = p.M; a.m0 = m0; a.mcount = mcount; a.nt = p.nt; a.roff = roff;
   a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;
   a.subtract_mean = p.desc.subtract_mean;
   a.inv_nt = 1.0 / (double)p.nt;
@@ -228,10 +230,10 @@ cudaError_t launch_adj_gmat(const spod_plan_s& p, const double* d_g, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_chunk(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t m0, int64_t mcount,
-                                 void* d_dX, cudaStream_t s) {
-  return p.f64 ? launch_adjoint_t<double>(p, d_R, rs, m0, mcount, d_dX, s)
-               : launch_adjoint_t<float>(p, d_R, rs, m0, mcount, d_dX, s);
+cudaError_t launch_adjoint_chunk(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t roff, int64_t m0,
+                                 int64_t mcount, void* d_dX, cudaStream_t s) {
+  return p.f64 ? launch_adjoint_t<double>(p, d_R, rs, roff, m0, mcount, d_dX, s)
+               : launch_adjoint_t<float>(p, d_R, rs, roff, m0, mcount, d_dX, s);
 }
 
 }  // namespace spod

@@ -215,7 +215,7 @@ template <typename R, int KG>
 __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, int64_t rs, int nb, int nmodes,
                                                     int nmp, int64_t mcount, int64_t m0, int64_t M,
                                                     const R* __restrict__ bmat, const R* __restrict__ scale,
-                                                    R* __restrict__ phi, int f0, int64_t phioff) {
+                                                    R* __restrict__ phi, int f0, int64_t phioff, int64_t qoff) {
   using V2 = typename Cplx<R>::T;
   const int f = f0 + blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, 
   const int64_t m = m0 + lm;
   const R s0 = scale[m], s1 = two ? scale[m + 1] : (R)0;
   // point lm + 1 < mpad: the FFT wrote zeros past mcount, so the pair load stays in the chunk
-  const R* qf = qhat + (int64_t)f * 2 * nb * rs + lm;
+  const R* qf = qhat + (int64_t)f * 2 * nb * rs + qoff + lm;
   const bool vec = (M % 2) == 0;                                  // two points = one aligned 2-complex store
   for (int k0 = 0; k0 < nmodes; k0 += KG) {
     R ar0[KG], ai0[KG], ar1[KG], ai1[KG];
@@ -315,7 +315,8 @@ cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s)
 
 template <typename R>
 static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1) {
+                                  cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1, int64_t qoff,
+                                  int64_t out_ld, int64_t out_off) {
   constexpr int KG = sizeof(R) == 8 ? 8 : 16;
   const int nmp = (nmodes + KG - 1) / KG * KG;
   const size_t smem = sizeof(typename Cplx<R>::T) * (size_t)p.nb * nmp;
@@ -324,11 +325,11 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
   if (e != cudaSuccess) return e;
   constexpr int threads = 128;
   dim3 grid((unsigned)((mcount + 2 * threads - 1) / (2 * threads)), (unsigned)(f1 - f0));
-  const int64_t ld = (p.phi_ld && !adjoint) ? p.phi_ld : p.M;
+  const int64_t ld = out_ld ? out_ld : (p.phi_ld && !adjoint) ? p.phi_ld : p.M;
   kern<<<grid, threads, smem, s>>>(static_cast<const R*>(p.d_qhat), p.chunk_points, p.nb, nmodes, nmp, mcount, m0,
                                    ld, static_cast<const R*>(p.d_bmat),
                                    static_cast<const R*>(adjoint ? p.d_sqrtW : p.d_rsqrtW), static_cast<R*>(d_Phi),
-                                   f0, adjoint ? 0 : p.phi_off);
+                                   f0, out_ld ? out_off : adjoint ? 0 : p.phi_off, qoff);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nlaunch;
@@ -336,11 +337,14 @@ static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcou
 }
 
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                               cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1) {
+                               cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1, int64_t qoff,
+                               int64_t out_ld, int64_t out_off) {
   if (f1 < 0) f1 = p.nf;
-  if (f0 < 0 || f1 > p.nf || f0 >= f1) return cudaErrorInvalidValue;
-  return p.f64 ? launch_modes_t<double>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint, f0, f1)
-               : launch_modes_t<float>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint, f0, f1);
+  if (f0 < 0 || f1 > p.nf || f0 >= f1 || qoff % 2 != 0) return cudaErrorInvalidValue;
+  return p.f64 ? launch_modes_t<double>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint, f0, f1, qoff, out_ld,
+                                        out_off)
+               : launch_modes_t<float>(p, m0, mcount, nmodes, d_Phi, s, nlaunch, adjoint, f0, f1, qoff, out_ld,
+                                       out_off);
 }
 
 }  // namespace spod

@@ -35,7 +35,7 @@ namespace spod {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxIter = 60;           // QL iterations per eigenvalue
+constexpr int kMaxIter = 60;           // QL iterations per eigenvalue (default; the plan may set another cap)
 constexpr int kBarFull = 1;            // named barriers 1, 2: rotation buffer published
 constexpr int kBarEmpty = 3;           // named barriers 3, 4: rotation buffer applied
 constexpr int kBarQ = 5;               // named barrier of the Q-forming warps
@@ -233,7 +233,7 @@ __device__ __noinline__ int ql_sweep_dw(float2* dd, float2* ee, int l, int mm, d
 // rewritten the appliers must have released it; at the end the last buffer
 // is waited for, so every arrival on the named barriers is matched.
 template <bool kDW>
-__device__ void ql_producer(double* d, double* e, int n, double* rc, double* rsn, int* ctl) {
+__device__ void ql_producer(double* d, double* e, int n, double* rc, double* rsn, int* ctl, int max_iter) {
   const int lane = threadIdx.x & 31;
   double tn = 0.0;
   for (int i = lane; i < n; i += 32) tn = fmax(tn, fabs(d[i]) + fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0));
@@ -274,7 +274,7 @@ __device__ void ql_producer(double* d, double* e, int n, double* rc, double* rsn
         if (bal) { mm = base + __ffs(bal) - 1; break; }
       }
       if (mm == l) break;
-      if (iter >= kMaxIter) {                 // give up on this eigenvalue
+      if (iter >= max_iter) {                 // give up on this eigenvalue
         if (lane == 0) ctl[0] = 1;
         break;
       }
@@ -377,7 +377,8 @@ __device__ void form_q(const double2* A, double2* Qm, int lda, int n, const doub
 template <bool kDW>
 __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restrict__ gram, int n,
                                                           double* __restrict__ lam, double* __restrict__ psi,
-                                                          double* __restrict__ gws, unsigned* __restrict__ flags) {
+                                                          double* __restrict__ gws, unsigned* __restrict__ flags,
+                                                          int max_iter) {
   const int f = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int warp = tid >> 5;
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
   __syncthreads();
 
   // ---------------- 2. QL (warp 0) | Z updates (warps 1-2) | Q (warps 3-7)
-  if (warp == 0) ql_producer<kDW>(d, e, n, rc, rsn, ctl);
+  if (warp == 0) ql_producer<kDW>(d, e, n, rc, rsn, ctl, max_iter);
   else if (warp < 3) ql_applier(Z, lda, n, rc, rsn, ctl);
   else form_q(A, Qm, lda, n, tau, pv);
   __syncthreads();
@@ -580,7 +581,8 @@ cudaError_t launch_eig_tridiag(const spod_plan_s& p, cudaStream_t s) {
   auto kern = p.f64 ? k_eig_tridiag<false> : k_eig_tridiag<true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<p.nf, kThreads, smem, s>>>(p.d_gram, p.nb, p.d_lam, p.d_psi, p.d_eigws, p.d_flags);
+  kern<<<p.nf, kThreads, smem, s>>>(p.d_gram, p.nb, p.d_lam, p.d_psi, p.d_eigws, p.d_flags,
+                                    p.eig_max_iter > 0 ? p.eig_max_iter : kMaxIter);
   return cudaGetLastError();
 }
 

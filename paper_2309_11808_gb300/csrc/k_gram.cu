@@ -217,6 +217,27 @@ __global__ void k_gram_reduce(const double* __restrict__ gpart, int splits, int 
   }
 }
 
+// Sum of the Grams of nparts spatial slabs (Sec. 3.1: the one reduction of the
+// paper's spatial decomposition), [nparts][nf][nb][nb] complex FP64, in part
+// order (the same sum, bit for bit, wherever the same parts are given), NaN check.
+__global__ void k_gram_sum_parts(const double* __restrict__ parts, int nparts, int nf, int nb,
+                                 double* __restrict__ gram, unsigned* __restrict__ flags) {
+  const int f = blockIdx.x;
+  const int64_t per = (int64_t)nf * nb * nb * 2;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int64_t o = ((int64_t)f * nb * nb + e) * 2;
+    double vr = 0.0, vi = 0.0;
+    for (int q = 0; q < nparts; ++q) {
+      vr += parts[q * per + o];
+      vi += parts[q * per + o + 1];
+    }
+    const int i = e / nb, j = e - i * nb;
+    if (i == j && !isfinite(vr)) atomicOr(flags, FLAG_NAN);
+    gram[o] = vr;
+    gram[o + 1] = vi;
+  }
+}
+
 // Staging buffers (two when they fit) and shared bytes for element size rb.
 int gram_simt_nbuf(int nb, size_t rb, size_t* smem_out) {
   const size_t acc = sizeof(double) * 32 * kThreads;
@@ -255,6 +276,11 @@ size_t gram_simt_smem_bytes(const spod_plan_s& p) {
 
 cudaError_t launch_gram_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s) {
   return p.f64 ? launch_gram_t<double>(p, mcount, first, s) : launch_gram_t<float>(p, mcount, first, s);
+}
+
+cudaError_t launch_gram_sum_parts(const spod_plan_s& p, const double* parts, int nparts, cudaStream_t s) {
+  k_gram_sum_parts<<<p.nf, 256, 0, s>>>(parts, nparts, p.nf, p.nb, p.d_gram, p.d_flags);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_reduce(const spod_plan_s& p, cudaStream_t s) {

@@ -9,7 +9,13 @@
 // boxes (NP rows x 64 points x 2 blocks, NP = 2nb rounded up to 16, 128-byte
 // swizzle) of hi and, for BF16X3, of lo.  Per K step of 16 (N = NP):
 //   A1 (+)= hi hi^T   restarted every `flush` blocks (short FP32 runs in the
-//                      tensor core), drained into Kahan-compensated registers;
+//                      tensor core), drained into Kahan-compensated registers.
+//                      The tensor core's FP32 accumulation rounds toward zero,
+//                      so a run of R MMAs carries a relative bias of about
+//                      R * 2^-24 on the positive diagonal; measured on the
+//                      512 x 256 x 3 jet grid, the mean diagonal bias was
+//                      -2e-7 / -6e-7 / -3e-6 / -1.4e-5 for runs of 2 / 4 / 16 / 64
+//                      blocks.  Runs are therefore short (one or two blocks);
 //   A2 (+)= hi lo^T   BF16X3, one run per frequency segment (2^-8 of D, so its
 //                      tensor-core rounding is far below the FP32 level of D),
 //                      read once when the segment ends;
@@ -44,14 +50,18 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTmaWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1, kDiagWarp0 = kEpiWarps + 2;
 constexpr int kDiagThreads = 64;
 constexpr int kThreadsGram = (kEpiWarps + 4) * 32;
-constexpr uint32_t kTmemCols = 512;       // A1 buffers at columns 0 and 128, A2 buffers at 256 and 384
+constexpr uint32_t kTmemCols = 512;       // A1 buffers at columns b * np (b < nacc), then two A2 buffers
+constexpr int kMaxAcc = 4;                // A1 accumulator buffers at most
 
 struct GramTcArgs {
   int nb, r2, np, nf;
   int64_t nkb;                            // items (block pairs) per frequency in this chunk
   int64_t nblk;                           // 64-point blocks per frequency in this chunk
   int64_t nitems;                         // nf * nkb
-  int flush;                              // items per A1 run
+  int flush;                              // 64-point blocks per A1 run
+  int nacc;                               // A1 buffers in tensor memory (2..kMaxAcc, as np allows)
+  int stall0;                             // self-test: the first item's copies are never issued, so
+                                          // every wait on them runs out (the bounded-wait path)
   int nst;                                // pipeline stages
   uint32_t box_bytes;                     // one 64-point block of one operand: NP rows x 128 bytes
 };
@@ -75,24 +85,30 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct GramHdr {
-  uint64_t full[kMaxStages], empty[kMaxStages], accfull[2], accempty[2], a2empty[2], drain;
+  uint64_t full[kMaxStages], empty[kMaxStages], accfull[kMaxAcc], accempty[kMaxAcc], a2empty[2], drain;
   uint32_t tmem_base;
   int abort;
 };
 
-// Walks the group and segment structure of a CTA's item range: a segment is
-// the run of one frequency, a group at most `flush` consecutive items of a
-// segment.  All roles step it identically.
+// Walks the group and segment structure of a CTA's range, one 64-point
+// block at a time: a segment is the run of one frequency, a group (one A1
+// run in tensor memory) at most `flush` consecutive blocks of a segment; a
+// group may end inside an item.  All roles step it identically.
 struct GroupWalk {
   int fprev = -1;
   int in_group = 0;
   int g = -1, seg = -1;
+  int acc = -1, accph = 0;      // the group's A1 buffer and the parity of its use (g / nacc) & 1
   bool sstart = false;
-  __device__ __forceinline__ bool step(int f, int flush) {   // true when the item starts a group
+  __device__ __forceinline__ bool step(int f, int flush, int nacc) {   // true when the block starts a group
     sstart = f != fprev;
     const bool start = sstart || in_group == flush;
     if (sstart) ++seg;
-    if (start) { ++g; in_group = 0; }
+    if (start) {
+      ++g;
+      in_group = 0;
+      if (++acc == nacc) { acc = 0; accph ^= 1; }
+    }
     ++in_group;
     fprev = f;
     return start;
@@ -148,9 +164,11 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
       // released by the MMA commit, and for BF16X3 also by the lo-square warps
       mbar_init(smem_u32(&hdr->empty[i]), X3 ? 1 + kDiagThreads : 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < a.nacc; ++i) {
       mbar_init(smem_u32(&hdr->accfull[i]), 1);
       mbar_init(smem_u32(&hdr->accempty[i]), kEpiThreads);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&hdr->a2empty[i]), kEpiThreads);
     }
     mbar_init(smem_u32(&hdr->drain), 1);
@@ -172,11 +190,16 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
     prefetch_tmap(&map_hi);
     if (X3) prefetch_tmap(&map_lo);
     int issued = 0;
+    const int skipped = a.stall0 ? 1 : 0;       // items at the head never issued (self-test)
     Cursor cu;
     cu.init(i0, nkb);
     for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
       const int s = cu.s;
       if (i >= a.nst && !mbar_wait(smem_u32(&hdr->empty[s]), cu.ph ^ 1, abort_flag, gflags)) break;
+      if (i < skipped) {
+        issued = i + 1;
+        continue;
+      }
       const uint32_t fb = smem_u32(&hdr->full[s]);
       mbar_arrive_expect_tx(fb, stage_bytes);
       uint8_t* st = stages + (size_t)s * stage_bytes;
@@ -185,7 +208,7 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
       issued = i + 1;
     }
     // copies still in flight must land before the CTA can exit
-    for (int i = max(0, issued - a.nst); i < issued; ++i)
+    for (int i = max(skipped, issued - a.nst); i < issued; ++i)
       mbar_drain(smem_u32(&hdr->full[i % a.nst]), (i / a.nst) & 1, gflags);
   } else if (warp == kMmaWarp && lane == 0 && nit > 0) {
     // ---------------- MMA issuer
@@ -193,41 +216,49 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
     GroupWalk gw;
     Cursor cu;
     cu.init(i0, nkb);
-    for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
+    bool ok = true;
+    for (int i = 0; i < nit && ok; ++i, cu.next(nkb, a.nst)) {
       const int f = cu.f, kp = cu.kp;
-      const bool gstart = gw.step(f, FB);
-      const bool sstart = gw.sstart;
-      const int g = gw.g, acc = g & 1, sg = gw.seg, a2b = sg & 1;
-      const bool gend = i + 1 == nit || cu.last_of_f(nkb) || gw.in_group == FB;
-      if (gstart && g >= 2 && !mbar_wait(smem_u32(&hdr->accempty[acc]), ((g >> 1) - 1) & 1, abort_flag, gflags))
-        break;
-      if (X3 && sstart && sg >= 2 &&
-          !mbar_wait(smem_u32(&hdr->a2empty[a2b]), ((sg >> 1) - 1) & 1, abort_flag, gflags))
-        break;
       const int s = cu.s;
       if (!mbar_wait(smem_u32(&hdr->full[s]), cu.ph, abort_flag, gflags)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(stages + (size_t)s * stage_bytes);
-      const uint32_t d1 = tmem + (uint32_t)acc * 128u;
-      const uint32_t d2 = tmem + 256u + (uint32_t)a2b * 128u;
-#pragma unroll
-      for (int j = 0; j < kKpb; ++j) {
-        // a block past the chunk's points (odd block count) holds no data of this chunk
-        if (kp * kKpb + j >= nblk) break;
+      // a block past the chunk's points (odd block count) holds no data of this chunk
+      const int nvalid = min(kKpb, nblk - kp * kKpb);
+      const bool item_last = i + 1 == nit || cu.last_of_f(nkb);
+      for (int j = 0; j < nvalid; ++j) {
+        const bool gstart = gw.step(f, FB, a.nacc);
+        const bool sstart = gw.sstart;              // only on an item's first block
+        const int g = gw.g, acc = gw.acc, sg = gw.seg, a2b = sg & 1;
+        const bool gend = (item_last && j + 1 == nvalid) || gw.in_group == FB;
+        // the buffer's previous run (use (g / nacc) - 1) must have been drained
+        if (gstart && g >= a.nacc &&
+            !mbar_wait(smem_u32(&hdr->accempty[acc]), gw.accph ^ 1, abort_flag, gflags)) {
+          ok = false;
+          break;
+        }
+        if (X3 && sstart && sg >= 2 &&
+            !mbar_wait(smem_u32(&hdr->a2empty[a2b]), ((sg >> 1) - 1) & 1, abort_flag, gflags)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d1 = tmem + (uint32_t)(acc * a.np);
+        const uint32_t d2 = tmem + (uint32_t)((a.nacc + a2b) * a.np);
         const uint32_t hi = st + (uint32_t)j * a.box_bytes;
         const uint32_t lo = hi + op_bytes;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint64_t dh = sdesc_sw128(hi + k * 32, 16, 1024);
-          mma_bf16(d1, dh, dh, idesc, (gstart && j == 0 && k == 0) ? 0u : 1u);     // A1 (+)= hi hi^T
+          mma_bf16(d1, dh, dh, idesc, (gstart && k == 0) ? 0u : 1u);                // A1 (+)= hi hi^T
           if (X3) {
             const uint64_t dl = sdesc_sw128(lo + k * 32, 16, 1024);
             mma_bf16(d2, dh, dl, idesc, (sstart && j == 0 && k == 0) ? 0u : 1u);   // A2 (+)= hi lo^T
           }
         }
+        if (gend) mma_commit(smem_u32(&hdr->accfull[acc]));
       }
-      mma_commit(smem_u32(&hdr->empty[s]));
-      if (gend) mma_commit(smem_u32(&hdr->accfull[acc]));
+      if (ok) mma_commit(smem_u32(&hdr->empty[s]));
     }
     mma_commit(smem_u32(&hdr->drain));
     mbar_drain(smem_u32(&hdr->drain), 0, gflags);
@@ -288,70 +319,97 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
       }
     }
   } else if (warp < kEpiWarps) {
-    // ---------------- epilogue: TMEM -> registers -> slots
+    // ---------------- epilogue: TMEM -> registers -> slots.  Warp (quad,
+    // half) drains rows quad*32 .. +31 and the HC columns of its half; of A1
+    // (symmetric) only the 8-column chunks that reach the upper triangle
+    // (some row of the quad <= some column of the chunk) are read and summed.
+    constexpr int CH = HC / 8;
     const int quad = warp & 3, half = warp >> 2;
-    const int hcols = a.np / 2;                   // multiple of 8, <= HC
     const int row = quad * 32 + lane;
-    const int col0 = half * hcols;
+    const int col0 = half * HC;
     const bool active = quad * 32 < a.r2;         // this lane quadrant holds rows of D
+    int nch = 0;                                  // chunks [CH - nch, CH) of this warp are upper-triangle ones
+#pragma unroll
+    for (int c = 0; c < CH; ++c) nch += (col0 + 8 * c + 7 >= quad * 32) ? 1 : 0;
+    const int c_first = CH - nch;
     float s1[HC], c1[HC];
 #pragma unroll
     for (int j = 0; j < HC; ++j) { s1[j] = 0.f; c1[j] = 0.f; }
     GroupWalk gw;
     Cursor cu;
     cu.init(i0, nkb);
-    for (int i = 0; i < nit; ++i, cu.next(nkb, a.nst)) {
-      const int f = cu.f;
-      gw.step(f, FB);
-      const bool send = i + 1 == nit || cu.last_of_f(nkb);
+    bool ok = true;
+    for (int i = 0; i < nit && ok; ++i, cu.next(nkb, a.nst)) {
+     const int f = cu.f;
+     const int nvalid = min(kKpb, nblk - cu.kp * kKpb);
+     const bool item_last = i + 1 == nit || cu.last_of_f(nkb);
+     for (int j = 0; j < nvalid; ++j) {
+      gw.step(f, FB, a.nacc);
+      const bool send = item_last && j + 1 == nvalid;
       const bool gend = send || gw.in_group == FB;
       if (!gend) continue;
-      const int g = gw.g, acc = g & 1, a2b = gw.seg & 1;
-      if (!mbar_wait(smem_u32(&hdr->accfull[acc]), (g >> 1) & 1, abort_flag, gflags)) break;
+      const int acc = gw.acc, a2b = gw.seg & 1;
+      // one decision per warp: the tcgen05.ld below must be executed by the whole warp
+      const bool got = mbar_wait(smem_u32(&hdr->accfull[acc]), gw.accph, abort_flag, gflags);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
-      uint8_t* slot = slots + ((size_t)blockIdx.x + (size_t)f) * gram_slot_bytes(a.r2);
-      const bool wr = send && row < a.r2;
-      if (active) {
-        // this warp's A1 columns in one batch of loads and one wait
-        const uint32_t t1 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 128u + (uint32_t)col0;
+      if (active && nch > 0) {
+        // this warp's A1 chunks in one batch of loads and one wait
+        const uint32_t t1 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * a.np) + (uint32_t)col0;
         float v[HC];
 #pragma unroll
-        for (int c = 0; c < HC / 8; ++c)
-          if (c * 8 < hcols) tmem_ld8(t1 + (uint32_t)(c * 8), v + c * 8);
+        for (int c = 0; c < CH; ++c)
+          if (c >= c_first) tmem_ld8(t1 + (uint32_t)(c * 8), v + c * 8);
         tmem_wait_ld();
         tc_fence_before();
         mbar_arrive(smem_u32(&hdr->accempty[acc]));
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (c >= c_first) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) kahan_add(s1[c * 8 + e], c1[c * 8 + e], v[c * 8 + e]);
+          }
+      } else {
+        tc_fence_before();
+        mbar_arrive(smem_u32(&hdr->accempty[acc]));
+      }
+      if (!send) continue;
+      // the CTA's run of frequency f ends: its sums go to slot (cta + f)
+      uint8_t* slot = slots + ((size_t)blockIdx.x + (size_t)f) * gram_slot_bytes(a.r2);
+      const bool wr = row < a.r2;
+      if (active) {
         float2* d1 = reinterpret_cast<float2*>(slot) + (size_t)row * a.r2 + col0;
 #pragma unroll
-        for (int j = 0; j < HC; ++j) {
-          if (j < hcols) {
-            kahan_add(s1[j], c1[j], v[j]);
-            if (send) {
-              if (wr && col0 + j < a.r2) d1[j] = make_float2(s1[j], c1[j]);
-              s1[j] = 0.f;
-              c1[j] = 0.f;
-            }
-          }
+        for (int jj = 0; jj < HC; ++jj) {
+          if (wr && col0 + jj < a.r2) d1[jj] = make_float2(s1[jj], c1[jj]);
+          s1[jj] = 0.f;
+          c1[jj] = 0.f;
         }
-        if (X3 && send) {
-          // the segment's A2 (its MMAs completed with the last group's)
-          const uint32_t t2 = tmem + ((uint32_t)(quad * 32) << 16) + 256u + (uint32_t)a2b * 128u + (uint32_t)col0;
+      }
+      if (X3) {
+        if (active) {
+          // the segment's A2 (its MMAs completed with the last group's), not symmetric: all of it
+          const uint32_t t2 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((a.nacc + a2b) * a.np) +
+                              (uint32_t)col0;
+          float v[HC];
 #pragma unroll
-          for (int c = 0; c < HC / 8; ++c)
-            if (c * 8 < hcols) tmem_ld8(t2 + (uint32_t)(c * 8), v + c * 8);
+          for (int c = 0; c < CH; ++c) tmem_ld8(t2 + (uint32_t)(c * 8), v + c * 8);
           tmem_wait_ld();
           tc_fence_before();
           mbar_arrive(smem_u32(&hdr->a2empty[a2b]));
           float* d2 = reinterpret_cast<float*>(slot + (size_t)a.r2 * a.r2 * 8) + (size_t)row * a.r2 + col0;
 #pragma unroll
-          for (int j = 0; j < HC; ++j)
-            if (j < hcols && wr && col0 + j < a.r2) d2[j] = v[j];
+          for (int jj = 0; jj < HC; ++jj)
+            if (wr && col0 + jj < a.r2) d2[jj] = v[jj];
+        } else {
+          tc_fence_before();
+          mbar_arrive(smem_u32(&hdr->a2empty[a2b]));
         }
-      } else {
-        tc_fence_before();
-        mbar_arrive(smem_u32(&hdr->accempty[acc]));
-        if (X3 && send) mbar_arrive(smem_u32(&hdr->a2empty[a2b]));
       }
+     }
     }
   }
   tc_fence_before();
@@ -366,7 +424,8 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
 __device__ __forceinline__ int64_t cta_of_item(int64_t i, int64_t W, int64_t G) { return ((i + 1) * G - 1) / W; }
 
 // acc[f] (+)= sum over the CTAs c that covered frequency f of slot (c + f), in
-// CTA order, of D = A1 + A2 + A2^T + diag(lo lo^T) (A1 as a compensated (sum, carry) pair).
+// CTA order, of D = A1 + A2 + A2^T + diag(lo lo^T) (A1 as a compensated (sum, carry)
+// pair, read from its upper triangle).
 __global__ void k_gram_tc_collect(const uint8_t* __restrict__ slots, int r2, int64_t nkb, int64_t G, int x3,
                                   int first, double* __restrict__ acc) {
   const int f = blockIdx.x;
@@ -380,7 +439,8 @@ __global__ void k_gram_tc_collect(const uint8_t* __restrict__ slots, int r2, int
     double v = 0.0;
     for (int64_t c = c0; c <= c1; ++c) {
       const uint8_t* slot = slots + (size_t)(c + f) * sb;
-      const float2 sc = reinterpret_cast<const float2*>(slot)[e];
+      // A1 is symmetric and only its upper triangle is summed by the epilogue
+      const float2 sc = reinterpret_cast<const float2*>(slot)[i <= j ? e : j * r2 + i];
       v += (double)sc.x + (double)sc.y;
       if (x3) {
         const float* a2 = reinterpret_cast<const float*>(slot + (size_t)r2 * r2 * 8);
@@ -435,13 +495,17 @@ cudaError_t launch_gram_tc_t(const spod_plan_s& p, const GramTcArgs& a, int grid
 
 template <bool X3>
 cudaError_t launch_gram_tc_x(const spod_plan_s& p, const GramTcArgs& a, int grid, size_t smem, cudaStream_t s) {
-  const int hc = a.np / 2;                 // columns per epilogue thread, a multiple of 8
-  if (hc <= 16) return launch_gram_tc_t<X3, 16>(p, a, grid, smem, s);
-  if (hc <= 24) return launch_gram_tc_t<X3, 24>(p, a, grid, smem, s);
-  if (hc <= 32) return launch_gram_tc_t<X3, 32>(p, a, grid, smem, s);
-  if (hc <= 40) return launch_gram_tc_t<X3, 40>(p, a, grid, smem, s);
-  if (hc <= 48) return launch_gram_tc_t<X3, 48>(p, a, grid, smem, s);
-  return launch_gram_tc_t<X3, 64>(p, a, grid, smem, s);
+  switch (a.np / 2) {                      // columns per epilogue warp (np is a multiple of 16)
+    case 8: return launch_gram_tc_t<X3, 8>(p, a, grid, smem, s);
+    case 16: return launch_gram_tc_t<X3, 16>(p, a, grid, smem, s);
+    case 24: return launch_gram_tc_t<X3, 24>(p, a, grid, smem, s);
+    case 32: return launch_gram_tc_t<X3, 32>(p, a, grid, smem, s);
+    case 40: return launch_gram_tc_t<X3, 40>(p, a, grid, smem, s);
+    case 48: return launch_gram_tc_t<X3, 48>(p, a, grid, smem, s);
+    case 56: return launch_gram_tc_t<X3, 56>(p, a, grid, smem, s);
+    case 64: return launch_gram_tc_t<X3, 64>(p, a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -468,12 +532,16 @@ cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool firs
   a.r2 = 2 * p.nb;
   a.np = (2 * p.nb + 15) / 16 * 16;
   a.nf = p.nf;
-  a.flush = p.gram_flush > 0 ? p.gram_flush : 4;
+  a.flush = p.gram_flush > 0 ? p.gram_flush : 1;
   a.box_bytes = (uint32_t)a.np * 128u;
+  // A1 buffers: as many as the 512 tensor-memory columns hold beside the two
+  // A2 buffers (np = 80 for nb = 38: four), so that short A1 runs are drained
+  // while the next ones accumulate
+  a.nacc = std::max(2, std::min(kMaxAcc, ((int)kTmemCols - 2 * a.np) / a.np));
+  a.stall0 = p.wait_selftest ? 1 : 0;
   a.nblk = (mcount + 63) / 64;
   a.nkb = (a.nblk + kKpb - 1) / kKpb;
   a.nitems = a.nkb * p.nf;
-  a.flush = std::max(1, a.flush / kKpb);  // the flush interval is given in 64-point blocks
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device);
   a.nst = kMaxStages;

@@ -41,6 +41,7 @@ struct ModesTcArgs {
   int64_t mcount, m0, M;                  // M: row stride of Phi in points
   int64_t phioff;                          // point of Phi's first column (tiled output)
   int64_t ntp;                             // 128-point tiles per frequency
+  int64_t qtile0;                          // first 128-point tile of the call inside the Qhat chunk
   int64_t nitems;                          // (f1 - f0) * ntp
   int f0;                                  // first frequency of the call's range
   uint32_t box_bytes;                      // one Qhat TMA box: np rows x 128 bytes
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
       const uint32_t fb = smem_u32(&hdr->full[s]);
       mbar_arrive_expect_tx(fb, stage_bytes);
       uint8_t* st = stages + (size_t)s * stage_bytes;
-      const int kb = 2 * tp;
+      const int kb = 2 * (tp + (int)a.qtile0);
       // one copy per operand: the tile's two 64-point blocks side by side
       tma_load_4d(smem_u32(st), &map_hi, 0, 0, f, kb, fb);
       if (X3) tma_load_4d(smem_u32(st + 2 * a.box_bytes), &map_lo, 0, 0, f, kb, fb);
@@ -262,7 +263,9 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
       const int f = cu.f, tp = cu.tp;
       const int acc = i & 1;
-      if (!mbar_wait(smem_u32(&hdr->accfull[acc]), (i >> 1) & 1, abort_flag, gflags)) break;
+      // one decision per warp: the tcgen05.ld below must be executed by the whole warp
+      const bool got = mbar_wait(smem_u32(&hdr->accfull[acc]), (i >> 1) & 1, abort_flag, gflags);
+      if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 128u + (uint32_t)(half * hcols);
       float v[64];
@@ -324,7 +327,9 @@ cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s) 
 }
 
 cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, bool adjoint, int f0, int f1) {
+                                  cudaStream_t s, bool adjoint, int f0, int f1, int64_t qoff, int64_t out_ld,
+                                  int64_t out_off) {
+  if (qoff % 128 != 0) return cudaErrorInvalidValue;
   if (f1 < 0) f1 = p.nf;
   if (f0 < 0 || f1 > p.nf || f0 >= f1) return cudaErrorInvalidValue;
   const float* scale = static_cast<const float*>(adjoint ? p.d_sqrtW : p.d_rsqrtW);
@@ -336,9 +341,10 @@ cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcou
   a.nf = p.nf;
   a.mcount = mcount;
   a.m0 = m0;
-  a.M = (p.phi_ld && !adjoint) ? p.phi_ld : p.M;
-  a.phioff = adjoint ? 0 : p.phi_off;
+  a.M = out_ld ? out_ld : (p.phi_ld && !adjoint) ? p.phi_ld : p.M;
+  a.phioff = out_ld ? out_off : adjoint ? 0 : p.phi_off;
   a.ntp = (mcount + 127) / 128;
+  a.qtile0 = qoff / 128;
   a.nitems = a.ntp * (f1 - f0);
   a.f0 = f0;
   a.box_bytes = (uint32_t)a.np * 128u;

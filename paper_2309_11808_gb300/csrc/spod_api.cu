@@ -416,6 +416,13 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
   const size_t o_bimg = p->tensor ? carve(modes_image_bytes(*p)) : 0;
   const size_t o_wc = carve(2 * R * (size_t)nf);
+  // R_f of the adjoint, one column sub-chunk at a time: at most 512 MiB (real data only)
+  if (!p->cplx) {
+    const size_t rpp = 2 * R * (size_t)nf * nb;
+    const int64_t want = std::max<int64_t>(128, (int64_t)(((size_t)512 << 20) / rpp) / 128 * 128);
+    p->radj_points = std::min<int64_t>((chunk + 127) / 128 * 128, want);
+  }
+  const size_t o_radj = p->radj_points ? carve(2 * R * (size_t)nf * nb * (size_t)p->radj_points) : 0;
   const size_t o_qhat = carve(per_point * (size_t)chunk);
   p->ws.bytes = off;
   {
@@ -448,6 +455,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_bmat = b + o_bmat;
   if (p->tensor) p->d_bimg = b + o_bimg;
   p->d_wc = b + o_wc;
+  if (p->radj_points) p->d_radj = b + o_radj;
   p->d_qhat = b + o_qhat;
   if (d->precision == SPOD_PREC_BF16X3)
     p->d_qlo = b + o_qhat + (size_t)p->nf * 2 * p->nb * 2 * (size_t)chunk;
@@ -531,7 +539,6 @@ spod_status spod_plan_destroy(spod_plan_t p) {
     if (p->d_xstage) cudaFree(p->d_xstage);
     if (p->d_phistage) cudaFree(p->d_phistage);
     if (p->d_gradlam) cudaFree(p->d_gradlam);
-    if (p->d_radj) cudaFree(p->d_radj);
     for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : p->ev_free) cudaEventDestroy(e);
     if (p->d_xstage2) cudaFree(p->d_xstage2);
@@ -571,10 +578,11 @@ static spod_status check_ptr(const void* ptr, const char* what) {
 // The fit over spatial chunks of at most w points (w <= chunk_points): per
 // chunk the time mean of its columns, the FFT into Qhat and the Gram partial
 // sums; then the reduction and the eigen-solve.
-static spod_status fit_impl(spod_plan_t p, const void* d_X, cudaStream_t s, int64_t w) {
+static spod_status fit_impl(spod_plan_t p, const void* d_X, cudaStream_t s, int64_t w, bool eig = true) {
   p->fitted = false;
+  p->partial = false;
   p->qhat_valid = false;
-  SPOD_CUDA(cudaMemsetAsync(p->d_flags, 0, 4 * sizeof(unsigned), s), "clear flags");
+  SPOD_CUDA(cudaMemsetAsync(p->d_flags, 0, sizeof(unsigned), s), "clear flags");   // [1] is the wait bound
   if (!p->desc.subtract_mean)
     SPOD_CUDA(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * p->M * (p->cplx ? 2 : 1), s), "zero mean");
   alignas(64) CUtensorMap xmap;
@@ -603,11 +611,12 @@ static spod_status fit_impl(spod_plan_t p, const void* d_X, cudaStream_t s, int6
     if (p->tensor) SPOD_CUDA(launch_gram_tc_finish(*p, s), "gram finish kernel");
     else SPOD_CUDA(launch_gram_reduce(*p, s), "gram reduce kernel");
   }
-  {
+  if (eig) {
     Phase ph(p, SPOD_PHASE_EIG, s, 1);
     SPOD_CUDA(launch_eig_tridiag(*p, s), "eigen-solver kernel");
   }
-  p->fitted = true;
+  p->fitted = eig;
+  p->partial = !eig;
   p->qhat_valid = nchunks == 1;
   p->last_stream = s;
   return SPOD_OK;
@@ -619,6 +628,40 @@ spod_status spod_fit(spod_plan_t p, const void* d_X, void* stream) {
   DeviceGuard g(p->device);
   if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plan's device");
   return fit_impl(p, d_X, static_cast<cudaStream_t>(stream), p->chunk_points);
+}
+
+spod_status spod_fit_partial(spod_plan_t p, const void* d_X, double* d_gram, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (spod_status st = check_ptr(d_X, "d_X")) return st;
+  if (spod_status st = check_ptr(d_gram, "d_gram")) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plan's device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (spod_status st = fit_impl(p, d_X, s, p->chunk_points, false)) return st;
+  const size_t gb = 2 * sizeof(double) * (size_t)p->nf * p->nb * p->nb;
+  SPOD_CUDA(cudaMemcpyAsync(d_gram, p->d_gram, gb, cudaMemcpyDeviceToDevice, s), "copy the slab Gram");
+  return SPOD_OK;
+}
+
+spod_status spod_fit_from_grams(spod_plan_t p, const double* d_grams, int nparts, void* stream) {
+  if (spod_status st = check_plan(p)) return st;
+  if (!p->partial) return fail(SPOD_ESTATE, "spod_fit_from_grams before spod_fit_partial on this plan");
+  if (nparts < 1) return fail(SPOD_EINVAL, "nparts must be >= 1");
+  if (spod_status st = check_ptr(d_grams, "d_grams")) return st;
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(SPOD_ECUDA, "cannot select the plan's device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    Phase ph(p, SPOD_PHASE_REDUCE, s, 1);
+    SPOD_CUDA(launch_gram_sum_parts(*p, d_grams, nparts, s), "slab Gram sum kernel");
+  }
+  {
+    Phase ph(p, SPOD_PHASE_EIG, s, 1);
+    SPOD_CUDA(launch_eig_tridiag(*p, s), "eigen-solver kernel");
+  }
+  p->fitted = true;
+  p->last_stream = s;
+  return SPOD_OK;
 }
 
 spod_status spod_sync(spod_plan_t p, void* stream) {
@@ -745,16 +788,6 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
   if (adjoint_smem_bytes(*p) > 227 * 1024) return fail(SPOD_EUNSUPPORTED, "nfft too large for the adjoint kernel");
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t rb = (size_t)p->nf * p->nb * p->M * 2 * (p->f64 ? 8 : 4);
-  if (p->radj_bytes < rb) {
-    // R_f of the adjoint, kept for later calls (allocated on first use)
-    SPOD_CUDA(cudaStreamSynchronize(s), "stream synchronize");
-    if (p->d_radj) cudaFree(p->d_radj);
-    p->d_radj = nullptr;
-    p->radj_bytes = 0;
-    if (cudaMalloc(&p->d_radj, rb) != cudaSuccess) { cudaGetLastError(); return fail(SPOD_ENOMEM, "adjoint buffer"); }
-    p->radj_bytes = rb;
-  }
   Phase ph(p, SPOD_PHASE_BACKWARD, s, 0);
   SPOD_CUDA(launch_adj_gmat(*p, d_dLdlambda, s), "adjoint G kernel");
   ph.n += 1;
@@ -768,22 +801,32 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
     if (spod_status st = make_x_map(p, d_X, &xmap)) return st;
     xm = &xmap;
   }
+  // per Qhat chunk (recomputed unless the fit left it in place), per column
+  // sub-chunk of the plan's R buffer: R = W Qhat G, then the inverse DFT,
+  // overlap-add and mean projection of those columns.  R is written and read
+  // back one sub-chunk (<= 512 MiB) at a time; no device memory is allocated here.
+  const int64_t rw = p->radj_points;
   for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points) {
     const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);
     if (!p->qhat_valid) {
       if (spod_status st = run_fft_chunk(p, d_X, xm, m0, mc, s)) return st;
       ph.n += 1;
     }
-    if (p->tensor) {
-      SPOD_CUDA(launch_modes_tc_chunk(*p, m0, mc, p->nb, p->d_radj, s, true), "adjoint R kernel (tensor cores)");
+    for (int64_t s0 = m0; s0 < m0 + mc; s0 += rw) {
+      const int64_t sw = std::min<int64_t>(rw, m0 + mc - s0);
+      if (p->tensor) {
+        SPOD_CUDA(launch_modes_tc_chunk(*p, s0, sw, p->nb, p->d_radj, s, true, 0, -1, s0 - m0, rw, s0),
+                  "adjoint R kernel (tensor cores)");
+        ph.n += 1;
+      } else {
+        int nl = 0;
+        SPOD_CUDA(launch_modes_chunk(*p, s0, sw, p->nb, p->d_radj, s, &nl, true, 0, -1, s0 - m0, rw, s0),
+                  "adjoint R kernel");
+        ph.n += nl;
+      }
+      SPOD_CUDA(launch_adjoint_chunk(*p, p->d_radj, rw, s0, s0, sw, d_dX, s), "adjoint kernel");
       ph.n += 1;
-    } else {
-      int nl = 0;
-      SPOD_CUDA(launch_modes_chunk(*p, m0, mc, p->nb, p->d_radj, s, &nl, true), "adjoint R kernel");
-      ph.n += nl;
     }
-    SPOD_CUDA(launch_adjoint_chunk(*p, p->d_radj, p->M, m0, mc, d_dX, s), "adjoint kernel");
-    ph.n += 1;
   }
   p->last_stream = s;
   return SPOD_OK;
@@ -1012,7 +1055,7 @@ spod_status spod_run_host_ooc(spod_plan_t p, const void* h_X, int nmodes, void* 
   p->fitted = false;
   p->qhat_valid = false;
   p->x_ld = w;
-  ck(cudaMemsetAsync(p->d_flags, 0, 4 * sizeof(unsigned), s), "clear flags");
+  ck(cudaMemsetAsync(p->d_flags, 0, sizeof(unsigned), s), "clear flags");      // [1] is the wait bound
   if (!p->desc.subtract_mean) ck(cudaMemsetAsync(p->d_mu, 0, sizeof(double) * M * (p->cplx ? 2 : 1), s), "zero mean");
   int use = 0;
   for (int64_t c = 0; c < ntile && st == SPOD_OK; ++c, ++use) {
@@ -1035,7 +1078,10 @@ spod_status spod_run_host_ooc(spod_plan_t p, const void* h_X, int nmodes, void* 
   if (p->tensor) ck(launch_gram_tc_finish(*p, s), "gram finish kernel");
   else ck(launch_gram_reduce(*p, s), "gram reduce kernel");
   ck(launch_eig_tridiag(*p, s), "eigen-solver kernel");
-  if (st == SPOD_OK) p->fitted = true;
+  if (st == SPOD_OK) {
+    p->fitted = true;
+    p->partial = false;
+  }
   if (h_lambda)
     ck(cudaMemcpyAsync(h_lambda, p->d_lam, sizeof(double) * (size_t)p->nf * p->nb, cudaMemcpyDeviceToHost, s),
        "copy lambda to host");
@@ -1135,6 +1181,9 @@ spod_status spod_plan_get_tuning(spod_plan_t p, spod_tuning* t) {
   t->gram_splits_max = p->gram_splits_max;
   t->gram_flush_blocks = p->gram_flush;
   t->modes_ctas = p->modes_ctas;
+  t->eig_max_iter = p->eig_max_iter;
+  t->wait_timeout_us = p->wait_timeout_us;
+  t->wait_selftest = p->wait_selftest;
   return SPOD_OK;
 }
 
@@ -1145,9 +1194,21 @@ spod_status spod_plan_set_tuning(spod_plan_t p, const spod_tuning* t) {
     return fail(SPOD_EINVAL, "gram_splits must be in 1..gram_splits_max");
   if (t->gram_flush_blocks < 0 || t->gram_flush_blocks > 64) return fail(SPOD_EINVAL, "gram_flush_blocks must be in 1..64");
   if (t->modes_ctas < 0 || t->modes_ctas > 4096) return fail(SPOD_EINVAL, "modes_ctas must be in 0..4096");
+  if (t->eig_max_iter < 0 || t->eig_max_iter > 1000) return fail(SPOD_EINVAL, "eig_max_iter must be in 0..1000");
+  if (t->wait_timeout_us < 0 || t->wait_timeout_us > 4000000)
+    return fail(SPOD_EINVAL, "wait_timeout_us must be in 0..4000000");
+  if (t->wait_selftest < 0 || t->wait_selftest > 1) return fail(SPOD_EINVAL, "wait_selftest must be 0 or 1");
+  if (t->wait_timeout_us != p->wait_timeout_us) {
+    DeviceGuard g(p->device);
+    const unsigned us = (unsigned)t->wait_timeout_us;
+    SPOD_CUDA(cudaMemcpy(p->d_flags + 1, &us, sizeof(us), cudaMemcpyHostToDevice), "set the wait bound");
+    p->wait_timeout_us = t->wait_timeout_us;
+  }
   if (t->gram_splits) p->gram_splits = t->gram_splits;
   if (t->gram_flush_blocks) p->gram_flush = t->gram_flush_blocks;
   p->modes_ctas = t->modes_ctas;
+  p->eig_max_iter = t->eig_max_iter;
+  p->wait_selftest = t->wait_selftest;
   ++p->version;
   return SPOD_OK;
 }

@@ -71,8 +71,11 @@ struct spod_plan_s {
   int64_t chunk_points = 0;   // points per chunk (multiple of the FFT tile)
   int gram_splits = 1;        // CTAs per frequency per chunk in the Gram kernel
   int gram_splits_max = 1;    // partial-Gram slots allocated
-  int gram_flush = 4;         // tensor-core Gram: blocks per FP32 accumulation group
+  int gram_flush = 1;         // tensor-core Gram: 64-point blocks per tensor-memory accumulation run
   int modes_ctas = 0;         // tensor-core modes: CTAs per frequency (0 = automatic)
+  int eig_max_iter = 0;       // QL iterations per eigenvalue (0 = the solver's default)
+  int wait_timeout_us = 0;    // bound of every device wait, in microseconds (0 = 2 s); mirrored in d_flags[1]
+  int wait_selftest = 0;      // tensor-core Gram leaves its first stage unissued (the bounded-wait self-test)
   int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
   bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
   bool cplx = false;          // complex input: two-sided spectrum, complex mean
@@ -116,11 +119,12 @@ struct spod_plan_s {
   void* d_bimg = nullptr;          // tensor path: per-frequency BF16 B images of the mode GEMM
   void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa), or G_f
   void* d_wc = nullptr;            // [nf] complex compute type: c sum_n w_n e^{+2 pi i f n / nfft}
-  void* d_radj = nullptr;          // [nf][nb][M] complex compute type: R_f of the adjoint (allocated on first use)
-  size_t radj_bytes = 0;
-  unsigned* d_flags = nullptr;     // [4]
+  void* d_radj = nullptr;          // [nf][nb][radj_points] complex compute type: R_f of the adjoint, one column sub-chunk
+  int64_t radj_points = 0;         // points per adjoint sub-chunk (a multiple of 128; 0: no adjoint, complex data)
+  unsigned* d_flags = nullptr;     // [4]: [0] condition bits (cleared per fit), [1] wait bound in us
 
   bool fitted = false;
+  bool partial = false;            // spod_fit_partial ran: the Gram of this plan's slab is in d_gram, not decomposed
   bool qhat_valid = false;         // d_qhat holds the fit's Qhat for all points (single chunk)
   cudaStream_t last_stream = nullptr;
 
@@ -158,20 +162,27 @@ cudaError_t launch_fft_chunk(const spod_plan_s& p, const void* d_X, int64_t m0, 
                              cudaStream_t s);
 cudaError_t launch_gram_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
 cudaError_t launch_gram_reduce(const spod_plan_s& p, cudaStream_t s);
+// Part-order sum of slab Grams [nparts][nf][nb][nb] (complex FP64) into the plan's Gram.
+cudaError_t launch_gram_sum_parts(const spod_plan_s& p, const double* parts, int nparts, cudaStream_t s);
 cudaError_t launch_eig(const spod_plan_s& p, cudaStream_t s);
 cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s);
 // Modes of the points [m0, m0 + mcount) at the frequencies [f0, f1) (f1 < 0: all).
+// qoff: the points' first column inside the plan's Qhat chunk; out_ld / out_off
+// (when out_ld > 0): row stride and first point of the output (the adjoint's R
+// sub-chunks), else the plan's Phi view.
 cudaError_t launch_modes_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes,
                                void* d_Phi, cudaStream_t s, int* nlaunch, bool adjoint = false, int f0 = 0,
-                               int f1 = -1);
+                               int f1 = -1, int64_t qoff = 0, int64_t out_ld = 0, int64_t out_off = 0);
 cudaError_t launch_adj_gmat(const spod_plan_s& p, const double* d_g, cudaStream_t s);
-cudaError_t launch_adjoint_chunk(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t m0, int64_t mcount,
-                                 void* d_dX, cudaStream_t s);
+// dL/dX of the points [m0, m0 + mcount) from R held as [nf][nb][rs] starting at point roff.
+cudaError_t launch_adjoint_chunk(const spod_plan_s& p, const void* d_R, int64_t rs, int64_t roff, int64_t m0,
+                                 int64_t mcount, void* d_dX, cudaStream_t s);
 size_t adjoint_smem_bytes(const spod_plan_s& p);
 
 cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s);
 cudaError_t launch_modes_tc_chunk(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
-                                  cudaStream_t s, bool adjoint = false, int f0 = 0, int f1 = -1);
+                                  cudaStream_t s, bool adjoint = false, int f0 = 0, int f1 = -1, int64_t qoff = 0,
+                                  int64_t out_ld = 0, int64_t out_off = 0);
 size_t gram_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_tc_smem_bytes(const spod_plan_s& p);
 size_t modes_image_bytes(const spod_plan_s& p);

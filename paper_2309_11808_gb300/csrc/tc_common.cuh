@@ -2,10 +2,12 @@
 // tensor loads, tensor-memory allocation, tcgen05.mma (kind::f16, BF16 inputs,
 // FP32 accumulation in TMEM) and tcgen05.ld.
 //
-// Every wait is bounded: a wait that has not completed after kWaitNs of
+// Every wait is bounded: a wait that has not completed after the plan's wait
+// bound (gflags[1] microseconds, set by spod_plan_set_tuning; 0 = kWaitNs) of
 // %globaltimer time raises the CTA's abort flag and FLAG_TIMEOUT in the
 // plan's device flags and returns false, so that no kernel of this library
-// can spin forever.
+// can spin forever.  The drains that let copies and MMAs already in flight
+// land before a CTA exits always use kWaitNs.
 #pragma once
 
 #include <cuda.h>
@@ -53,15 +55,49 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps at most ~hint_ns
+// before the test is answered (without a hint the time is the system's, and a
+// short bound would never be checked before the phase completes).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// The plan's wait bound in ns (read on the slow path of a wait only).
+__device__ __forceinline__ uint64_t wait_bound_ns(const unsigned* gflags) {
+  const unsigned us = reinterpret_cast<const volatile unsigned*>(gflags)[1];
+  return us ? (uint64_t)us * 1000ull : kWaitNs;
+}
+
 // Bounded wait for the phase with the given parity to complete.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned* gflags) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
+  // most waits end within a microsecond: only a longer one reads the bound
+  if (mbar_try_wait_hint(bar, parity, 1000u)) return true;
+  const uint64_t lim = wait_bound_ns(gflags);
+  const uint32_t hint = (uint32_t)(lim < 1000000ull ? lim : 1000000ull);    // at most 1 ms asleep per test
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_hint(bar, parity, hint)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitNs) {
+    if (globaltimer() - t0 > lim) {
       *abort_flag = 1;
       atomicOr(gflags, FLAG_TIMEOUT);
       return false;

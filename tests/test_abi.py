@@ -63,6 +63,9 @@ def test_struct_layout_matches_c(tmp_path):
     prog = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){"]
     prog.append('printf("desc %zu\\n", sizeof(spod_plan_desc));')
     prog.append('printf("info %zu\\n", sizeof(spod_plan_info));')
+    prog.append('printf("tun %zu\\n", sizeof(spod_tuning));')
+    for f, _ in _lib.spod_tuning._fields_:
+        prog.append(f'printf("t.{f} %zu\\n", offsetof(spod_tuning, {f}));')
     for f in fields_desc:
         prog.append(f'printf("d.{f} %zu\\n", offsetof(spod_plan_desc, {f}));')
     for f in fields_info:
@@ -79,6 +82,9 @@ def test_struct_layout_matches_c(tmp_path):
         assert int(out[f"d.{f}"]) == getattr(_lib.spod_plan_desc, f).offset, f
     for f in fields_info:
         assert int(out[f"i.{f}"]) == getattr(_lib.spod_plan_info, f).offset, f
+    assert int(out["tun"]) == ctypes.sizeof(_lib.spod_tuning)
+    for f, _ in _lib.spod_tuning._fields_:
+        assert int(out[f"t.{f}"]) == getattr(_lib.spod_tuning, f).offset, f
 
 
 def test_argument_validation_on_host(L):
@@ -126,3 +132,5 @@ def test_argument_validation_on_host(L):
     assert L.spod_profile_enable(None, 1) == E
     assert L.spod_profile_read(None, None, None) == E
     assert L.spod_fit_batch(None, None, 1, None) == E
+    assert L.spod_fit_partial(None, None, None, None) == E
+    assert L.spod_fit_from_grams(None, None, 1, None) == E

@@ -131,3 +131,42 @@ def test_backward_before_fit():
         _lib.spod_backward(sp.handle, g, X, torch.empty_like(X))
     assert e.value.status == _lib.SPOD_ESTATE
     sp.close()
+
+
+@cuda
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5)])
+def test_backward_at_the_differentiation_size_sampled(prec, tol):
+    # the differentiation workload at its full size: 256 x 128 grid, 2 variables,
+    # nt = 4096, nfft = 256 (nb = 31), cos-latitude weights, loss = sum over
+    # bins 5..40 of lambda_1 + lambda_2.  The oracle forms the whole Gram over
+    # spatial chunks (numpy FFT step), its eigenvectors, and the gradient of
+    # 1024 sampled columns (a column's gradient depends on the data only
+    # through that column and the eigenvectors)
+    wl = diff_like(seed=2, dtype=torch.float32, device=DEV)
+    X = wl.X
+    M = X.shape[1]
+    sp = SPOD(wl.npoints, 2, wl.nt, wl.nfft, wl.noverlap, dtype=torch.float32, precision=prec, weights=wl.W)
+    g = loss_weights(sp.nf, sp.nb, range(5, 41))
+    sp.fit(X)
+    dX = torch.empty(X.shape, dtype=torch.float32, device=DEV)
+    _lib.spod_backward(sp.handle, torch.from_numpy(g).to(DEV), X, dX)
+    cols = np.unique(np.linspace(0, M - 1, 1024).round().astype(np.int64))
+    tc = torch.from_numpy(cols).to(DEV)
+    got = dX[:, tc].double().cpu().numpy()
+    lam = sp.eigs()
+    sp.close()
+    W = wl.W.numpy()
+    d = O.Desc(nt=wl.nt, M=M, nfft=wl.nfft, noverlap=wl.noverlap, weights=W)
+    G = np.zeros((d.nf, d.nb, d.nb), dtype=np.complex128)
+    for m0 in range(0, M, 8192):
+        xc = X[:, m0:m0 + 8192].double().cpu().numpy()
+        Q = O.block_dft(xc, d.nfft, d.noverlap, d.w(), O.time_mean(xc), method="fft")
+        G += O.gram(Q, W[m0:m0 + 8192], d.norm)
+    lam_ref, Psi, _, conv = O.jacobi_eigh(G)
+    assert np.all(conv)
+    ref = O.grad_columns(X[:, tc].double().cpu().numpy(), d, g, Psi, W[cols])
+    err = rel(got, ref)
+    print(prec, "differentiation size: sampled-gradient rel err %.3e, eigenvalues of the loss bins %.3e"
+          % (err, float(np.abs(lam[5:41, :2] - lam_ref[5:41, :2]).max() / lam_ref[5:41, :2].min())))
+    assert err <= tol

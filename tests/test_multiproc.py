@@ -1,10 +1,15 @@
-"""The N > 1 bench path on the CPU: world-size-2 gloo ranks.
+"""The N > 1 paths on the CPU: gloo ranks, world size 2 and 3.
 
-The hot path does not shard across GPUs here (every rank runs an independent
-replica of the workload, section on multi-GPU in the design notes), so what
-is tested is the host-side logic around it: the max-over-ranks job time and
-the torchrun launch of the reference arm (rank 0 prints the single JSON line,
-the other ranks exit 0).
+Under torchrun the bench shards the domain into spatial slabs, one per rank
+(the paper's decomposition, Sec. 3.1): each rank's library plan forms its
+slab's part of every Gram, the parts are all-gathered in rank order, and
+every rank's plan sums them in that order and solves the same eigenproblems.
+The library calls need a GPU and are tested on one GPU (two slab plans); here
+the host side is tested: the rank-ordered gather of the parts, the
+max-over-ranks job time, the torchrun launch of the reference arm (rank 0
+prints the single JSON line, the other ranks exit 0), and the whole
+decomposition carried out with the oracle on gloo ranks against the
+single-process fit.
 """
 import json
 import os
@@ -46,10 +51,37 @@ def test_max_over_ranks_gloo(tmp_path):
     assert vals == [2.5, 2.5]
 
 
+def _gather_main(rank, world, port, outdir):
+    import numpy as np
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+    part = torch.arange(24, dtype=torch.float64).reshape(3, 2, 2, 2) + 100.0 * rank
+    parts = torch.empty((world, 3, 2, 2, 2), dtype=torch.float64)
+    bench.gather_slab_grams(part, parts)
+    np.save(os.path.join(outdir, f"g{rank}.npy"), parts.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_gram_gather_is_in_rank_order_on_every_rank(tmp_path, world):
+    import numpy as np
+    mp.spawn(_gather_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    got = [np.load(tmp_path / f"g{r}.npy") for r in range(world)]
+    base = np.arange(24, dtype=np.float64).reshape(3, 2, 2, 2)
+    for g in got:
+        assert np.array_equal(g, got[0])
+        for r in range(world):
+            assert np.array_equal(g[r], base + 100.0 * r)
+
+
 def test_reference_arm_under_torchrun_two_ranks():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--small"]
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="2")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -58,6 +90,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert "columns" in d["config"]["sample"] and d["cpu_baseline"]["sample"] == d["config"]["sample"]
 
 
 # ---------------------------------------------------------------- slab partition

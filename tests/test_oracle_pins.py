@@ -318,6 +318,25 @@ def test_gradient_matches_finite_differences():
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
 
 
+def test_gradient_of_sampled_columns_equals_the_whole_gradient():
+    # the gradient restricted to a few columns (their own Qhat, the whole
+    # fit's eigenvectors) equals those columns of the whole-array gradient,
+    # which is pinned against finite differences above
+    rng = _rng(33)
+    nt, M, nfft = 700, 40, 64
+    W = 0.5 + rng.random(M)
+    X = rng.standard_normal((nt, M)) + 2.0 * rng.standard_normal(M)[None, :]
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=32, weights=W)
+    fit = O.spod_fit(X, d)
+    g = np.zeros((d.nf, d.nb))
+    g[3:20, :2] = 1.0
+    g[7, 4] = -0.5
+    full = O.spod_grad(X, d, g, fit)
+    cols = [0, 7, 8, 39]
+    part = O.grad_columns(X[:, cols], d, g, fit.Psi, W[cols])
+    np.testing.assert_allclose(part, full[:, cols], rtol=0, atol=1e-12 * np.abs(full).max())
+
+
 def test_gradient_homogeneity_and_shift():
     d, X, g = _grad_case(seed=1)
     fit = O.spod_fit(X, d)

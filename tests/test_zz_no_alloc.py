@@ -68,6 +68,24 @@ def test_noalloc_matches_regular_path_twice(npts, nt, nfft, nov, seed):
 
 
 @cuda
+def test_noalloc_near_the_capacity_of_the_array():
+    # nb = 256 (the largest block count a plan takes) at nf = 13: the working
+    # copies fill 13 * 32 * 256^2 bytes = 27.3 MB of the 32 MiB array
+    from paper_2309_11808_gb300 import _lib
+    gram, lam_ref, psi_ref, nf, nb = _regular_path(300, 3084, 24, 12, 3)
+    assert (nf, nb) == (13, 256)
+    d_gram = torch.from_numpy(gram.view(np.float64).copy()).to(DEV)
+    for call in range(2):
+        d_lam = torch.full((nf, nb), float("nan"), dtype=torch.float64, device=DEV)
+        d_psi = torch.full((nf, nb, nb, 2), float("nan"), dtype=torch.float64, device=DEV)
+        _lib.spod_eigh_batched_noalloc(d_gram, nf, nb, d_lam, d_psi, torch.cuda.current_stream())
+        lam = d_lam.cpu().numpy()
+        np.testing.assert_allclose(lam, lam_ref, rtol=1e-9, atol=1e-12 * np.abs(lam_ref).max(),
+                                   err_msg=f"call {call}")
+        assert np.isfinite(d_psi.cpu().numpy()).all()
+
+
+@cuda
 def test_noalloc_rejects_sizes_beyond_the_array():
     from paper_2309_11808_gb300 import SpodError, _lib
     nf, nb = 100, 200            # needs 100 * 32 * 200^2 bytes = 128 MB > 32 MiB
