@@ -554,7 +554,7 @@ def coeffs_leg(args, rank):
             "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": max(3, args.warmup),
             "config": {"workload": f"jet-shaped {nx}x{nr}x{nv}, nt={nt}, nfft={nfft}", "M": M, "nt": nt,
                        "modes_per_bin": nr_, "bins": fsel, "real_basis_vectors": K, "fit_precision": args.precision,
-                       "gemm": "cuBLAS FP32 (pedantic)"},
+                       "gemm": "library SIMT GEMM (k_gemm_simt), FP32; split over the points, parts summed in FP64"},
             "roofline": {"bound": "alu", "achieved": round(flops / (ms * 1e-3) / 1e12, 3), "peak": round(FP32_PEAK, 1),
                          "unit": "TFLOP/s", "frac": round(flops / (ms * 1e-3) / 1e12 / FP32_PEAK, 4),
                          "flops": flops},

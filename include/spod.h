@@ -301,9 +301,10 @@ spod_status spod_run_host_ooc(spod_plan_t plan, const void* h_X, int nmodes, voi
  * conjugate).  Real data with F32 input (FP32 / BF16 / BF16X3 plans) or F64
  * input (FP64 plans) only, else SPOD_EUNSUPPORTED; at most 4096 real basis
  * vectors.  A basis that is not linearly independent is reported by the
- * next spod_sync as SPOD_ENOTCONVERGED.  The two large products run as
- * cuBLAS GEMMs (FP32 or FP64 as the plan) on `stream`.  No counterpart of
- * this API shape in the paper. */
+ * next spod_sync as SPOD_ENOTCONVERGED.  The two large products run on this
+ * library's SIMT GEMM kernel (FP32 or FP64 as the plan) on `stream`, with
+ * stream-ordered scratch (cudaMallocAsync).  No counterpart of this API shape
+ * in the paper. */
 spod_status spod_coeffs(spod_plan_t plan, const void* d_X, const void* d_Phi, int nmodes, int nmodes_r, int nfreq_r,
                         const int* h_freqs, double* d_A, void* stream);
 

@@ -16,11 +16,11 @@
 // Nyquist) recovers the complex coefficient of the mode at the positive bin
 // (its conjugate bin carries conj(a)).  The reconstruction is
 //   X~ = mu + P_b^T C  (real rows [nt][M]).
-// The two large products are plain GEMMs and go to cuBLAS (FP32 or FP64 as
-// the plan); the K x K Gram of the basis, its inverse and the packing are
-// kernels of this file.
-#include <cublas_v2.h>
-
+// The two large products run on k_gemm_simt, this file's SIMT GEMM (FP32 or
+// FP64 as the plan; the product over the M points is split over CTAs and the
+// parts summed in FP64 in a fixed order), as do C = G^{-1} B and the K x K
+// Gram of the basis, its inverse and the packing.
+#include <algorithm>
 #include <vector>
 
 #include "spod_internal.cuh"
@@ -119,14 +119,6 @@ __global__ void k_spd_inverse(double* __restrict__ G, double* __restrict__ Ginv,
   }
 }
 
-// B64 = B - v 1^T (B column-major K x nt, type R).
-template <typename R>
-__global__ void k_coeff_center(const R* __restrict__ B, const double* __restrict__ v, int K, int64_t n,
-                               double* __restrict__ B64) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    B64[e] = (double)B[e] - v[e % K];
-}
-
 // d_A[q][t] (q = j * nmodes_r + k) from the real coefficients C (column-major
 // K x nt): a = c[re] (DC, Nyquist) or c[re] / 2 - i c[im] / 2.
 __global__ void k_coeff_pack(const double* __restrict__ C, const int2* __restrict__ qrows, int nq, int K,
@@ -161,6 +153,91 @@ template <typename R>
 __global__ void k_fill_mean(const double* __restrict__ mu, int64_t M, int64_t n, R* __restrict__ X) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     X[e] = (R)mu[e % M];
+}
+
+// D(i, j) = beta D(i, j) + sum_k A(i, k) B(k, j) over the split's range of k,
+// every operand given by element strides: A(i, k) = A[i sai + k sak],
+// B(k, j) = B[k sbk + j sbj], D(i, j) = D[i sdi + j sdj].  64 x 64 tiles of D,
+// 256 threads with 4 x 4 results each, k in steps of 16 staged in shared
+// memory (loads along whichever index is contiguous).  Split z covers
+// k in [z kper, (z + 1) kper) and writes D + z dsplit.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gemm_simt(int ni, int nj, int64_t nk, const R* __restrict__ A, int64_t sai,
+                                                   int64_t sak, const R* __restrict__ B, int64_t sbk, int64_t sbj,
+                                                   R* __restrict__ D, int64_t sdi, int64_t sdj, int64_t dsplit,
+                                                   R beta, int64_t kper) {
+  constexpr int TI = 64, TJ = 64, TK = 16;
+  __shared__ R As[TK][TI + 4];
+  __shared__ R Bs[TK][TJ + 4];
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int64_t k0 = (int64_t)blockIdx.z * kper;
+  const int64_t k1 = k0 + kper < nk ? k0 + kper : nk;
+  R* Dz = D + (int64_t)blockIdx.z * dsplit;
+  const int tid = threadIdx.x;
+  // the output index that is contiguous in D varies fastest across threads
+  const bool jfast = sdj == 1;
+  const int ti = (jfast ? tid / 16 : tid % 16) * 4, tj = (jfast ? tid % 16 : tid / 16) * 4;
+  R acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = (R)0;
+  for (int64_t kb = k0; kb < k1; kb += TK) {
+    for (int e = tid; e < TI * TK; e += 256) {
+      const int kk = sak == 1 ? e % TK : e / TI, ii = sak == 1 ? e / TK : e % TI;
+      const int gi = i0 + ii;
+      const int64_t gk = kb + kk;
+      As[kk][ii] = (gi < ni && gk < k1) ? A[(int64_t)gi * sai + gk * sak] : (R)0;
+    }
+    for (int e = tid; e < TK * TJ; e += 256) {
+      const int kk = sbk == 1 ? e % TK : e / TJ, jj = sbk == 1 ? e / TK : e % TJ;
+      const int gj = j0 + jj;
+      const int64_t gk = kb + kk;
+      Bs[kk][jj] = (gj < nj && gk < k1) ? B[gk * sbk + (int64_t)gj * sbj] : (R)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      R a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[kk][ti + q]; b[q] = Bs[kk][tj + q]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int gi = i0 + ti + x, gj = j0 + tj + y;
+      if (gi < ni && gj < nj) {
+        R* d = Dz + (int64_t)gi * sdi + (int64_t)gj * sdj;
+        *d = beta == (R)0 ? acc[x][y] : beta * *d + acc[x][y];
+      }
+    }
+}
+
+// out[e] = sum_z parts[z][e] (FP64, z in order) - v[e % K]  (B - v 1^T, column-major K x nt)
+template <typename R>
+__global__ void k_coeff_center_parts(const R* __restrict__ parts, int nsplit, const double* __restrict__ v, int K,
+                                     int64_t n, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < nsplit; ++z) acc += (double)parts[(int64_t)z * n + e];
+    out[e] = acc - v[e % K];
+  }
+}
+
+template <typename R>
+cudaError_t gemm(int ni, int nj, int64_t nk, const R* A, int64_t sai, int64_t sak, const R* B, int64_t sbk,
+                 int64_t sbj, R* D, int64_t sdi, int64_t sdj, R beta, int nsplit, int64_t dsplit, cudaStream_t s) {
+  const int64_t kper = ((nk + nsplit - 1) / nsplit + 15) / 16 * 16;
+  dim3 grid((unsigned)((ni + 63) / 64), (unsigned)((nj + 63) / 64), (unsigned)nsplit);
+  k_gemm_simt<R><<<grid, 256, 0, s>>>(ni, nj, nk, A, sai, sak, B, sbk, sbj, D, sdi, sdj, dsplit, beta, kper);
+  return cudaGetLastError();
 }
 
 bool self_conjugate(int f, int nfft) { return f == 0 || (nfft % 2 == 0 && f == nfft / 2); }
@@ -200,32 +277,6 @@ struct Scratch {
   }
 };
 
-cudaError_t cublas_err(cublasStatus_t st) { return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown; }
-
-cublasHandle_t handle_of(spod_plan_s& p, cudaStream_t s, cudaError_t* e) {
-  if (!p.blas) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-      *e = cudaErrorUnknown;
-      return nullptr;
-    }
-    cublasSetMathMode(h, CUBLAS_PEDANTIC_MATH);      // FP32 stays FP32 (no TF32)
-    p.blas = h;
-  }
-  cublasHandle_t h = static_cast<cublasHandle_t>(p.blas);
-  if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) *e = cudaErrorUnknown;
-  return h;
-}
-
-template <typename R>
-cudaError_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, R alpha,
-                 const R* A, int lda, const R* B, int ldb, R beta, R* C, int ldc) {
-  if constexpr (sizeof(R) == 8)
-    return cublas_err(cublasDgemm(h, ta, tb, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc));
-  else
-    return cublas_err(cublasSgemm(h, ta, tb, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc));
-}
-
 // P_w, P_b (K x M, type R) of the selected modes.
 template <typename R>
 cudaError_t build_basis(const spod_plan_s& p, const void* d_Phi, int nmodes, const std::vector<BasisRow>& rows,
@@ -257,7 +308,10 @@ cudaError_t coeffs_t(spod_plan_s& p, const void* d_X, const void* d_Phi, int nmo
   R *Pw = nullptr, *Pb = nullptr;
   cudaError_t e = build_basis<R>(p, d_Phi, nmodes, rows, sc, &Pw, &Pb, s);
   if (e != cudaSuccess) return e;
-  R* B = static_cast<R*>(sc.get(sizeof(R) * (size_t)K * nt));
+  // the product over the M points, split so that the grid covers the GPU
+  const int tiles = ((K + 63) / 64) * (int)((nt + 63) / 64);
+  const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({64, (4 * p.num_sms + tiles - 1) / tiles, M / 1024}));
+  R* B = static_cast<R*>(sc.get(sizeof(R) * (size_t)K * nt * nsplit));
   double* B64 = static_cast<double*>(sc.get(sizeof(double) * (size_t)K * nt));
   double* C = static_cast<double*>(sc.get(sizeof(double) * (size_t)K * nt));
   double* G = static_cast<double*>(sc.get(sizeof(double) * (size_t)K * K));
@@ -272,15 +326,13 @@ cudaError_t coeffs_t(spod_plan_s& p, const void* d_X, const void* d_Phi, int nmo
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_spd_inverse<<<1, 1024, sizeof(double) * K, s>>>(G, Ginv, K, p.d_flags);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // B = P_w X^T (column-major K x nt): X is column-major M x nt
-  cublasHandle_t h = handle_of(p, s, &e);
+  // B = P_w X^T (column-major K x nt; X[t][m]), per split of the points, then B - v 1^T in FP64
+  e = gemm<R>(K, (int)nt, M, Pw, M, 1, static_cast<const R*>(d_X), 1, M, B, 1, K, (R)0, nsplit, (int64_t)K * nt, s);
   if (e != cudaSuccess) return e;
-  e = gemm<R>(h, CUBLAS_OP_T, CUBLAS_OP_N, K, (int)nt, (int)M, (R)1, Pw, (int)M, static_cast<const R*>(d_X), (int)M,
-              (R)0, B, K);
-  if (e != cudaSuccess) return e;
-  k_coeff_center<R><<<1024, 256, 0, s>>>(B, v, K, (int64_t)K * nt, B64);
+  k_coeff_center_parts<R><<<1024, 256, 0, s>>>(B, nsplit, v, K, (int64_t)K * nt, B64);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = gemm<double>(h, CUBLAS_OP_N, CUBLAS_OP_N, K, (int)nt, K, 1.0, Ginv, K, B64, K, 0.0, C, K);
+  // C = G^{-1} (B - v 1^T)  (FP64, column-major K x nt)
+  e = gemm<double>(K, (int)nt, K, Ginv, K, 1, B64, 1, K, C, 1, K, 0.0, 1, 0, s);
   if (e != cudaSuccess) return e;
   dim3 pg((unsigned)std::min<int64_t>((nt + 255) / 256, 1024), (unsigned)qrows.size());
   k_coeff_pack<<<pg, 256, 0, s>>>(C, d_q, (int)qrows.size(), K, nt, reinterpret_cast<double2*>(d_A));
@@ -311,10 +363,8 @@ cudaError_t reconstruct_t(spod_plan_s& p, const void* d_Phi, int nmodes, int nmo
   R* X = static_cast<R*>(d_Xrec);
   k_fill_mean<R><<<2048, 256, 0, s>>>(p.d_mu, M, M * nt, X);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  cublasHandle_t h = handle_of(p, s, &e);
-  if (e != cudaSuccess) return e;
-  // X (column-major M x nt) += P_b^T C: P_b is column-major M x K
-  return gemm<R>(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)M, (int)nt, K, (R)1, Pb, (int)M, C, K, (R)1, X, (int)M);
+  // X[t][m] += sum_r C[t][r] P_b[r][m]  (C column-major K x nt, P_b rows of M)
+  return gemm<R>((int)nt, (int)M, K, C, K, 1, Pb, M, 1, X, M, 1, (R)1, 1, 0, s);
 }
 
 }  // namespace
@@ -335,11 +385,6 @@ cudaError_t launch_reconstruct(spod_plan_s& p, const void* d_Phi, int nmodes, in
                                const int* h_freqs, const double* d_A, void* d_Xrec, cudaStream_t s) {
   return p.f64 ? reconstruct_t<double>(p, d_Phi, nmodes, nmodes_r, nsel, h_freqs, d_A, d_Xrec, s)
                : reconstruct_t<float>(p, d_Phi, nmodes, nmodes_r, nsel, h_freqs, d_A, d_Xrec, s);
-}
-
-void destroy_blas(spod_plan_s& p) {
-  if (p.blas) cublasDestroy(static_cast<cublasHandle_t>(p.blas));
-  p.blas = nullptr;
 }
 
 }  // namespace spod

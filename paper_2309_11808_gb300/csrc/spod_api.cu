@@ -545,7 +545,6 @@ spod_status spod_plan_destroy(spod_plan_t p) {
     if (p->d_lamstage) cudaFree(p->d_lamstage);
     if (p->d_phistage2) cudaFree(p->d_phistage2);
     for (auto e : p->host_ev) cudaEventDestroy(e);
-    destroy_blas(*p);
     if (p->h2d_stream) cudaStreamDestroy(p->h2d_stream);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
   }

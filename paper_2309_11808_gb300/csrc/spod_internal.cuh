@@ -79,7 +79,6 @@ struct spod_plan_s {
   int ring_boxr = 0;          // TMA ring FFT: rows per box (0 = ring kernel not usable)
   bool ring_ok = false;       // a TMA-fed FFT kernel (pipelined or ring) is used
   bool cplx = false;          // complex input: two-sided spectrum, complex mean
-  void* blas = nullptr;       // cuBLAS handle of the expansion-coefficient GEMMs (created on first use)
   // Views for data held in tiles (out-of-core driver): X is read as rows of
   // x_ld points starting at point x_off, Phi written as rows of phi_ld points
   // starting at point phi_off (0, 0: the full arrays, row stride M).
@@ -218,7 +217,6 @@ cudaError_t launch_coeffs(spod_plan_s& p, const void* d_X, const void* d_Phi, in
                           const int* h_freqs, double* d_A, cudaStream_t s);
 cudaError_t launch_reconstruct(spod_plan_s& p, const void* d_Phi, int nmodes, int nmodes_r, int nsel,
                                const int* h_freqs, const double* d_A, void* d_Xrec, cudaStream_t s);
-void destroy_blas(spod_plan_s& p);
 // strided tile copy (k_tile_copy.cu)
 // rows x width bytes from src (pitch spitch) to dst (pitch dpitch); bytes
 // [width, dwidth) of each destination row are set to zero
