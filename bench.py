@@ -8,7 +8,7 @@ Metric: snapshot-GB/s = nt * M * sizeof(element) / (time per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3]
                     [--impl native|reference] [--no-compare] [--no-e2e] [--no-cpu]
-    python bench.py --complex | --coeffs | --ooc | --backward     (separate measurements)
+    python bench.py --complex | --coeffs | --ooc | --backward | --batch     (separate measurements)
 
 The default precision is bf16x3 (BF16 tensor-core Gram and modes with split
 products); the same input is then also run through the plain FP32 GPU form
@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--backward", action="store_true",
                     help="time spod_backward (the adjoint of the eigenvalues) after a fit on the headline grid; "
                          "a separate measurement")
+    ap.add_argument("--batch", action="store_true",
+                    help="time spod_fit_batch on the six ERA5-shaped one-year datasets at full size (162 GB of "
+                         "FP32 input resident in HBM), one graph launch per step, bf16x3 and FP32; a separate "
+                         "measurement")
     ap.add_argument("--ooc", action="store_true",
                     help="time the out-of-core run (spod_run_host_ooc: X and Phi in pinned host memory, column "
                          "tiles over the host link) on the headline grid; a separate measurement")
@@ -186,6 +190,8 @@ def main():
         return ooc_leg(args, rank)
     if args.backward:
         return backward_leg(args, rank)
+    if args.batch:
+        return batch_leg(args, rank)
 
     import __graft_entry__ as g
     from paper_2309_11808_gb300 import _lib
@@ -482,6 +488,7 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, e
 # Absent entries: no capture of the current kernel version.
 TRAFFIC = {
     ("fft", "bf16x3"): int((491.146752 + 910.630400) * 1e6 * 32),    # k_fft_pipe<float, 1, 32, 512> (L2 prefetch)
+    ("gram", "bf16x3"): int((960.439296 + 19.947264) * 1e6 * 32),    # k_gram_tc<1, 40> (one-block runs, upper-triangle drains)
     ("modes", "bf16x3"): int((976.941568 + 907.403264) * 1e6 * 32),  # k_modes_tc<1> (Phi view)
     ("gram", "fp32"): int((961.233 + 25.105920) * 1e6 * 32),         # k_gram_simt<float>
     # k_modes_simt changed (frequency range, Phi view) after its capture: no entry
@@ -634,6 +641,78 @@ def backward_leg(args, rank):
     line = {"metric": "SPOD adjoint (spod_backward) ms per call", "value": runs[0]["ms_per_call"], "unit": "ms",
             "higher_is_better": False, "steps": args.steps, "warmup": max(3, args.warmup),
             "config": {"workload": runs[0]["workload"], "precision": args.precision}, "runs": runs}
+    print(json.dumps(line), flush=True)
+
+
+def batch_leg(args, rank):
+    """spod_fit_batch over the six ERA5-shaped one-year datasets (lat-lon grids
+    181 x 360, 361 x 720 (x 2), 721 x 1440 (x 3), 2 variables, nt 2920 / 4380 /
+    8760, nfft 256 / 384 / 512 / 720, cos-latitude weights): all inputs
+    resident in HBM (162 GB FP32), one CUDA-graph launch fits all six (a
+    branch per dataset); each plan's Qhat chunk is bounded so that the six
+    workspaces fit beside the inputs.  Timed with CUDA events over graph
+    launches after a capture and warm-up; the same datasets fitted one after
+    another with spod_fit for comparison.  Metric: snapshot-GB/s over the six
+    datasets (their FP32 bytes / time per launch)."""
+    import torch
+    import __graft_entry__ as g
+    from paper_2309_11808_gb300 import SPOD, _lib
+    from workloads import geo_datasets, geo_like
+    g.build()
+    dev = torch.device("cuda", 0)
+    wls = []
+    for i, ((nla, nlo), nt, nfft) in enumerate(geo_datasets()):
+        wls.append(geo_like(nla, nlo, nt, nfft, seed=60 + i, dtype=torch.float32, device=dev))
+    total = sum(w.X.numel() * 4 for w in wls)
+    st = torch.cuda.current_stream()
+    out = {}
+    for prec in ("bf16x3", "fp32"):
+        free = torch.cuda.mem_get_info()[0]
+        budget = max(1 << 30, int(free * 0.8) // 6)          # Qhat bytes per plan
+        sps = []
+        for wl in wls:
+            nb = (wl.nt - wl.noverlap) // (wl.nfft - wl.noverlap)
+            per_pt = (wl.nfft // 2 + 1) * 2 * nb * 4
+            chunk = max(64, min(wl.X.shape[1], budget // per_pt) // 64 * 64)
+            sps.append(SPOD(wl.npoints, wl.nvars, wl.nt, wl.nfft, wl.noverlap, precision=prec, weights=wl.W,
+                            chunk_points=chunk))
+        handles = [sp.handle for sp in sps]
+        Xs = [wl.X for wl in wls]
+        for _ in range(max(3, args.warmup)):
+            _lib.spod_fit_batch(handles, Xs, st)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            _lib.spod_fit_batch(handles, Xs, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        for sp in sps:
+            sp.eigs()                                          # status of every dataset
+        # the same fits one after another
+        e0.record(st)
+        for sp, X in zip(sps, Xs):
+            _lib.spod_fit(sp.handle, X, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_serial = e0.elapsed_time(e1)
+        out[prec] = {"ms_per_launch": round(ms, 2), "value": round(total / (ms * 1e-3) / 1e9, 2),
+                     "serial_ms": round(ms_serial, 2),
+                     "chunks": [int(sp.info.chunk_points) for sp in sps],
+                     "workspace_GB": round(sum(sp.info.workspace_bytes for sp in sps) / 1e9, 2)}
+        for sp in sps:
+            sp.close()
+        torch.cuda.empty_cache()
+    line = {"metric": "SPOD snapshot-GB/s over six ERA5-shaped datasets in one graph launch (fit)",
+            "value": out["bf16x3"]["value"], "unit": "GB/s", "higher_is_better": True, "steps": args.steps,
+            "warmup": max(3, args.warmup), "dtype": "bf16x3",
+            "data": "synthetic (seeded AR(1) red noise + planted annual and diurnal-bin patterns)",
+            "config": {"workload": "six one-year lat-lon records: " + ", ".join(
+                f"{nla}x{nlo}x2 nt={nt} nfft={nfft}" for (nla, nlo), nt, nfft in geo_datasets()),
+                "input_GB": round(total / 1e9, 1), "weights": "cos(latitude)"},
+            "bf16x3": out["bf16x3"], "fp32": out["fp32"],
+            "speedup_vs_fp32": round(out["fp32"]["ms_per_launch"] / out["bf16x3"]["ms_per_launch"], 3)}
     print(json.dumps(line), flush=True)
 
 

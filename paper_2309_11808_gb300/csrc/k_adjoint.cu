@@ -125,28 +125,33 @@ __global__ void __launch_bounds__(256) k_adjoint(const typename C2<R>::T* __rest
   };
 
   for (int l = 0; l < a.nb; ++l) {
-    // ---- conj of the packed Hermitian extension: conj(H_a + i H_b) for each column pair
-    for (int idx = tid; idx < N * C; idx += blockDim.x) {
+    // ---- conj of the packed Hermitian extension: conj(H_a + i H_b) for each column
+    // pair, H[f] = Rt[f] + conj Rt[(N - f) mod N] with Rt = R on the one-sided bins
+    // and 0 elsewhere.  Each R value is read once: a bin f of the one-sided range
+    // gives entry f and, for 0 < f < N - f, the mirror entry N - f (whose H is
+    // conj R[f]); the bins f with N - f < nf as well (f = 0, N/2) are their own
+    // mirrors.
+    for (int idx = tid; idx < a.nf * C; idx += blockDim.x) {
       const int f = idx / C, j = idx - f * C;
       const int fm = (f == 0) ? 0 : N - f;
-      V ha = mk<R>(0, 0), hb = mk<R>(0, 0);
+      V ra = mk<R>(0, 0), rb = mk<R>(0, 0);
       const int64_t pa = lm0 + 2 * j;       // local index (bounds)
       const int64_t ga = rm0 + 2 * j;       // column in R
-      if (f < a.nf) {
-        if (pa < a.mcount) ha = Rsp[((int64_t)f * a.nb + l) * rs + ga];
-        if (pa + 1 < a.mcount) hb = Rsp[((int64_t)f * a.nb + l) * rs + ga + 1];
-      }
-      if (fm < a.nf) {
-        V ca = mk<R>(0, 0), cb = mk<R>(0, 0);
-        if (pa < a.mcount) ca = Rsp[((int64_t)fm * a.nb + l) * rs + ga];
-        if (pa + 1 < a.mcount) cb = Rsp[((int64_t)fm * a.nb + l) * rs + ga + 1];
-        ha.x += ca.x; ha.y -= ca.y;          // + conj
-        hb.x += cb.x; hb.y -= cb.y;
-      }
+      if (pa < a.mcount) ra = Rsp[((int64_t)f * a.nb + l) * rs + ga];
+      if (pa + 1 < a.mcount) rb = Rsp[((int64_t)f * a.nb + l) * rs + ga + 1];
       // Y = (ha + i hb) / 2 ; store conj(Y)
-      const R yr = (R)0.5 * (ha.x - hb.y), yi = (R)0.5 * (ha.y + hb.x);
-      bufA[f * C + j] = mk<R>(yr, -yi);
+      auto put = [&](int e, V ha, V hb) {
+        const R yr = (R)0.5 * (ha.x - hb.y), yi = (R)0.5 * (ha.y + hb.x);
+        bufA[e * C + j] = mk<R>(yr, -yi);
+      };
+      if (fm < a.nf) {                       // f = 0 or f = N/2: H = R + conj R
+        put(f, mk<R>(ra.x + ra.x, (R)0), mk<R>(rb.x + rb.x, (R)0));
+      } else {
+        put(f, ra, rb);                                      // H[f] = R[f]
+        put(fm, mk<R>(ra.x, -ra.y), mk<R>(rb.x, -rb.y));     // H[N - f] = conj R[f]
+      }
     }
+    // (the entries written cover 0 .. N-1 once each, for even and odd N)
     __syncthreads();
     V* src = bufA;
     V* dst = bufB;

@@ -80,20 +80,24 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_gram_simt(
   const R* qf = qhat + (int64_t)f * 2 * nb * rs;
   const int nrounds = p1 > p0 ? (int)((p1 - p0 + TK - 1) / TK) : 0;
 
-  // staging: element e of a round = (plane c, row l, point k), point fastest (coalesced)
+  // staging: element e of a round = (plane c, row l, point k), point fastest
+  // (coalesced).  Element tid + j * kThreads has point k = tid % TK (fixed per
+  // thread) and staged row tid / TK + j * (kThreads / TK) < 2 RS, so its plane
+  // and row follow from one comparison (no division in the round loop).
   constexpr int kMaxPer = (2 * 64 * TK + kThreads - 1) / kThreads;   // nb <= 64
+  constexpr int kRowStep = kThreads / TK;
+  const int k_th = tid % TK, row_th = tid / TK;
   R pre[kMaxPer];
   auto fetch = [&](int r) {
     const int64_t pb = p0 + (int64_t)r * TK;
+    const bool kin = pb + k_th < p1;
+    const R* src = qf + pb + k_th;
 #pragma unroll
     for (int j = 0; j < kMaxPer; ++j) {
-      const int idx = tid + j * kThreads;
+      const int row = row_th + j * kRowStep;
+      const int c = row >= RS ? 1 : 0, l = row - c * RS;
       R v = 0;
-      if (idx < buf_elems) {
-        const int row = idx / TK, k = idx - row * TK;
-        const int c = row / RS, l = row - c * RS;
-        if (l < nb && pb + k < p1) v = qf[((int64_t)c * nb + l) * rs + pb + k];
-      }
+      if (row < 2 * RS && l < nb && kin) v = src[((int64_t)c * nb + l) * rs];
       pre[j] = v;
     }
   };
@@ -101,12 +105,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_gram_simt(
     R* st = stage + b * buf_elems;
 #pragma unroll
     for (int j = 0; j < kMaxPer; ++j) {
-      const int idx = tid + j * kThreads;
-      if (idx < buf_elems) {
-        const int row = idx / TK, k = idx - row * TK;
-        const int c = row / RS, l = row - c * RS;
-        st[c * TK * RS + k * RS + l] = pre[j];
-      }
+      const int row = row_th + j * kRowStep;
+      const int c = row >= RS ? 1 : 0, l = row - c * RS;
+      if (row < 2 * RS) st[c * TK * RS + k_th * RS + l] = pre[j];
     }
     // rows beyond the prefetched ones (nb > 64) are copied directly
     const int64_t pb = p0 + (int64_t)r * TK;

@@ -416,10 +416,11 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
   const size_t o_bimg = p->tensor ? carve(modes_image_bytes(*p)) : 0;
   const size_t o_wc = carve(2 * R * (size_t)nf);
-  // R_f of the adjoint, one column sub-chunk at a time: at most 512 MiB (real data only)
+  // R_f of the adjoint, one column sub-chunk at a time: at most 2 GiB (real data only),
+  // enough columns for several waves of the adjoint kernel's 16-point CTAs
   if (!p->cplx) {
     const size_t rpp = 2 * R * (size_t)nf * nb;
-    const int64_t want = std::max<int64_t>(128, (int64_t)(((size_t)512 << 20) / rpp) / 128 * 128);
+    const int64_t want = std::max<int64_t>(128, (int64_t)(((size_t)2 << 30) / rpp) / 128 * 128);
     p->radj_points = std::min<int64_t>((chunk + 127) / 128 * 128, want);
   }
   const size_t o_radj = p->radj_points ? carve(2 * R * (size_t)nf * nb * (size_t)p->radj_points) : 0;
@@ -803,7 +804,7 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
   // per Qhat chunk (recomputed unless the fit left it in place), per column
   // sub-chunk of the plan's R buffer: R = W Qhat G, then the inverse DFT,
   // overlap-add and mean projection of those columns.  R is written and read
-  // back one sub-chunk (<= 512 MiB) at a time; no device memory is allocated here.
+  // back one sub-chunk (<= 2 GiB) at a time; no device memory is allocated here.
   const int64_t rw = p->radj_points;
   for (int64_t m0 = 0; m0 < p->M; m0 += p->chunk_points) {
     const int64_t mc = std::min<int64_t>(p->chunk_points, p->M - m0);

@@ -109,7 +109,7 @@ def test_autograd_function_and_bf16x3():
     wl = diff_like(nx=32, ny=16, nvars=2, nt=1024, nfft=64, seed=5)
     X = wl.X.to(DEV).requires_grad_(True)
     d = O.Desc(nt=1024, M=wl.M, nfft=64, noverlap=32, weights=wl.W.numpy())
-    for prec, tol in (("fp32", 1e-5), ("bf16x3", 1e-3)):
+    for prec, tol in (("fp32", 1e-5), ("bf16x3", 1e-5)):
         sp = SPOD(wl.npoints, 2, 1024, 64, 32, precision=prec, weights=wl.W)
         lam = spod_eigs(X, sp)
         g = torch.from_numpy(loss_weights(sp.nf, sp.nb, range(5, 21))).to(DEV)

@@ -100,3 +100,48 @@ def test_autotune_keeps_results(prec):
     assert (np.abs(lam1 - lam0).max(axis=1) / lam0[:, 0]).max() <= 1e-6
     for s in sps:
         s.close()
+
+
+@cuda
+@pytest.mark.slow
+@pytest.mark.parametrize("which", [0, 1, 3])
+def test_geo_dataset_full_size_against_oracle(which):
+    # three of the six one-year records at their full size (181 x 360 x 2,
+    # nt 2920, nfft 256; 361 x 720 x 2, nt 4380, nfft 384; 721 x 1440 x 2,
+    # nt 2920, nfft 720: the three FFT code paths of the batch), bf16x3 and
+    # FP32, against the oracle's Gram at the planted annual bin and the diurnal
+    # bin (computed over spatial chunks from the DFT rows of those bins)
+    from paper_2309_11808_gb300 import SPOD
+    from workloads import geo_datasets
+    (nla, nlo), nt, nfft = geo_datasets()[which]
+    wl = geo_like(nla, nlo, nt, nfft, seed=60 + which, dtype=torch.float32, device="cuda:0")
+    X = wl.X
+    M = X.shape[1]
+    nb = (nt - nfft // 2) // (nfft // 2)
+    chunk = min(M, (8 << 30) // ((nfft // 2 + 1) * 2 * nb * 4)) // 64 * 64
+    fsel = [1, wl.meta["diurnal_bin"]]
+    lams = {}
+    for prec in ("bf16x3", "fp32"):
+        sp = SPOD(wl.npoints, 2, nt, nfft, nfft // 2, precision=prec, weights=wl.W, chunk_points=chunk)
+        sp.fit(X)
+        lams[prec] = sp.eigs()[fsel]
+        sp.close()
+    d = O.Desc(nt=nt, M=M, nfft=nfft, noverlap=nfft // 2, weights=wl.W.numpy())
+    G = O.gram_at_freqs(d, fsel, lambda a, b: X[:, a:b].contiguous().cpu().numpy(), chunk=16384)
+    lam_ref, _, _, conv = O.jacobi_eigh(G)
+    assert np.all(conv)
+    # the gate: relative where lambda_1/lambda_j <= 100; at the planted diurnal bin of
+    # the 721 x 1440 record lambda_1/lambda_j reaches 2e3..4e3 for j = 2..5, where a
+    # relative 1e-5 would need the Gram to 3e-9, below FP32's unit roundoff (Weyl:
+    # |dlambda_j| <= ||dM||_2), so those entries are gated normwise at tol / 10
+    k = min(5, d.nb)
+    cond = lam_ref[:, :1] / lam_ref[:, :k]
+    worst = {}
+    for prec, tol in (("bf16x3", 1e-5), ("fp32", 1e-4)):
+        rel = np.abs(lams[prec][:, :k] - lam_ref[:, :k]) / lam_ref[:, :k]
+        normwise = float((np.abs(lams[prec][:, :k] - lam_ref[:, :k]) / lam_ref[:, :1]).max())
+        print("geo dataset", which, prec, "bins", fsel, "rel err", np.array2string(rel, precision=2),
+              "normwise %.2e" % normwise, "lambda_1/lambda_j", np.array2string(cond, precision=1))
+        worst[prec] = (float(rel[cond <= 100].max()), normwise, tol)
+    for prec, (rel_ok, normwise, tol) in worst.items():
+        assert rel_ok <= tol and normwise <= tol / 10, (prec, rel_ok, normwise)
