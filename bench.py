@@ -68,6 +68,9 @@ def parse():
                     help="time spod_fit_batch on the six ERA5-shaped one-year datasets at full size (162 GB of "
                          "FP32 input resident in HBM), one graph launch per step, bf16x3 and FP32; a separate "
                          "measurement")
+    ap.add_argument("--mean-pass", action="store_true",
+                    help="take the time mean in a separate pass over X instead of inside the FFT pass "
+                         "(spod_plan_desc.mean_in_fft = 0), for comparison")
     ap.add_argument("--ooc", action="store_true",
                     help="time the out-of-core run (spod_run_host_ooc: X and Phi in pinned host memory, column "
                          "tiles over the host link) on the headline grid; a separate measurement")
@@ -173,7 +176,9 @@ def sample_columns(X, P, seed=0):
 
 # --------------------------------------------------------------- main
 def main():
+    global MEAN_IN_FFT
     args = parse()
+    MEAN_IN_FFT = not args.mean_pass
     import torch
     import torch.distributed as dist
 
@@ -230,7 +235,8 @@ def main():
         pass
     # one step launches each phase's kernels once (modes: the small coefficient
     # kernel + the mode GEMM), so the per-step phase time is the launch time
-    per_phase = {k: kernel_roofline(k, phase_ms[k] / args.steps, M, nb, nf, nmodes, peaks, args.precision, elem)
+    per_phase = {k: kernel_roofline(k, phase_ms[k] / args.steps, M, nb, nf, nmodes, peaks, args.precision, elem,
+                                    sp.mean_in_fft)
                  for k in phase_ms if phase_launch.get(k, 0) > 0}
     dom = max(per_phase, key=lambda k: phase_ms[k])
     roof = per_phase[dom]
@@ -246,7 +252,8 @@ def main():
             "phases_ms_per_step": {k: round(v / args.steps, 4) for k, v in phase_ms.items()},
             "phase_rooflines": per_phase,
             "gpu_launches": int(sum(phase_launch.values())), "clocks": clk,
-            "snapshots_per_s": round(world * NT / (ms_step * 1e-3), 1)}
+            "snapshots_per_s": round(world * NT / (ms_step * 1e-3), 1),
+            "mean_in_fft": bool(sp.mean_in_fft)}
     # fit alone (mean, FFT, Gram, reduction, eigen-solve: the phase events of
     # spod_fit, which runs its phases back to back on one stream)
     fit_ms = sum(phase_ms[k] for k in ("mean", "fft", "gram", "reduce", "eig")) / args.steps
@@ -320,9 +327,13 @@ def gather_slab_grams(part, parts) -> None:
         parts[0].copy_(part)
 
 
+MEAN_IN_FFT = True      # --mean-pass clears it
+
+
 def make_plan(precision, wl):
     from paper_2309_11808_gb300 import SPOD
-    return SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=wl.X.dtype, precision=precision, weights=wl.W)
+    return SPOD(wl.npoints, NVARS, NT, NFFT, NOVERLAP, dtype=wl.X.dtype, precision=precision, weights=wl.W,
+                mean_in_fft=MEAN_IN_FFT)
 
 
 def timed_run(precision, wl, steps, warmup, world, dev, clocks):
@@ -401,13 +412,14 @@ KERNELS = {
 }
 
 
-def qhat_bytes_per_point(nb, nf, precision):
-    """Bytes of Qhat per spatial point: nf x 2 nb real entries."""
+def qhat_bytes_per_point(nb, nf, precision, folded=False):
+    """Bytes of Qhat per spatial point: nf x 2 nb real entries (+ nf for the
+    rho row when the time mean is taken inside the FFT pass)."""
     per = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4}[precision]
-    return nf * 2 * nb * per
+    return nf * (2 * nb + (1 if folded else 0)) * per
 
 
-def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, elem=4):
+def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, elem=4, folded=False):
     """Roofline of one launch of a phase's kernel on its ALGORITHMIC work.
 
     The method's compulsory traffic is X read once and the modes written
@@ -428,7 +440,7 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, e
         kern = kern[precision]
     if phase == "fft" and elem == 8:
         kern = "k_fft_pipe (complex input)"
-    q = qhat_bytes_per_point(nb, nf, precision) * M
+    q = qhat_bytes_per_point(nb, nf, precision, folded) * M
     phi = nf * nmodes * M * (16 if precision == "fp64" else 8)
     x = NT * M * (8 if precision == "fp64" and phase == "mean" else elem)
     traffic = TRAFFIC.get((phase, precision)) if elem == 4 else None
@@ -487,9 +499,7 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, e
 # points processed (x 32) to the full grid; the summaries are in profiles/.
 # Absent entries: no capture of the current kernel version.
 TRAFFIC = {
-    ("fft", "bf16x3"): int((491.146752 + 910.630400) * 1e6 * 32),    # k_fft_pipe<float, 1, 32, 512> (L2 prefetch)
-    ("gram", "bf16x3"): int((960.439296 + 19.947264) * 1e6 * 32),    # k_gram_tc<1, 40> (one-block runs, upper-triangle drains)
-    ("modes", "bf16x3"): int((976.941568 + 907.403264) * 1e6 * 32),  # k_modes_tc<1> (Phi view)
+    # bf16x3 fft / gram / modes: recaptured after the time mean moved into the FFT pass
     ("gram", "fp32"): int((961.233 + 25.105920) * 1e6 * 32),         # k_gram_simt<float>
     # k_modes_simt changed (frequency range, Phi view) after its capture: no entry
 }

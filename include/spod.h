@@ -124,6 +124,16 @@ typedef struct {
                                 grid when its Qhat fits in the larger of 40 GiB and 35 % of
                                 the device memory free at plan creation, else chunks of that
                                 size.  Bounds the device workspace (Qhat of one chunk). */
+  int mean_in_fft;           /* 1 (default): where the plan allows it, the time mean is taken
+                                inside the pipelined FFT pass, which then reads X only once
+                                (real data, BF16 / BF16X3 precision, nfft 256 / 384 / 512 /
+                                720, 2 nb not a multiple of 16): each column is centred on
+                                the mean c of 128 evenly spaced snapshots, the spectra of
+                                x - c are stored with one more row rho = sqrt(W) (mu - c),
+                                and the Gram and the modes apply the exact rank-one
+                                correction Qhat_f = Z_f - rho What_f in FP64 / in the MMA.
+                                0: a separate mean pass reads X first.  Read back whether
+                                it applies from spod_plan_info.mean_in_fft. */
 } spod_plan_desc;
 
 typedef struct {
@@ -135,6 +145,7 @@ typedef struct {
   int device;                /* CUDA device the plan lives on */
   size_t workspace_bytes;    /* device memory owned by the plan */
   int64_t chunk_points;      /* spatial points per FFT->Gram pass */
+  int mean_in_fft;           /* 1: the time mean is folded into the FFT pass (see the desc) */
 } spod_plan_info;
 
 /* Fill *desc with defaults (Hamming, 50 % overlap unset = 0, FP32, NORM_NB,

@@ -27,7 +27,8 @@ _NORMS = {"nb": SPOD_NORM_NB, "nb-1": SPOD_NORM_NB_MINUS_1}
 
 def make_desc(npoints: int, nvars: int, nt: int, nfft: int, noverlap: int, *, dtype=torch.float32,
               precision: str = "fp32", window: str = "hamming", user_window=None, weights=None,
-              norm: str = "nb", subtract_mean: bool = True, dt: float = 1.0, chunk_points: int = 0):
+              norm: str = "nb", subtract_mean: bool = True, dt: float = 1.0, chunk_points: int = 0,
+              mean_in_fft: bool = True):
     """Build an spod_plan_desc; returns (desc, keepalive) -- keep the second
     object alive until spod_plan_create has returned (it owns the host arrays)."""
     d = _lib.spod_desc_init()
@@ -44,6 +45,7 @@ def make_desc(npoints: int, nvars: int, nt: int, nfft: int, noverlap: int, *, dt
     d.subtract_mean = int(bool(subtract_mean))
     d.dt = float(dt)
     d.chunk_points = int(chunk_points)
+    d.mean_in_fft = int(bool(mean_in_fft))
     keep = []
     if user_window is not None:
         uw = np.ascontiguousarray(np.asarray(user_window, dtype=np.float64))
@@ -69,6 +71,7 @@ class SPOD:
         info = _lib.spod_plan_get_info(self.handle)
         self.M, self.nb, self.nf, self.nt = info.M, info.nb, info.nf, info.nt
         self.info = info
+        self.mean_in_fft = bool(info.mean_in_fft)
         self.f64 = desc.precision == SPOD_PREC_FP64
 
     def close(self) -> None:

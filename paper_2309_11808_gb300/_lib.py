@@ -37,13 +37,13 @@ class spod_plan_desc(C.Structure):
                 ("nfft", C.c_int), ("noverlap", C.c_int), ("window", C.c_int),
                 ("user_window", C.POINTER(C.c_double)), ("weights", C.POINTER(C.c_double)),
                 ("dt", C.c_double), ("in_dtype", C.c_int), ("precision", C.c_int), ("norm", C.c_int),
-                ("subtract_mean", C.c_int), ("chunk_points", C.c_int64)]
+                ("subtract_mean", C.c_int), ("chunk_points", C.c_int64), ("mean_in_fft", C.c_int)]
 
 
 class spod_plan_info(C.Structure):
     _fields_ = [("M", C.c_int64), ("nt", C.c_int64), ("nfft", C.c_int), ("noverlap", C.c_int),
                 ("step", C.c_int), ("nb", C.c_int), ("nf", C.c_int), ("device", C.c_int),
-                ("workspace_bytes", C.c_size_t), ("chunk_points", C.c_int64)]
+                ("workspace_bytes", C.c_size_t), ("chunk_points", C.c_int64), ("mean_in_fft", C.c_int)]
 
 
 class spod_tuning(C.Structure):

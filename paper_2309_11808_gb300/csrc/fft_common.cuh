@@ -37,6 +37,7 @@ struct FftArgs {
   int64_t xoff;                   // point of X's first column (tiled data)
   int64_t mpad;                   // points written: mcount rounded up to 64 (zeros past mcount)
   int nfft, step, nb, nf;
+  int qrows;                      // Qhat rows per frequency of the blocked layout
   int subtract_mean;
   FftPlan fp;
 };

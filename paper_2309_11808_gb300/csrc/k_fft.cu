@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_fft(const Tin* __restrict__ X, const R*
     }
     // planar FP32/FP64 rows, or 64-point blocked BF16 rows (qhat_blocked_offset)
     const int64_t o_re = (OUTK == OUT_NATIVE) ? ((int64_t)f * 2 * a.nb + l) * rs + lm
-                                              : qhat_blocked_offset(a.nf, a.nb, f, l, lm);
+                                              : qhat_blocked_offset(a.nf, a.qrows, f, l, lm);
     const int64_t o_im = o_re + (int64_t)a.nb * ((OUTK == OUT_NATIVE) ? rs : (int64_t)kQBlock);
     if constexpr (OUTK == OUT_NATIVE) {
       R* q = static_cast<R*>(qout);
@@ -200,6 +200,7 @@ cudaError_t launch_fft_t(const spod_plan_s& p, const void* d_X, int64_t m0, int6
   a.M = p.x_ld ? p.x_ld : p.M; a.xoff = p.x_off; a.m0 = m0; a.mcount = mcount; a.chunk = p.chunk_points;
   a.mpad = std::min<int64_t>(p.chunk_points, (mcount + 63) / 64 * 64);
   a.nfft = p.nfft; a.step = p.step; a.nb = p.nb; a.nf = p.nf;
+  a.qrows = p.qrows;
   a.subtract_mean = p.desc.subtract_mean;
   a.fp = p.fft;
   const size_t smem = fft_smem_bytes(p);

@@ -56,7 +56,34 @@ struct PipeArgs {
   int64_t xoff;                      // column of X's first TMA column (tiled data)
   int step, nb, nf, boxr;
   int subtract_mean;
+  int qrows;                         // Qhat rows per frequency (blocked layout)
+  // time mean folded into the transform (real data): a provisional centre
+  // c (the mean of kCentreSamples evenly spaced snapshots of the column) is
+  // subtracted instead of the mean, the sum of x - c over all nt snapshots
+  // accumulated, mu = c + mean(x - c) written to mu_out and
+  // rho = sqrt(W) mean(x - c) to Qhat row 2 nb of every frequency
+  int fold;
+  int64_t nt, tail0;                 // snapshots; first snapshot in no block
+  const void* xg;                    // X itself (tail samples), row stride xld, column of point lm: xc0 + lm
+  int64_t xld, xc0;
+  double* mu_out;
 };
+
+// Snapshots that give the provisional centre of a column when the mean is
+// folded: the closer c is to mu, the smaller the rank-one correction and the
+// cancellation it brings to the low bins (the centre's offset from mu enters
+// the uncorrected spectra times sum_n w_n)
+constexpr int kCentreSamples = 128;
+
+// Compensated (Kahan) FP32 sum: s + (-c) carries the running total to about
+// one rounding of the result.  The folded mean's sums use it instead of FP64
+// adds, which run at a small fraction of the FP32 rate on this part.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 
 struct PipeHdr {
   uint64_t full;
@@ -80,11 +107,13 @@ template <> struct PairLoad<double> {
 };
 
 // Pass 0 (Ns = 1, no twiddles): butterfly inputs come from the ring rows of
-// the current block with the mean removed and the window applied.
-template <typename Tin, int TP, int N, int RAD>
+// the current block with the mean removed and the window applied.  Element r
+// of butterfly b is sample n = b + r N / RAD; with FOLD the elements with
+// r >= rthr (a block-uniform bound) are also summed into acc0 / acc1.
+template <typename Tin, int TP, int N, int RAD, bool FOLD>
 __device__ __forceinline__ void pass_first(const Tin* __restrict__ ring, int rb, float2* __restrict__ dst,
                                            const float* __restrict__ wsm, float mhi0, float mlo0, float mhi1,
-                                           float mlo1) {
+                                           float mlo1, int rthr, float& acc0, float& acc1) {
   constexpr int PTP = Geo<TP>::PTP, PC = Geo<TP>::PC, PBSTEP = Geo<TP>::BSTEP;
   constexpr int nbut = N / RAD;
   constexpr int MAXB = (nbut + PBSTEP - 1) / PBSTEP;
@@ -102,7 +131,12 @@ __device__ __forceinline__ void pass_first(const Tin* __restrict__ ring, int rb,
         if (slot >= N) slot -= N;
         const float2 x = PairLoad<Tin>::get(ring + slot * PTP + 2 * col);
         const float wn = wsm[n];
-        v[i][r] = make_float2(((x.x - mhi0) - mlo0) * wn, ((x.y - mhi1) - mlo1) * wn);
+        const float d0 = (x.x - mhi0) - mlo0, d1 = (x.y - mhi1) - mlo1;
+        if (FOLD && r >= rthr) {           // a snapshot no earlier block held
+          acc0 += d0;
+          acc1 += d1;
+        }
+        v[i][r] = make_float2(d0 * wn, d1 * wn);
       }
     }
   }
@@ -226,9 +260,9 @@ __device__ __forceinline__ void output_phase_cplx(const float2* __restrict__ src
   const int f0 = threadIdx.x / kOutCp;
   constexpr bool BLK = OUTK != OUT_NATIVE;
   const int64_t rs = BLK ? (int64_t)kQBlock : a.chunk;
-  const int64_t rowstride = (int64_t)2 * a.nb * rs;
+  const int64_t rowstride = (int64_t)(BLK ? a.qrows : 2 * a.nb) * rs;
   const int64_t imoff = (int64_t)a.nb * rs;
-  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lp0 + 2 * cp)
+  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.qrows, f0, l, lp0 + 2 * cp)
                   : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lp0 + 2 * cp;
   const float4* src4 = reinterpret_cast<const float4*>(src);
   constexpr int kIters = (N + kOutFStep - 1) / kOutFStep;
@@ -269,9 +303,9 @@ __device__ __forceinline__ void output_phase(const float2* __restrict__ src, con
   // points, [chunk / 64][nf][2 nb][64] (see qhat_blocked_offset)
   constexpr bool BLK = OUTK != OUT_NATIVE;
   const int64_t rs = BLK ? (int64_t)kQBlock : a.chunk;           // row stride
-  const int64_t rowstride = (int64_t)2 * a.nb * rs;              // one frequency
+  const int64_t rowstride = (int64_t)(BLK ? a.qrows : 2 * a.nb) * rs;   // one frequency
   const int64_t imoff = (int64_t)a.nb * rs;
-  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.nb, f0, l, lm0 + 4 * cp)
+  int64_t o = BLK ? qhat_blocked_offset(a.nf, a.qrows, f0, l, lm0 + 4 * cp)
                   : ((int64_t)f0 * 2 * a.nb + l) * a.chunk + lm0 + 4 * cp;
   const float4* src4 = reinterpret_cast<const float4*>(src);
   // compile-time trip count (nf = N/2 + 1): the iterations' loads overlap
@@ -320,7 +354,16 @@ struct PipeLayout {
   static constexpr size_t buf1 = buf0 + (size_t)N * (TP / 2) * sizeof(float2);
   static constexpr size_t tw = buf1 + (size_t)N * (TP / 2) * sizeof(float2);
   static constexpr size_t win = tw + (size_t)N * sizeof(float2);
-  static constexpr size_t end = win + (size_t)N * sizeof(float);
+  // folded mean (kept out of the registers the passes need and of the pass
+  // buffers): each thread's compensated sums of x - c, (s0, c0, s1, c1); the
+  // threads' partial sums of the next tile's centre samples [32][TP]; the
+  // centres and the rho values of a tile [TP] each; the centre sample rows
+  static constexpr size_t acc = (win + (size_t)N * sizeof(float) + 15) / 16 * 16;
+  static constexpr size_t cred = acc + (size_t)Geo<TP>::THREADS * sizeof(float4);
+  static constexpr size_t cen = cred + (size_t)Geo<TP>::BSTEP * TP * sizeof(float);
+  static constexpr size_t rho = cen + (size_t)TP * sizeof(float);
+  static constexpr size_t crow = rho + (size_t)TP * sizeof(float);
+  static constexpr size_t end = crow + (size_t)kCentreSamples * sizeof(int);
   static constexpr size_t dyn = end + 1024;                    // alignment slack
 };
 
@@ -349,6 +392,12 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
   float2* tw = reinterpret_cast<float2*>(sm + L::tw);
   float* wsm = reinterpret_cast<float*>(sm + L::win);
   const int tid = threadIdx.x;
+  float4* const acc_all = reinterpret_cast<float4*>(sm + L::acc);
+  float4* const my_acc = acc_all + tid;
+  float* const cred = reinterpret_cast<float*>(sm + L::cred);
+  float* const cen = reinterpret_cast<float*>(sm + L::cen);
+  float* const rhos = reinterpret_cast<float*>(sm + L::rho);
+  int* const crow = reinterpret_cast<int*>(sm + L::crow);
   const uint32_t bar = smem_u32(&hdr->full);
   volatile int* abort_flag = &hdr->abort;
 
@@ -361,6 +410,9 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
     tw[i] = tw_g[i];
     wsm[i] = win[i];
   }
+  // folded mean: the centre's sample rows t_k = floor((2k + 1) nt / (2 nc))
+  const int ncen = (int)(a.nt < kCentreSamples ? a.nt : kCentreSamples);
+  if (tid < ncen) crow[tid] = (int)(((int64_t)(2 * tid + 1) * a.nt) / (2 * ncen));
   __syncthreads();
 
   const int64_t t_first = blockIdx.x;
@@ -392,6 +444,50 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
   uint32_t phase = 0;
   bool last_ok = true;               // thread 0: its last wait saw the copy land
   int par = 0;                       // buffer roles of the current block
+
+  // Folded mean (real data, BF16 / BF16X3 output): the provisional centre c
+  // of a column is the mean of its ncen snapshots at rows crow[k]; thread b of
+  // a column sums k = b, b + 32, ...  The loads for tile t + t_step are issued
+  // while tile t runs (pc0 / pc1) and reduced at its end.
+  constexpr bool FOLDK = !CPLX && OUTK != OUT_NATIVE;
+  const bool fold = FOLDK && a.fold;
+  constexpr int PB = Geo<TP>::BSTEP;
+  const int b0 = tid / PC;
+  const Tin* const xg = static_cast<const Tin*>(a.xg);
+  auto centre_partial = [&](int64_t t, float& c0, float& c1) {
+    c0 = 0.f;
+    c1 = 0.f;
+    if (t >= a.ntiles) return;
+    const int64_t lmA = t * PTP + 2 * col;
+    const Tin* base = xg + a.xc0 + lmA;
+#pragma unroll 1
+    for (int k = b0; k < ncen; k += PB) {
+      const Tin* row = base + (int64_t)crow[k] * a.xld;
+      if (lmA < a.mcount) c0 += to_f32<Tin>(row[0]);
+      if (lmA + 1 < a.mcount) c1 += to_f32<Tin>(row[1]);
+    }
+  };
+  float cen0 = 0.f, cen1 = 0.f;      // this thread's column pair: centres of the current tile
+  float pc0 = 0.f, pc1 = 0.f;        // partial centre sums of the next tile
+  float swr = 0.f, cme = 0.f;        // threads < TP: sqrt(W) and centre of point tid of the tile
+  if (fold) {
+    centre_partial(t_first, pc0, pc1);
+    cred[b0 * PTP + 2 * col] = pc0;
+    cred[b0 * PTP + 2 * col + 1] = pc1;
+    __syncthreads();
+    if (tid < PTP) {
+      float sm = 0.f;
+#pragma unroll 1
+      for (int q = 0; q < PB; ++q) sm += cred[q * PTP + tid];
+      cen[tid] = sm / (float)ncen;
+    }
+    __syncthreads();
+    cen0 = cen[2 * col];
+    cen1 = cen[2 * col + 1];
+    if (tid < PTP) cme = cen[tid];
+    *my_acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    centre_partial(t_first + t_step, pc0, pc1);
+  }
   for (int64_t t = t_first; t < a.ntiles; t += t_step) {
     const int64_t lm0 = t * PTP;
     const int64_t gm0 = a.m0 + lm0;
@@ -400,10 +496,10 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
                                      // complex data: sqrt(W) of its two points
     {
       const int64_t lm = lm0 + 2 * col;
-      if (a.subtract_mean && lm < a.mcount) {
+      if (a.subtract_mean && !a.fold && lm < a.mcount) {
         const double d = mu[gm0 + 2 * col]; mhi0 = (float)d; mlo0 = (float)(d - (double)mhi0);
       }
-      if (a.subtract_mean && lm + 1 < a.mcount) {
+      if (a.subtract_mean && !a.fold && lm + 1 < a.mcount) {
         const double d = mu[gm0 + 2 * col + 1]; mhi1 = (float)d; mlo1 = (float)(d - (double)mhi1);
       }
       const int cp = tid % Geo<TP>::OUTCP;
@@ -417,13 +513,48 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
           sw[q] = (lm0 + 4 * cp + q < a.mcount) ? 0.5f * sqrtW[gm0 + 4 * cp + q] : 0.f;
       }
     }
+    if (fold) {
+      mhi0 = cen0;
+      mhi1 = cen1;
+      if (tid < PTP) swr = lm0 + tid < a.mcount ? sqrtW[gm0 + tid] : 0.f;
+    }
     int rb = 0;                      // ring slot of the block's first row
     for (int l = 0; l < a.nb; ++l) {
       last_ok = mbar_wait(bar, phase & 1, abort_flag, gflags);
       ++phase;
       float2* bA = par ? buf1 : buf0;
       float2* bB = par ? buf0 : buf1;
-      pass_first<Tin, TP, N, S::R0>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1);
+      {
+        // with the folded mean the centre c replaces mu (mlo = 0) and the
+        // snapshots no earlier block held (all of block 0, the last step rows
+        // of the others) are summed: FP32 runs of <= 16 samples, then a
+        // compensated FP32 running sum
+        // The new snapshots are n >= N - step; when N - step is a multiple of
+        // N / R0 (50 % overlap, none, 75 %, ...) they are the elements
+        // r >= (N - step) / (N / R0) of every first-pass butterfly, otherwise
+        // a separate loop re-reads them from the ring.
+        constexpr int NBUT = N / S::R0;
+        const int nnew0 = !fold ? N : l == 0 ? 0 : N - a.step;
+        const bool in_pass = nnew0 % NBUT == 0;
+        const int rthr = fold && in_pass ? nnew0 / NBUT : S::R0;
+        float s0 = 0.f, s1 = 0.f;
+        pass_first<Tin, TP, N, S::R0, FOLDK>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1, rthr, s0, s1);
+        if (fold) {
+          if (!in_pass) {
+            for (int n = nnew0 + tid / PC; n < N; n += Geo<TP>::BSTEP) {
+              int slot = rb + n;
+              if (slot >= N) slot -= N;
+              const float2 x = PairLoad<Tin>::get(ring + slot * PTP + 2 * col);
+              s0 += x.x - mhi0;
+              s1 += x.y - mhi1;
+            }
+          }
+          float4 ac = *my_acc;
+          kahan_add(ac.x, ac.y, s0);
+          kahan_add(ac.z, ac.w, s1);
+          *my_acc = ac;
+        }
+      }
       __syncthreads();
       if (hdr->abort) break;
       // the ring rows of this block are consumed: request the next rows
@@ -444,6 +575,65 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
       par ^= (S::P & 1);
     }
     if (hdr->abort) break;
+    if (fold) {
+      // the snapshots in no block (the tail): thread b of a column takes t = tail0 + b + 32 k
+      const int64_t lmA = lm0 + 2 * col;
+      float4 ac = *my_acc;
+      for (int64_t tt = a.tail0 + b0; tt < a.nt; tt += PB) {
+        const Tin* row = xg + tt * a.xld + a.xc0 + lmA;
+        if (lmA < a.mcount) kahan_add(ac.x, ac.y, to_f32<Tin>(row[0]) - mhi0);
+        if (lmA + 1 < a.mcount) kahan_add(ac.z, ac.w, to_f32<Tin>(row[1]) - mhi1);
+      }
+      *my_acc = ac;
+      cred[b0 * PTP + 2 * col] = pc0;
+      cred[b0 * PTP + 2 * col + 1] = pc1;
+      __syncthreads();
+      if (tid < PTP) {
+        // point tid: its column's 32 compensated partials in a fixed order,
+        // mu = c + sum / nt, rho = sqrt(W) (mu - c)
+        const int c = tid >> 1, h = tid & 1;
+        float ss = 0.f, sc = 0.f, cc = 0.f;
+#pragma unroll 1
+        for (int q = 0; q < PB; ++q) {
+          const float4 v = acc_all[q * PC + c];
+          kahan_add(ss, sc, h ? v.z : v.x);
+          cc += h ? v.w : v.y;
+        }
+        // each partial is s - c; the total (ss - sc) - sum of the c
+        const double mup = ((double)ss - (double)sc - (double)cc) / (double)a.nt;
+        float rho = 0.f;
+        if (lm0 + tid < a.mcount) {
+          a.mu_out[gm0 + tid] = (double)cme + mup;
+          rho = (float)(mup * (double)swr);
+        }
+        rhos[tid] = rho;
+      } else if (tid < 2 * PTP) {
+        // the next tile's centre of point tid - TP
+        const int p = tid - PTP;
+        float sm = 0.f;
+#pragma unroll 1
+        for (int q = 0; q < PB; ++q) sm += cred[q * PTP + p];
+        cen[p] = sm / (float)ncen;
+      }
+      __syncthreads();
+      // rho into Qhat row 2 nb of every frequency (two points per word)
+      for (int it = tid; it < a.nf * (PTP / 2); it += PTHREADS) {
+        const int f = it / (PTP / 2), j = it - f * (PTP / 2);
+        const int64_t o = qhat_blocked_offset(a.nf, a.qrows, f, 2 * a.nb, lm0 + 2 * j);
+        const uint32_t hw = pack_bf16x2(rhos[2 * j], rhos[2 * j + 1]);
+        *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(qout) + o) = hw;
+        if constexpr (OUTK == OUT_BF16X3)
+          *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(qlo) + o) =
+              pack_bf16x2(rhos[2 * j] - bf16_lo_f(hw), rhos[2 * j + 1] - bf16_hi_f(hw));
+      }
+      cen0 = cen[2 * col];
+      cen1 = cen[2 * col + 1];
+      if (tid < PTP) cme = cen[tid];
+      *my_acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      centre_partial(t + 2 * t_step, pc0, pc1);
+      // cen and rhos are next written after the next tile's first barrier,
+      // by which time every thread has read them
+    }
   }
   // a request issued before an abort must land before the CTA exits
   if (tid == 0 && !last_ok) mbar_drain(bar, (phase - 1) & 1, gflags);
@@ -452,8 +642,8 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
 // Complex data (CPLX): m0 and mcount count points; the ring, the mean and the
 // tiles work on the 2M interleaved components.
 template <typename Tin, int OUTK, int TP, int N, bool CPLX>
-cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
-                          cudaStream_t s) {
+cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, const void* d_X, int64_t m0,
+                          int64_t mcount, cudaStream_t s) {
   constexpr int PTHREADS = Geo<TP>::THREADS;
   constexpr int64_t K = CPLX ? 2 : 1;          // components per point
   PipeArgs a;
@@ -464,6 +654,14 @@ cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
   a.step = p.step; a.nb = p.nb; a.nf = p.nf;
   a.boxr = p.ring_boxr;
   a.subtract_mean = p.desc.subtract_mean;
+  a.qrows = p.qrows;
+  a.fold = (!CPLX && p.mean_fold) ? 1 : 0;
+  a.nt = p.nt;
+  a.tail0 = (int64_t)(p.nb - 1) * p.step + p.nfft;
+  a.xg = d_X;
+  a.xld = K * (p.x_ld ? p.x_ld : p.M);
+  a.xc0 = a.m0 - a.xoff;
+  a.mu_out = p.d_mu;
   const size_t smem = PipeLayout<Tin, TP, N>::dyn;
   auto kern = k_fft_pipe<Tin, OUTK, TP, N, CPLX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -479,33 +677,33 @@ cudaError_t launch_pipe_n(const spod_plan_s& p, const CUtensorMap& xmap, int64_t
 }
 
 template <typename Tin, int OUTK, bool CPLX>
-cudaError_t launch_pipe_t(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
-                          cudaStream_t s) {
+cudaError_t launch_pipe_t(const spod_plan_s& p, const CUtensorMap& xmap, const void* d_X, int64_t m0,
+                          int64_t mcount, cudaStream_t s) {
   if constexpr (sizeof(Tin) <= 4) {
     if (p.pipe_tp == 32) {
       switch (p.nfft) {
-        case 256: return launch_pipe_n<Tin, OUTK, 32, 256, CPLX>(p, xmap, m0, mcount, s);
-        case 384: return launch_pipe_n<Tin, OUTK, 32, 384, CPLX>(p, xmap, m0, mcount, s);
-        case 512: return launch_pipe_n<Tin, OUTK, 32, 512, CPLX>(p, xmap, m0, mcount, s);
+        case 256: return launch_pipe_n<Tin, OUTK, 32, 256, CPLX>(p, xmap, d_X, m0, mcount, s);
+        case 384: return launch_pipe_n<Tin, OUTK, 32, 384, CPLX>(p, xmap, d_X, m0, mcount, s);
+        case 512: return launch_pipe_n<Tin, OUTK, 32, 512, CPLX>(p, xmap, d_X, m0, mcount, s);
         default: return cudaErrorInvalidValue;
       }
     }
   }
   if (p.pipe_tp != 16) return cudaErrorInvalidValue;
   switch (p.nfft) {
-    case 256: return launch_pipe_n<Tin, OUTK, 16, 256, CPLX>(p, xmap, m0, mcount, s);
-    case 384: return launch_pipe_n<Tin, OUTK, 16, 384, CPLX>(p, xmap, m0, mcount, s);
-    case 512: return launch_pipe_n<Tin, OUTK, 16, 512, CPLX>(p, xmap, m0, mcount, s);
-    default: return launch_pipe_n<Tin, OUTK, 16, 720, CPLX>(p, xmap, m0, mcount, s);
+    case 256: return launch_pipe_n<Tin, OUTK, 16, 256, CPLX>(p, xmap, d_X, m0, mcount, s);
+    case 384: return launch_pipe_n<Tin, OUTK, 16, 384, CPLX>(p, xmap, d_X, m0, mcount, s);
+    case 512: return launch_pipe_n<Tin, OUTK, 16, 512, CPLX>(p, xmap, d_X, m0, mcount, s);
+    default: return launch_pipe_n<Tin, OUTK, 16, 720, CPLX>(p, xmap, d_X, m0, mcount, s);
   }
 }
 
 template <typename Tin, bool CPLX = false>
-cudaError_t launch_pipe_in(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
-                           cudaStream_t s) {
-  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_pipe_t<Tin, OUT_BF16X3, CPLX>(p, xmap, m0, mcount, s);
-  if (p.desc.precision == SPOD_PREC_BF16) return launch_pipe_t<Tin, OUT_BF16, CPLX>(p, xmap, m0, mcount, s);
-  return launch_pipe_t<Tin, OUT_NATIVE, CPLX>(p, xmap, m0, mcount, s);
+cudaError_t launch_pipe_in(const spod_plan_s& p, const CUtensorMap& xmap, const void* d_X, int64_t m0,
+                           int64_t mcount, cudaStream_t s) {
+  if (p.desc.precision == SPOD_PREC_BF16X3) return launch_pipe_t<Tin, OUT_BF16X3, CPLX>(p, xmap, d_X, m0, mcount, s);
+  if (p.desc.precision == SPOD_PREC_BF16) return launch_pipe_t<Tin, OUT_BF16, CPLX>(p, xmap, d_X, m0, mcount, s);
+  return launch_pipe_t<Tin, OUT_NATIVE, CPLX>(p, xmap, d_X, m0, mcount, s);
 }
 
 template <typename Tin, int TP>
@@ -560,14 +758,14 @@ bool fft_pipe_usable(const spod_plan_s& p, int smem_optin) {
   return smem > 0 && smem <= (size_t)smem_optin;
 }
 
-cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
-                                  cudaStream_t s) {
+cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, const void* d_X, int64_t m0,
+                                  int64_t mcount, cudaStream_t s) {
   switch (p.desc.in_dtype) {
-    case SPOD_F64: return launch_pipe_in<double>(p, xmap, m0, mcount, s);
-    case SPOD_F32: return launch_pipe_in<float>(p, xmap, m0, mcount, s);
-    case SPOD_C64: return launch_pipe_in<float, true>(p, xmap, m0, mcount, s);
-    case SPOD_C128: return launch_pipe_in<double, true>(p, xmap, m0, mcount, s);
-    default: return launch_pipe_in<__nv_bfloat16>(p, xmap, m0, mcount, s);
+    case SPOD_F64: return launch_pipe_in<double>(p, xmap, d_X, m0, mcount, s);
+    case SPOD_F32: return launch_pipe_in<float>(p, xmap, d_X, m0, mcount, s);
+    case SPOD_C64: return launch_pipe_in<float, true>(p, xmap, d_X, m0, mcount, s);
+    case SPOD_C128: return launch_pipe_in<double, true>(p, xmap, d_X, m0, mcount, s);
+    default: return launch_pipe_in<__nv_bfloat16>(p, xmap, d_X, m0, mcount, s);
   }
 }
 

@@ -453,16 +453,31 @@ __global__ void k_gram_tc_collect(const uint8_t* __restrict__ slots, int r2, int
 }
 
 // M_f from D = Y Y^T: upper triangle formed, kappa applied, Hermitian completion, NaN check.
-__global__ void k_gram_tc_finish(const double* __restrict__ acc, int nb, double kappa, double* __restrict__ gram,
-                                 unsigned* __restrict__ flags) {
+//
+// Folded mean (what != nullptr, r2 = 2 nb + 1): the stored rows are the
+// spectra Z of x - c and row 2 nb is rho = sqrt(W) (mu - c); the spectra of
+// x - mu are Z - rho What_f, i.e. row i loses rho u_i with u_i = Re What_f
+// (i < nb) or Im What_f (nb <= i < 2 nb), so in FP64
+//   Dc[i][j] = D[i][j] - u_i D[j][2nb] - u_j D[i][2nb] + u_i u_j D[2nb][2nb].
+__global__ void k_gram_tc_finish(const double* __restrict__ acc, int nb, int r2, const double* __restrict__ what,
+                                 double kappa, double* __restrict__ gram, unsigned* __restrict__ flags) {
   const int f = blockIdx.x;
-  const int r2 = 2 * nb;
   const double* D = acc + (int64_t)f * r2 * r2;
+  const double ur = what ? what[2 * f] : 0.0, ui = what ? what[2 * f + 1] : 0.0;
+  const int rr = 2 * nb;
+  auto dc = [&](int i, int j) -> double {
+    double v = D[i * r2 + j];
+    if (what) {
+      const double u_i = i < nb ? ur : ui, u_j = j < nb ? ur : ui;
+      v += u_i * u_j * D[rr * r2 + rr] - u_i * D[j * r2 + rr] - u_j * D[i * r2 + rr];
+    }
+    return v;
+  };
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     const int i = e / nb, j = e - i * nb;
     const int l = min(i, j), lp = max(i, j);
-    double vr = D[l * r2 + lp] + D[(nb + l) * r2 + nb + lp];
-    double vi = D[l * r2 + nb + lp] - D[(nb + l) * r2 + lp];
+    double vr = dc(l, lp) + dc(nb + l, nb + lp);
+    double vi = dc(l, nb + lp) - dc(nb + l, lp);
     vr *= kappa;
     vi *= kappa;
     if (i > j) vi = -vi;
@@ -513,12 +528,13 @@ cudaError_t launch_gram_tc_x(const spod_plan_s& p, const GramTcArgs& a, int grid
 // Shared memory of the smallest (2-stage) configuration; launches use up to 8 stages.
 size_t gram_tc_smem_bytes(const spod_plan_s& p) { return gram_tc_smem_stages(p, 2); }
 
-// Slots of the persistent kernel, (max CTAs + nf - 1) x 12 (2 nb)^2 bytes (counted
-// in doubles), and the per-frequency FP64 accumulator of D over chunks, nf x (2 nb)^2.
+// Slots of the persistent kernel, (max CTAs + nf - 1) x gram_slot_bytes(qrows)
+// (counted in doubles), and the per-frequency FP64 accumulator of D over
+// chunks, nf x qrows^2 (qrows = 2 nb, + 1 with the folded mean's rho row).
 size_t gram_tc_slot_doubles(const spod_plan_s& p, int max_ctas) {
-  return ((size_t)(max_ctas + p.nf - 1) * gram_slot_bytes(2 * p.nb) + 7) / 8;
+  return ((size_t)(max_ctas + p.nf - 1) * gram_slot_bytes(p.qrows) + 7) / 8;
 }
-size_t gram_tc_acc_doubles(const spod_plan_s& p) { return (size_t)p.nf * (2 * p.nb) * (2 * p.nb); }
+size_t gram_tc_acc_doubles(const spod_plan_s& p) { return (size_t)p.nf * p.qrows * p.qrows; }
 
 // Persistent CTAs of the tensor-core Gram: one per SM unless tuned.
 int gram_tc_ctas(const spod_plan_s& p) {
@@ -529,7 +545,7 @@ int gram_tc_ctas(const spod_plan_s& p) {
 cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool first, cudaStream_t s) {
   GramTcArgs a;
   a.nb = p.nb;
-  a.r2 = 2 * p.nb;
+  a.r2 = p.qrows;                          // 2 nb, or 2 nb + 1 (rho row, same padding)
   a.np = (2 * p.nb + 15) / 16 * 16;
   a.nf = p.nf;
   a.flush = p.gram_flush > 0 ? p.gram_flush : 1;
@@ -557,7 +573,8 @@ cudaError_t launch_gram_tc_chunk(const spod_plan_s& p, int64_t mcount, bool firs
 }
 
 cudaError_t launch_gram_tc_finish(const spod_plan_s& p, cudaStream_t s) {
-  k_gram_tc_finish<<<p.nf, 256, 0, s>>>(p.d_gacc, p.nb, p.kappa, p.d_gram, p.d_flags);
+  k_gram_tc_finish<<<p.nf, 256, 0, s>>>(p.d_gacc, p.nb, p.qrows, p.mean_fold ? p.d_what : nullptr, p.kappa,
+                                        p.d_gram, p.d_flags);
   return cudaGetLastError();
 }
 

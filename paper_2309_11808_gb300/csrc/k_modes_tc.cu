@@ -82,9 +82,10 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // part), K index kk < np (l: Re Qhat row l, nb + l: Im Qhat row l), BF16 hi
 // (and lo = bf16(v - hi)), K-major 128-byte-swizzled atoms of 64 K values.
 __global__ void k_mode_image(const float* __restrict__ bmat, int nb, int nm, int np, int nn, int x3,
-                             uint32_t img_bytes, uint8_t* __restrict__ img) {
+                             const double* __restrict__ what, uint32_t img_bytes, uint8_t* __restrict__ img) {
   const int f = blockIdx.x;
   const float* Bf = bmat + (size_t)f * nb * nm * 2;
+  const double wr = what ? what[2 * f] : 0.0, wi = what ? what[2 * f + 1] : 0.0;
   uint8_t* hi = img + (size_t)f * img_bytes * (x3 ? 2 : 1);
   uint8_t* lo = hi + img_bytes;
   const int katoms = (np + 63) / 64;
@@ -98,6 +99,16 @@ __global__ void k_mode_image(const float* __restrict__ bmat, int nb, int nm, int
       const float br = Bf[(l * nm + k) * 2], bi = Bf[(l * nm + k) * 2 + 1];
       if ((n & 1) == 0) v = kk < nb ? br : -bi;
       else v = kk < nb ? bi : br;
+    } else if (what && kk == 2 * nb && k < nm) {
+      // folded mean: Qhat rows are the spectra Z of x - c, row 2 nb is rho; the
+      // spectra of x - mu are Z - rho What_f, so column k gains
+      // -rho What_f c_k with c_k = sum_l B_f[l][k]
+      double cr = 0.0, ci = 0.0;
+      for (int l = 0; l < nb; ++l) {
+        cr += (double)Bf[(l * nm + k) * 2];
+        ci += (double)Bf[(l * nm + k) * 2 + 1];
+      }
+      v = (float)((n & 1) == 0 ? -(wr * cr - wi * ci) : -(wr * ci + wi * cr));
     }
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const uint32_t off = (uint32_t)(kk >> 6) * (uint32_t)(nn * 128) + sw128_offset(n, kk & 63);
@@ -321,7 +332,8 @@ size_t modes_image_bytes(const spod_plan_s& p) {
 cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s) {
   const int np = modes_np(p), nn = modes_nn(nmodes);
   k_mode_image<<<p.nf, 256, 0, s>>>(static_cast<const float*>(p.d_bmat), p.nb, nmodes, np, nn,
-                                    p.desc.precision == SPOD_PREC_BF16X3 ? 1 : 0, modes_img_bytes(np, nn),
+                                    p.desc.precision == SPOD_PREC_BF16X3 ? 1 : 0,
+                                    p.mean_fold ? p.d_what : nullptr, modes_img_bytes(np, nn),
                                     static_cast<uint8_t*>(p.d_bimg));
   return cudaGetLastError();
 }

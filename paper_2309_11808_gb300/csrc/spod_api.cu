@@ -164,8 +164,11 @@ spod_status make_x_map(const spod_plan_s* p, const void* d_X, CUtensorMap* map) 
 // FFT of one spatial chunk: the TMA-ring kernel when the shape allows it.
 spod_status run_fft_chunk(spod_plan_s* p, const void* d_X, const CUtensorMap* xmap, int64_t m0, int64_t mc,
                           cudaStream_t s) {
+  // the folded mean lives in the pipelined kernel only (mean_fold implies pipe_ok,
+  // and every caller builds the X map when ring_ok holds)
+  if (p->mean_fold && !xmap) return fail(SPOD_EUNSUPPORTED, "folded time mean without the X tensor map");
   cudaError_t e = !xmap        ? launch_fft_chunk(*p, d_X, m0, mc, s)
-                  : p->pipe_ok ? launch_fft_pipe_chunk(*p, *xmap, m0, mc, s)
+                  : p->pipe_ok ? launch_fft_pipe_chunk(*p, *xmap, d_X, m0, mc, s)
                                : launch_fft_ring_chunk(*p, *xmap, m0, mc, s);
   if (e != cudaSuccess) return cuda_fail(e, "fft kernel");
   return SPOD_OK;
@@ -184,9 +187,9 @@ void make_fft_store_maps(spod_plan_s* p) {
   const int rank = p->tensor ? 4 : 3;
   cuuint64_t dims[4], strides[3];
   if (p->tensor) {
-    dims[0] = kQBlock; dims[1] = 2 * p->nb; dims[2] = p->nf; dims[3] = p->chunk_points / kQBlock;
+    dims[0] = kQBlock; dims[1] = p->qrows; dims[2] = p->nf; dims[3] = p->chunk_points / kQBlock;
     strides[0] = (cuuint64_t)kQBlock * el;
-    strides[1] = strides[0] * 2 * p->nb;
+    strides[1] = strides[0] * p->qrows;
     strides[2] = strides[1] * p->nf;
   } else {
     dims[0] = p->chunk_points; dims[1] = 2 * p->nb; dims[2] = p->nf;
@@ -212,10 +215,10 @@ spod_status make_qhat_maps(spod_plan_s* p) {
   if (!encode) return fail(SPOD_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
   // blocked layout [chunk / 64][nf][2 nb][64] (qhat_blocked_offset): one box =
   // one frequency's rows over one 64-point K step; rows past 2 nb read as zero
-  const cuuint64_t dims[4] = {(cuuint64_t)kQBlock, (cuuint64_t)(2 * p->nb), (cuuint64_t)p->nf,
+  const cuuint64_t dims[4] = {(cuuint64_t)kQBlock, (cuuint64_t)p->qrows, (cuuint64_t)p->nf,
                               (cuuint64_t)(p->chunk_points / kQBlock)};
   const cuuint64_t row = (cuuint64_t)kQBlock * 2;
-  const cuuint64_t strides[3] = {row, row * 2 * p->nb, row * 2 * p->nb * p->nf};
+  const cuuint64_t strides[3] = {row, row * p->qrows, row * p->qrows * p->nf};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   void* bases[2] = {p->d_qhat, p->d_qlo ? p->d_qlo : p->d_qhat};
   CUtensorMap* maps[4] = {&p->tmap_hi, &p->tmap_lo, &p->tmap_hi2, &p->tmap_lo2};
@@ -256,6 +259,7 @@ spod_status spod_desc_init(spod_plan_desc* d) {
   d->norm = SPOD_NORM_NB;
   d->subtract_mean = 1;
   d->chunk_points = 0;
+  d->mean_in_fft = 1;
   return SPOD_OK;
 }
 
@@ -359,13 +363,23 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
     return bail(SPOD_EUNSUPPORTED, "tensor-core kernels do not fit in shared memory for this nb");
   if (p->tensor && prop.major < 10) return bail(SPOD_EUNSUPPORTED, "tensor-core path needs an sm_100-class GPU");
 
+  // ---- which FFT kernel; whether the time mean is folded into it
+  {
+    const bool q = p->encode_fn != nullptr;
+    if (q) p->pipe_tp = fft_pipe_tile(*p, (int)prop.sharedMemPerBlockOptin);
+    p->pipe_ok = q && fft_pipe_usable(*p, (int)prop.sharedMemPerBlockOptin);
+  }
+  p->mean_fold = d->mean_in_fft && p->tensor && p->pipe_ok && !p->cplx && d->subtract_mean &&
+                 (2 * p->nb + 1 + 15) / 16 == (2 * p->nb + 15) / 16;
+  p->qrows = 2 * p->nb + (p->mean_fold ? 1 : 0);
+
   // ---- sizes of the workspace
   const size_t R = p->f64 ? 8 : 4;
   const int64_t tile = 64;
   // Qhat bytes per point: FP64/FP32 planar, or BF16 hi (+ lo for BF16X3)
   const size_t qelem = p->tensor ? 2 : R;
   const size_t nq = d->precision == SPOD_PREC_BF16X3 ? 2 : 1;
-  const size_t per_point = (size_t)p->nf * 2 * p->nb * qelem * nq;
+  const size_t per_point = (size_t)p->nf * p->qrows * qelem * nq;
   int64_t chunk = d->chunk_points;
   if (chunk == 0) {
     // whole-array Qhat up to the larger of 40 GiB and 35 % of the device memory
@@ -416,6 +430,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
   const size_t o_bimg = p->tensor ? carve(modes_image_bytes(*p)) : 0;
   const size_t o_wc = carve(2 * R * (size_t)nf);
+  const size_t o_what = carve(2 * sizeof(double) * (size_t)nf);
   // R_f of the adjoint, one column sub-chunk at a time: at most 2 GiB (real data only),
   // enough columns for several waves of the adjoint kernel's 16-point CTAs
   if (!p->cplx) {
@@ -456,20 +471,16 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   p->d_bmat = b + o_bmat;
   if (p->tensor) p->d_bimg = b + o_bimg;
   p->d_wc = b + o_wc;
+  p->d_what = reinterpret_cast<double*>(b + o_what);
   if (p->radj_points) p->d_radj = b + o_radj;
   p->d_qhat = b + o_qhat;
   if (d->precision == SPOD_PREC_BF16X3)
-    p->d_qlo = b + o_qhat + (size_t)p->nf * 2 * p->nb * 2 * (size_t)chunk;
+    p->d_qlo = b + o_qhat + (size_t)p->nf * p->qrows * 2 * (size_t)chunk;
   make_fft_store_maps(p);
-  {
-    cudaDeviceProp prop2;
-    const bool q = p->encode_fn && cudaGetDeviceProperties(&prop2, p->device) == cudaSuccess;
-    if (q) p->pipe_tp = fft_pipe_tile(*p, (int)prop2.sharedMemPerBlockOptin);
-    // the runtime-radix ring kernel handles real data only; complex data takes
-    // the pipelined kernel (compiled nfft) or the per-block one
-    p->pipe_ok = q && fft_pipe_usable(*p, (int)prop2.sharedMemPerBlockOptin);
-    p->ring_ok = p->pipe_ok || (!p->cplx && q && fft_ring_usable(*p, (int)prop2.sharedMemPerBlockOptin));
-  }
+  // the runtime-radix ring kernel (real data only, needs the store maps); complex
+  // data takes the pipelined kernel (compiled nfft) or the per-block one
+  p->ring_ok = p->pipe_ok || (!p->cplx && p->encode_fn &&
+                              fft_ring_usable(*p, (int)prop.sharedMemPerBlockOptin));
   if (p->tensor) {
     if (spod_status st = make_qhat_maps(p)) {
       std::string msg = spod_last_error();
@@ -517,6 +528,23 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
         wc[2 * f + 1] = p->c * im;
       }
       e = up(p->d_wc, wc);
+      if (e == cudaSuccess) {
+        // What_f = c sum_n w_n exp(-2 pi i f n / N) = conj(Wc_f): the DFT of
+        // the device window (c w_n) at the scale of the stored Qhat, in FP64,
+        // for the rank-one correction of the folded mean
+        std::vector<double> wh(2 * (size_t)p->nf);
+        for (int f = 0; f < p->nf; ++f) {
+          double re = 0.0, im = 0.0;
+          for (int n = 0; n < N; ++n) {
+            const double ang = 2.0 * pi * (double)(((int64_t)f * n) % N) / (double)N;
+            re += p->w[n] * std::cos(ang);
+            im -= p->w[n] * std::sin(ang);
+          }
+          wh[2 * f] = p->c * re;
+          wh[2 * f + 1] = p->c * im;
+        }
+        e = cudaMemcpy(p->d_what, wh.data(), wh.size() * sizeof(double), cudaMemcpyHostToDevice);
+      }
     }
     if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, 4 * sizeof(unsigned));
     if (e != cudaSuccess) {
@@ -566,6 +594,7 @@ spod_status spod_plan_get_info(spod_plan_t p, spod_plan_info* info) {
   info->device = p->device;
   info->workspace_bytes = p->ws.bytes;
   info->chunk_points = p->chunk_points;
+  info->mean_in_fft = p->mean_fold ? 1 : 0;
   return SPOD_OK;
 }
 
@@ -594,7 +623,7 @@ static spod_status fit_impl(spod_plan_t p, const void* d_X, cudaStream_t s, int6
   int64_t nchunks = 0;
   for (int64_t m0 = 0; m0 < p->M; m0 += w, ++nchunks) {
     const int64_t mc = std::min<int64_t>(w, p->M - m0);
-    if (p->desc.subtract_mean) {
+    if (p->desc.subtract_mean && !p->mean_fold) {
       Phase ph(p, SPOD_PHASE_MEAN, s, 2);
       SPOD_CUDA(launch_mean(*p, d_X, m0, mc, s), "mean kernel");
     }
@@ -1063,7 +1092,7 @@ spod_status spod_run_host_ooc(spod_plan_t p, const void* h_X, int nmodes, void* 
     const int64_t c0 = c * w, wc = std::min<int64_t>(w, M - c0);
     gather(c, b, use);
     p->x_off = c0;
-    if (p->desc.subtract_mean) ck(launch_mean(*p, xt[b], c0, wc, s), "mean kernel");
+    if (p->desc.subtract_mean && !p->mean_fold) ck(launch_mean(*p, xt[b], c0, wc, s), "mean kernel");
     alignas(64) CUtensorMap xmap;
     const CUtensorMap* xm = nullptr;
     if (p->ring_ok && st == SPOD_OK) {

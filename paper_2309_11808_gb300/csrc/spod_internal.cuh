@@ -29,11 +29,14 @@ constexpr int kEigSmemMaxNb = 48;      // eigen-solver keeps A and V in shared m
 // tensor-core path are blocked by kQBlock points, [chunk / kQBlock][nf][2 nb]
 // [kQBlock]: the rows that one spatial tile contributes to every frequency lie
 // within a few MB (a handful of pages, whatever the chunk size), and the
-// K step of one frequency is a single contiguous 2 nb x 128-byte box for the
-// tensor-core kernels.  Rows are re = l, im = nb + l for Welch block l.
+// K step of one frequency is a single contiguous qrows x 128-byte box for the
+// tensor-core kernels.  Rows are re = l, im = nb + l for Welch block l; when
+// the time mean is folded into the FFT (spod_plan_s::mean_fold) one more row,
+// 2 nb, holds rho_m = sqrt(W_m) (mu_m - x_m(t = 0)) of every point (qrows =
+// 2 nb + 1), the input of the rank-one mean correction of the consumers.
 constexpr int kQBlock = 64;
-__host__ __device__ inline int64_t qhat_blocked_offset(int nf, int nb, int f, int row, int64_t m) {
-  return (((m / kQBlock) * nf + f) * 2 * nb + row) * kQBlock + (m % kQBlock);
+__host__ __device__ inline int64_t qhat_blocked_offset(int nf, int qrows, int f, int row, int64_t m) {
+  return (((m / kQBlock) * nf + f) * qrows + row) * kQBlock + (m % kQBlock);
 }
 
 struct FftPlan {
@@ -84,6 +87,13 @@ struct spod_plan_s {
   // starting at point phi_off (0, 0: the full arrays, row stride M).
   int64_t x_ld = 0, x_off = 0, phi_ld = 0, phi_off = 0;
   bool pipe_ok = false;       // the pipelined kernel (compiled nfft) is used
+  // The time mean folded into the pipelined FFT (real data, tensor-core
+  // precisions, 2 nb + 1 rows within the 16-row MMA padding of 2 nb): the FFT
+  // subtracts each column's first sample, accumulates the mean of the rest,
+  // writes mu and the rho row; the Gram and the modes apply the exact rank-one
+  // correction Qhat = Z - mu' What_f.  No separate mean pass reads X.
+  bool mean_fold = false;
+  int qrows = 0;              // Qhat rows per frequency: 2 nb (+ 1 with mean_fold)
   int pipe_tp = 16;           // its tile width in points (16 or 32; also the X map's box width)
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   int num_sms = 0;
@@ -118,6 +128,7 @@ struct spod_plan_s {
   void* d_bimg = nullptr;          // tensor path: per-frequency BF16 B images of the mode GEMM
   void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa), or G_f
   void* d_wc = nullptr;            // [nf] complex compute type: c sum_n w_n e^{+2 pi i f n / nfft}
+  double* d_what = nullptr;        // [nf] complex FP64: What_f = c sum_n w_n e^{-2 pi i f n / nfft} (mean fold)
   void* d_radj = nullptr;          // [nf][nb][radj_points] complex compute type: R_f of the adjoint, one column sub-chunk
   int64_t radj_points = 0;         // points per adjoint sub-chunk (a multiple of 128; 0: no adjoint, complex data)
   unsigned* d_flags = nullptr;     // [4]: [0] condition bits (cleared per fit), [1] wait bound in us
@@ -203,7 +214,8 @@ bool fft_ring_usable(const spod_plan_s& p, int smem_optin);
 size_t fft_pipe_smem_bytes(const spod_plan_s& p, int tp);
 bool fft_pipe_usable(const spod_plan_s& p, int smem_optin);
 int fft_pipe_tile(const spod_plan_s& p, int smem_optin);
-cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
+cudaError_t launch_fft_pipe_chunk(const spod_plan_s& p, const CUtensorMap& xmap, const void* d_X, int64_t m0,
+                                  int64_t mcount,
                                   cudaStream_t s);
 cudaError_t launch_fft_ring_chunk(const spod_plan_s& p, const CUtensorMap& xmap, int64_t m0, int64_t mcount,
                                   cudaStream_t s);

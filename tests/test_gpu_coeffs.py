@@ -25,11 +25,13 @@ def _built():
 from paper_2309_11808_gb300 import SPOD, SpodError, _lib  # noqa: E402
 
 
-def _run(prec, dtype, fsel, nmodes_r, npts=48 * 16, nt=2048, nfft=128, nmodes=4):
+def _run(prec, dtype, fsel, nmodes_r, npts=48 * 16, nt=2048, nfft=128, nmodes=4, expect_fold=None):
     W = 0.5 + torch.rand(npts, generator=torch.Generator().manual_seed(3), dtype=torch.float64)
     wl = planted(npts, 1, nt, nfft, nfft // 2, bins=(6, 13, 30), amps=(3.0, 2.0, 1.0), noise_std=0.2,
                  weights=W, seed=5, dtype=dtype, offset=0.4 + 0.1 * torch.rand(npts, dtype=torch.float64))
     sp = SPOD(npts, 1, nt, nfft, nfft // 2, dtype=dtype, precision=prec, weights=W)
+    if expect_fold is not None:
+        assert sp.mean_in_fft == expect_fold
     X = wl.X.to(DEV).contiguous()
     sp.fit(X)
     Phi = sp.modes(X, nmodes)
@@ -60,6 +62,16 @@ def test_coefficients_and_reconstruction_match_the_oracle(prec, dtype, tol):
     assert np.abs(Xr - Xref).max() <= tol * np.abs(X).max()
     # the planted bins dominate the reconstruction: the residual is mostly noise
     assert np.abs(Xr - X).std() < np.abs(X - X.mean(axis=0)).std()
+
+
+@cuda
+def test_coefficients_and_reconstruction_with_the_mean_in_the_fft():
+    # bf16x3 plan at nfft 256 (nb = 15): the time mean is taken inside the FFT
+    # pass, and the reconstruction adds it back; modes from the tensor cores
+    fsel = [0, 6, 13, 30, 128]
+    A, Aref, Xr, Xref, X = _run("bf16x3", torch.float32, fsel, 2, nfft=256, expect_fold=True)
+    assert np.abs(A - Aref).max() <= 1e-4 * np.abs(Aref).max()
+    assert np.abs(Xr - Xref).max() <= 1e-4 * np.abs(X).max()
 
 
 @cuda

@@ -30,10 +30,14 @@ WIN = {"hamming": O.WIN_HAMMING, "hamming_periodic": O.WIN_HAMMING_PERIODIC, "ha
 
 
 def run_both(X, npts, nvars, nfft, nov, prec, nmodes=None, W=None, window="hamming", norm="nb",
-             subtract_mean=True, chunk_points=0, dft="direct", user_window=None):
+             subtract_mean=True, chunk_points=0, dft="direct", user_window=None, mean_in_fft=True,
+             expect_fold=None):
     nt, M = X.shape
     sp = SPOD(npts, nvars, nt, nfft, nov, dtype=X.dtype, precision=prec, weights=W, window=window,
-              norm=norm, subtract_mean=subtract_mean, chunk_points=chunk_points, user_window=user_window)
+              norm=norm, subtract_mean=subtract_mean, chunk_points=chunk_points, user_window=user_window,
+              mean_in_fft=mean_in_fft)
+    if expect_fold is not None:
+        assert sp.mean_in_fft == expect_fold
     Xd = X.to(DEV).contiguous()
     sp.fit(Xd)
     lam, psi = sp.eigs(vectors=True)
@@ -427,8 +431,9 @@ def test_tensor_path_chunked_matches_single_pass(nfft):
     a = run_both(wl.X, wl.npoints, 2, nfft, nfft // 2, "bf16x3", W=wl.W.numpy(), nmodes=3, dft="fft")
     b = run_both(wl.X, wl.npoints, 2, nfft, nfft // 2, "bf16x3", W=wl.W.numpy(), nmodes=3, dft="fft",
                  chunk_points=128)
-    for r in (a, b):
-        ok, vals = small_field_gate(r["lam"], r["ref"].lam, 1e-5)
+    res = [small_field_gate(r["lam"], r["ref"].lam, 1e-5) for r in (a, b)]
+    print("single pass", res[0], "chunked", res[1])
+    for ok, vals in res:
         assert ok, vals
     # chunking changes only the FP32 accumulation order
     la, lb = a["lam"], b["lam"]
@@ -522,4 +527,79 @@ def test_complex_input_pipelined_fft(prec, nfft):
     assert ok, vals
     assert mode_err(Phi, ref, d, W, 2, cond=10.0) <= 1e-4
     assert lam[nfft - 17, 0] > 10 * lam[17, 0]
+    sp.close()
+
+
+# ---------------------------------------------------------------- time mean in the FFT pass
+def _trended(wl, seed, offset=3.0, drift=1.0):
+    """The workload plus a per-column offset and a linear drift over the record
+    (the time mean then sits far from zero and from the first snapshots)."""
+    g = torch.Generator().manual_seed(seed)
+    nt, M = wl.X.shape
+    a = offset * (1.0 + torch.rand(M, generator=g, dtype=torch.float64))
+    b = drift * (2.0 * torch.rand(M, generator=g, dtype=torch.float64) - 1.0)
+    t = torch.arange(nt, dtype=torch.float64)[:, None] / nt
+    return (wl.X.double() + a[None, :] + b[None, :] * t).to(wl.X.dtype)
+
+
+FOLD_CASES = [
+    # (nx, nr, nvars, nt, nfft, noverlap, in dtype): ragged M, a tail of snapshots in no block
+    (43, 16, 2, 3000, 256, 128, torch.float32),      # nb 22, tail 56, 1376 points (ragged tile)
+    (40, 16, 1, 4000, 384, 192, torch.float32),      # nb 19, tail 160 (radix-3 pass, separate sum loop)
+    (24, 16, 1, 5000, 720, 360, torch.float32),      # nb 12, tail 320 (16-point tiles)
+    (32, 16, 1, 4700, 512, 0, torch.float32),        # no overlap: every block is all new snapshots
+    (32, 16, 1, 3000, 256, 192, torch.float32),      # 3/4 overlap: nb 43
+    (29, 16, 2, 2600, 256, 128, torch.bfloat16),     # BF16-stored snapshots
+]
+
+
+@cuda
+@pytest.mark.parametrize("case", FOLD_CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}_nt{c[3]}_n{c[4]}_ov{c[5]}_"
+                                                   f"{str(c[6]).split('.')[-1]}" for c in FOLD_CASES])
+def test_mean_in_fft_matches_the_oracle(case):
+    # the folded mean (centre, sums over new rows and the tail, rho row,
+    # rank-one correction in the Gram finish and the mode image) against the
+    # oracle, on data whose mean is far from zero and drifts
+    nx, nr, nv, nt, nfft, nov, dt = case
+    wl = jet_like(nx=nx, nr=nr, nvars=nv, nt=nt, nfft=nfft, noverlap=nov, seed=41 + nfft, dtype=torch.float32)
+    X = _trended(wl, 7).to(dt)
+    r = run_both(X, wl.npoints, nv, nfft, nov, "bf16x3", W=wl.W.numpy(), dft="fft", expect_fold=True)
+    ok, vals = small_field_gate(r["lam"], r["ref"].lam, 1e-5)
+    print(case, "fold: leading-5 rel err (cond <= 10) %.2e, normwise %.2e, all %.2e" % vals)
+    assert ok, vals
+    assert mode_err(r["Phi"], r["ref"], r["desc"], wl.W.numpy(), r["lam"].shape[1], cond=100.0) <= 1e-4
+
+
+@cuda
+def test_mean_in_fft_equals_the_separate_mean_pass():
+    # the two ways of removing the mean agree to the bf16x3 representation
+    # error, also at the low bins where the correction acts (f = 0, 1)
+    wl = jet_like(nx=48, nr=16, nvars=2, nt=3000, nfft=256, seed=52, dtype=torch.float32)
+    X = _trended(wl, 9, offset=10.0, drift=2.0)
+    a = run_both(X, wl.npoints, 2, 256, 128, "bf16x3", W=wl.W.numpy(), dft="fft", expect_fold=True)
+    b = run_both(X, wl.npoints, 2, 256, 128, "bf16x3", W=wl.W.numpy(), dft="fft", mean_in_fft=False,
+                 expect_fold=False)
+    for r in (a, b):
+        ok, vals = small_field_gate(r["lam"], r["ref"].lam, 1e-5)
+        assert ok, vals
+    ref = a["ref"].lam
+    low = np.abs(a["lam"][:2, :5] - ref[:2, :5]) / ref[:2, :1]
+    print("fold, bins 0-1: max |dlambda| / lambda_1 = %.2e" % low.max())
+    assert low.max() <= 1e-5
+    scale = np.abs(a["ref"].M).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(a["gram"] - b["gram"]) / scale).max() <= 2e-5
+
+
+@cuda
+def test_mean_in_fft_not_taken_where_it_does_not_fit():
+    # 2 nb a multiple of 16 (no padding row for rho), FP32 arithmetic, complex
+    # data, or subtract_mean = 0: the separate mean pass (or none)
+    nt = 256 + 15 * 128                              # nb = 16 for nfft 256, 50 % overlap
+    assert O.n_blocks(nt, 256, 128) == 16
+    for prec, kw in (("bf16x3", {}), ("fp32", {}), ("bf16x3", {"subtract_mean": False})):
+        sp = SPOD(64, 1, 3000 if kw else nt, 256, 128, precision=prec, **kw)
+        assert not sp.mean_in_fft
+        sp.close()
+    sp = SPOD(64, 1, 3000, 256, 128, precision="bf16x3")
+    assert sp.mean_in_fft
     sp.close()
