@@ -351,6 +351,11 @@ typedef struct {
                              plans) leaves its first pipeline stage unfilled, so the waits on it run
                              out after wait_timeout_us and the fit reports SPOD_ETIMEOUT; 0 (default):
                              off.  No other effect. */
+  int fft_tile_points;    /* pipelined FFT (compiled nfft): spatial points per CTA tile, 16 (two CTAs
+                             per SM up to nfft 512) or 32 (one CTA per SM, whole 128-byte rows); the
+                             plan picks 32 where it fits in shared memory.  0 on read: the plan does
+                             not use the pipelined FFT; 0 on write: leave as is.  Changes only the
+                             launch shape, not the results. */
 } spod_tuning;
 
 /* The plan's launch shape into *tuning (host).  No counterpart in the paper. */
@@ -361,9 +366,10 @@ spod_status spod_plan_get_tuning(spod_plan_t plan, spod_tuning* tuning);
 spod_status spod_plan_set_tuning(spod_plan_t plan, const spod_tuning* tuning);
 
 /* Autotuner: runs spod_fit on d_X (device, as spod_fit) under candidate
- * launch shapes (the Gram's CTA split: persistent CTAs per GPU for the
- * tensor-core path, CTAs per frequency for the SIMT path), times each with
- * CUDA events on `stream` and keeps the fastest; gram_flush_blocks, which
+ * launch shapes (the pipelined FFT's tile width, 16 or 32 points, where both
+ * have a compiled form that fits; then the Gram's CTA split: persistent CTAs
+ * per GPU for the tensor-core path, CTAs per frequency for the SIMT path),
+ * times each with CUDA events on `stream` and keeps the fastest; gram_flush_blocks, which
  * changes rounding, is not searched.  Synchronises the stream; the plan holds
  * the last fit's results afterwards.  chosen (may be NULL) receives the
  * tuning kept.  No counterpart in the paper (an engineering aid). */

@@ -49,7 +49,7 @@ class spod_plan_info(C.Structure):
 class spod_tuning(C.Structure):
     _fields_ = [("gram_splits", C.c_int), ("gram_splits_max", C.c_int), ("gram_flush_blocks", C.c_int),
                 ("modes_ctas", C.c_int), ("eig_max_iter", C.c_int), ("wait_timeout_us", C.c_int),
-                ("wait_selftest", C.c_int)]
+                ("wait_selftest", C.c_int), ("fft_tile_points", C.c_int)]
 
 
 class SpodError(RuntimeError):
@@ -251,9 +251,10 @@ def spod_plan_get_tuning(plan: int) -> spod_tuning:
 
 
 def spod_plan_set_tuning(plan: int, gram_splits: int = 0, gram_flush_blocks: int = 0, modes_ctas: int = 0,
-                         eig_max_iter: int = 0, wait_timeout_us: int = 0, wait_selftest: int = 0) -> None:
+                         eig_max_iter: int = 0, wait_timeout_us: int = 0, wait_selftest: int = 0,
+                         fft_tile_points: int = 0) -> None:
     t = spod_tuning(int(gram_splits), 0, int(gram_flush_blocks), int(modes_ctas), int(eig_max_iter),
-                    int(wait_timeout_us), int(wait_selftest))
+                    int(wait_timeout_us), int(wait_selftest), int(fft_tile_points))
     check(lib().spod_plan_set_tuning(plan, C.byref(t)), "spod_plan_set_tuning")
 
 

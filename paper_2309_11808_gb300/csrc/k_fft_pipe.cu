@@ -345,6 +345,173 @@ __device__ __forceinline__ void output_phase(const float2* __restrict__ src, con
   }
 }
 
+// ---------------------------------------------------------------- nfft = 512 in two passes
+// n = 32 n1 + n2, k = k1 + 16 k2:
+//   X[k1 + 16 k2] = sum_n2 W32^(n2 k2) W512^(n2 k1) sum_n1 x[32 n1 + n2] W16^(n1 k1).
+// Pass A: thread (column, n2) takes its 16 samples from the ring, a 16-point
+// DFT in registers, the twiddle W512^(n2 k1), and stores Y[k1][n2].  Pass B:
+// thread (column, k1, h) takes Y[k1][2m + h], m < 16, and a 16-point DFT
+// gives U_h[k1][k2] (k2 < 16); the remaining radix-2 step,
+//   X[k1 + 16 k2] = U_0 + W32^k2 U_1,  X[k1 + 16 (k2 + 16)] = U_0 - W32^k2 U_1,
+// is taken by the output phase, which needs X[f], X[N - f], X[256 - f] and
+// X[256 + f] together anyway to separate the two real series of a column.
+// Per element: one ring read, two shared-memory writes and two reads (the
+// three-pass form: three writes and three reads), two barriers per block.
+
+// 16-point forward DFT in registers (radix 4 x 4).
+__device__ __forceinline__ void dft16(float2* v) {
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, r2 = 0.70710678118654752440f;
+  float2 a[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2 t[4] = {v[q], v[q + 4], v[q + 8], v[q + 12]};
+    dft_small<4, float2, float>(t);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[q][r] = t[r];
+  }
+  // a[q][r] *= W16^(q r)
+  const float2 w1 = make_float2(c1, -s1), w3 = make_float2(s1, -c1), w9 = make_float2(-c1, s1);
+  a[1][1] = cmul(a[1][1], w1);
+  a[1][2] = make_float2(r2 * (a[1][2].x + a[1][2].y), r2 * (a[1][2].y - a[1][2].x));   // W^2
+  a[1][3] = cmul(a[1][3], w3);
+  a[2][1] = make_float2(r2 * (a[2][1].x + a[2][1].y), r2 * (a[2][1].y - a[2][1].x));   // W^2
+  a[2][2] = mul_mi(a[2][2]);                                                            // W^4
+  a[2][3] = make_float2(r2 * (a[2][3].y - a[2][3].x), -r2 * (a[2][3].x + a[2][3].y));  // W^6
+  a[3][1] = cmul(a[3][1], w3);
+  a[3][2] = make_float2(r2 * (a[3][2].y - a[3][2].x), -r2 * (a[3][2].x + a[3][2].y));  // W^6
+  a[3][3] = cmul(a[3][3], w9);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    float2 t[4] = {a[0][r], a[1][r], a[2][r], a[3][r]};
+    dft_small<4, float2, float>(t);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[r + 4 * q] = t[q];
+  }
+}
+
+// Pass A (see above).  With FOLD the samples n1 >= n1thr (a block-uniform
+// bound) are also summed into acc0 / acc1.
+template <typename Tin, int TP, bool FOLD>
+__device__ __forceinline__ void pass_a512(const Tin* __restrict__ ring, int rb, float2* __restrict__ dst,
+                                          const float* __restrict__ wsm, const float2* __restrict__ tw, float mhi0,
+                                          float mlo0, float mhi1, float mlo1, int n1thr, float& acc0,
+                                          float& acc1) {
+  constexpr int N = 512, PTP = Geo<TP>::PTP, PC = Geo<TP>::PC;
+  const int col = threadIdx.x % PC;
+  const int n2 = threadIdx.x / PC;
+  float2 v[16];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) {
+    const int n = 32 * n1 + n2;
+    int slot = rb + n;
+    if (slot >= N) slot -= N;
+    const float2 x = PairLoad<Tin>::get(ring + slot * PTP + 2 * col);
+    const float wn = wsm[n];
+    const float d0 = (x.x - mhi0) - mlo0, d1 = (x.y - mhi1) - mlo1;
+    if (FOLD && n1 >= n1thr) {
+      acc0 += d0;
+      acc1 += d1;
+    }
+    v[n1] = make_float2(d0 * wn, d1 * wn);
+  }
+  dft16(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) dst[(k1 * 32 + n2) * PC + col] = v[k1];
+}
+
+// Pass B (see above): U_h[k1][k2] at row (h * 16 + k1) * 16 + k2.
+template <int TP>
+__device__ __forceinline__ void pass_b512(const float2* __restrict__ src, float2* __restrict__ dst) {
+  constexpr int PC = Geo<TP>::PC;
+  const int col = threadIdx.x % PC;
+  const int j = threadIdx.x / PC;
+  const int k1 = j >> 1, h = j & 1;
+  float2 v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) v[m] = src[(k1 * 32 + 2 * m + h) * PC + col];
+  dft16(v);
+  const int base = (h * 16 + k1) * 16;
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) dst[(base + k2) * PC + col] = v[k2];
+}
+
+// Store the one-sided spectra of the four points of column pair cp at bin f
+// from z = X[f] and zc = X[N - f] of its two complex columns (float4 = two
+// columns): the even point of a column is (z + conj zc) / 2, the odd one
+// (z - conj zc) / 2i; sw carries sqrt(W) / 2.
+template <int OUTK>
+__device__ __forceinline__ void store_bin4(const float4 z, const float4 zc, const float (&sw)[4], const PipeArgs& a,
+                                           int f, int l, int64_t lm, void* __restrict__ qout,
+                                           void* __restrict__ qlo) {
+  const float r0 = (z.x + zc.x) * sw[0], i0 = (z.y - zc.y) * sw[0];
+  const float r1 = (z.y + zc.y) * sw[1], i1 = (zc.x - z.x) * sw[1];
+  const float r2 = (z.z + zc.z) * sw[2], i2 = (z.w - zc.w) * sw[2];
+  const float r3 = (z.w + zc.w) * sw[3], i3 = (zc.z - z.z) * sw[3];
+  if constexpr (OUTK == OUT_NATIVE) {
+    float* q = static_cast<float*>(qout);
+    const int64_t o = ((int64_t)f * 2 * a.nb + l) * a.chunk + lm;
+    *reinterpret_cast<float4*>(q + o) = make_float4(r0, r1, r2, r3);
+    *reinterpret_cast<float4*>(q + o + (int64_t)a.nb * a.chunk) = make_float4(i0, i1, i2, i3);
+  } else {
+    const int64_t o = qhat_blocked_offset(a.nf, a.qrows, f, l, lm);
+    const int64_t imoff = (int64_t)a.nb * kQBlock;
+    __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
+    const uint32_t hr01 = pack_bf16x2(r0, r1), hr23 = pack_bf16x2(r2, r3);
+    const uint32_t hi01 = pack_bf16x2(i0, i1), hi23 = pack_bf16x2(i2, i3);
+    *reinterpret_cast<uint2*>(qh + o) = make_uint2(hr01, hr23);
+    *reinterpret_cast<uint2*>(qh + o + imoff) = make_uint2(hi01, hi23);
+    if constexpr (OUTK == OUT_BF16X3) {
+      __nv_bfloat16* ql = static_cast<__nv_bfloat16*>(qlo);
+      const uint32_t lr01 = pack_bf16x2(r0 - bf16_lo_f(hr01), r1 - bf16_hi_f(hr01));
+      const uint32_t lr23 = pack_bf16x2(r2 - bf16_lo_f(hr23), r3 - bf16_hi_f(hr23));
+      const uint32_t li01 = pack_bf16x2(i0 - bf16_lo_f(hi01), i1 - bf16_hi_f(hi01));
+      const uint32_t li23 = pack_bf16x2(i2 - bf16_lo_f(hi23), i3 - bf16_hi_f(hi23));
+      *reinterpret_cast<uint2*>(ql + o) = make_uint2(lr01, lr23);
+      *reinterpret_cast<uint2*>(ql + o + imoff) = make_uint2(li01, li23);
+    }
+  }
+}
+
+__device__ __forceinline__ float4 c2add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 c2sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+// both complex columns of a float4 times w
+__device__ __forceinline__ float4 c2mul(float4 a, float2 w) {
+  return make_float4(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x, a.z * w.x - a.w * w.y, a.z * w.y + a.w * w.x);
+}
+
+// Output phase of the two-pass form: item j = f in [0, 128] of column pair cp
+// gives bins f and 256 - f.  With (k1, k2) = (f mod 16, f / 16) and the
+// partner (k1', k2') = ((16 - k1) mod 16, k1 ? 15 - k2 : (16 - k2) mod 16):
+//   P = U_0[k1][k2] + W32^k2 U_1[k1][k2] = X[f],  P' = U_0 - W32^k2 U_1 = X[256 + f]
+//   Q = U_0[k1'][k2'] -/+ W32^k2' U_1[k1'][k2'] = X[N - f],  the other sign X[256 - f]
+// (the signs swap at f = 0, where the partner is the item itself).
+template <int OUTK, int TP>
+__device__ __forceinline__ void output_phase_512(const float2* __restrict__ U, const float2* __restrict__ tw,
+                                                 const PipeArgs& a, int l, int64_t lm0, const float (&sw)[4],
+                                                 void* __restrict__ qout, void* __restrict__ qlo) {
+  constexpr int kOutCp = Geo<TP>::OUTCP, kItems = Geo<TP>::THREADS / kOutCp;
+  const int cp = threadIdx.x % kOutCp;
+  const float4* U4 = reinterpret_cast<const float4*>(U);
+  const int64_t lm = lm0 + 4 * cp;
+  for (int j = threadIdx.x / kOutCp; j <= 128; j += kItems) {
+    const int k1 = j & 15, k2 = j >> 4;
+    const int k1p = (16 - k1) & 15;
+    const int k2p = k1 ? 15 - k2 : (16 - k2) & 15;
+    const float4 u0 = U4[(k1 * 16 + k2) * kOutCp + cp];
+    const float4 u1 = c2mul(U4[((16 + k1) * 16 + k2) * kOutCp + cp], tw[16 * k2]);
+    const float4 v0 = U4[(k1p * 16 + k2p) * kOutCp + cp];
+    const float4 v1 = c2mul(U4[((16 + k1p) * 16 + k2p) * kOutCp + cp], tw[16 * k2p]);
+    const float4 xf = c2add(u0, u1);                 // X[f]
+    const float4 xf256 = c2sub(u0, u1);              // X[256 + f]
+    const float4 xnf = j ? c2sub(v0, v1) : c2add(v0, v1);     // X[N - f]
+    const float4 xg = j ? c2add(v0, v1) : c2sub(v0, v1);      // X[256 - f]
+    store_bin4<OUTK>(xf, xnf, sw, a, j, l, lm, qout, qlo);
+    if (j != 128) store_bin4<OUTK>(xg, xf256, sw, a, 256 - j, l, lm, qout, qlo);
+  }
+}
+
 // Shared-memory layout (bytes from the 1024-aligned base).
 template <typename Tin, int TP, int N>
 struct PipeLayout {
@@ -451,6 +618,8 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
   // while tile t runs (pc0 / pc1) and reduced at its end.
   constexpr bool FOLDK = !CPLX && OUTK != OUT_NATIVE;
   const bool fold = FOLDK && a.fold;
+  // real data at nfft = 512: the two-pass form (16 x 32, last radix 2 in the output phase)
+  constexpr bool TWO = N == 512 && !CPLX;
   constexpr int PB = Geo<TP>::BSTEP;
   const int b0 = tid / PC;
   const Tin* const xg = static_cast<const Tin*>(a.xg);
@@ -533,12 +702,17 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
         // N / R0 (50 % overlap, none, 75 %, ...) they are the elements
         // r >= (N - step) / (N / R0) of every first-pass butterfly, otherwise
         // a separate loop re-reads them from the ring.
-        constexpr int NBUT = N / S::R0;
+        // (two-pass nfft = 512: the samples n1 >= (N - step) / 32 of pass A)
+        constexpr int NBUT = TWO ? 32 : N / S::R0;
+        constexpr int NGRP = TWO ? 16 : S::R0;
         const int nnew0 = !fold ? N : l == 0 ? 0 : N - a.step;
         const bool in_pass = nnew0 % NBUT == 0;
-        const int rthr = fold && in_pass ? nnew0 / NBUT : S::R0;
+        const int rthr = fold && in_pass ? nnew0 / NBUT : NGRP;
         float s0 = 0.f, s1 = 0.f;
-        pass_first<Tin, TP, N, S::R0, FOLDK>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1, rthr, s0, s1);
+        if constexpr (TWO)
+          pass_a512<Tin, TP, FOLDK>(ring, rb, bA, wsm, tw, mhi0, mlo0, mhi1, mlo1, rthr, s0, s1);
+        else
+          pass_first<Tin, TP, N, S::R0, FOLDK>(ring, rb, bA, wsm, mhi0, mlo0, mhi1, mlo1, rthr, s0, s1);
         if (fold) {
           if (!in_pass) {
             for (int n = nnew0 + tid / PC; n < N; n += Geo<TP>::BSTEP) {
@@ -567,12 +741,21 @@ __global__ void __launch_bounds__(Geo<TP>::THREADS, pipe_min_blocks<TP, N>()) k_
           if (a.nb > 1) prefetch(t + t_step, N, a.step);
         }
       }
-      const float2* spec = S::template rest<TP>(bA, bB, tw);
-      if constexpr (CPLX) output_phase_cplx<OUTK, TP, N>(spec, a, l, lm0 / 2, sw, qout, qlo);
-      else output_phase<OUTK, TP, N>(spec, a, l, lm0, sw, qout, qlo);
+      if constexpr (TWO) {
+        // pass B writes bB, which the previous block's output phase read: every
+        // thread has passed the barrier above since
+        pass_b512<TP>(bA, bB);
+        __syncthreads();
+        output_phase_512<OUTK, TP>(bB, tw, a, l, lm0, sw, qout, qlo);
+        // the next block's pass A writes bA, which nobody reads after pass B
+      } else {
+        const float2* spec = S::template rest<TP>(bA, bB, tw);
+        if constexpr (CPLX) output_phase_cplx<OUTK, TP, N>(spec, a, l, lm0 / 2, sw, qout, qlo);
+        else output_phase<OUTK, TP, N>(spec, a, l, lm0, sw, qout, qlo);
+        par ^= (S::P & 1);
+      }
       rb += a.step;
       if (rb >= N) rb -= N;
-      par ^= (S::P & 1);
     }
     if (hdr->abort) break;
     if (fold) {

@@ -1213,6 +1213,7 @@ spod_status spod_plan_get_tuning(spod_plan_t p, spod_tuning* t) {
   t->eig_max_iter = p->eig_max_iter;
   t->wait_timeout_us = p->wait_timeout_us;
   t->wait_selftest = p->wait_selftest;
+  t->fft_tile_points = p->pipe_ok ? p->pipe_tp : 0;
   return SPOD_OK;
 }
 
@@ -1227,6 +1228,16 @@ spod_status spod_plan_set_tuning(spod_plan_t p, const spod_tuning* t) {
   if (t->wait_timeout_us < 0 || t->wait_timeout_us > 4000000)
     return fail(SPOD_EINVAL, "wait_timeout_us must be in 0..4000000");
   if (t->wait_selftest < 0 || t->wait_selftest > 1) return fail(SPOD_EINVAL, "wait_selftest must be 0 or 1");
+  if (t->fft_tile_points != 0 && (p->pipe_ok ? t->fft_tile_points != p->pipe_tp : true)) {
+    if (!p->pipe_ok) return fail(SPOD_EINVAL, "fft_tile_points: this plan does not use the pipelined FFT");
+    if (t->fft_tile_points != 16 && t->fft_tile_points != 32)
+      return fail(SPOD_EINVAL, "fft_tile_points must be 16 or 32");
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const size_t sm = fft_pipe_smem_bytes(*p, t->fft_tile_points);
+    if (sm == 0 || sm > (size_t)optin)
+      return fail(SPOD_EINVAL, "fft_tile_points: no form of the pipelined FFT with that tile for this plan");
+  }
   if (t->wait_timeout_us != p->wait_timeout_us) {
     DeviceGuard g(p->device);
     const unsigned us = (unsigned)t->wait_timeout_us;
@@ -1238,6 +1249,7 @@ spod_status spod_plan_set_tuning(spod_plan_t p, const spod_tuning* t) {
   p->modes_ctas = t->modes_ctas;
   p->eig_max_iter = t->eig_max_iter;
   p->wait_selftest = t->wait_selftest;
+  if (t->fft_tile_points) p->pipe_tp = t->fft_tile_points;
   ++p->version;
   return SPOD_OK;
 }
@@ -1374,9 +1386,10 @@ spod_status spod_fit_batch(spod_plan_t* plans, const void* const* d_X, int n, vo
 }
 
 // ---- spod_plan_autotune: time spod_fit under candidate launch shapes on
-// the caller's input and keep the fastest.  Only how work is split across
-// CTAs is searched; the FP32 accumulation interval (gram_flush_blocks),
-// which changes rounding, is left as it is.
+// the caller's input and keep the fastest: the pipelined FFT's tile width,
+// then the Gram's CTA count.  Only how work is split across CTAs is
+// searched; the FP32 accumulation interval (gram_flush_blocks), which
+// changes rounding, is left as it is.
 spod_status spod_plan_autotune(spod_plan_t p, const void* d_X, void* stream, spod_tuning* chosen) {
   if (spod_status st = check_plan(p)) return st;
   if (spod_status st = check_ptr(d_X, "d_X")) return st;
@@ -1394,31 +1407,59 @@ spod_status spod_plan_autotune(spod_plan_t p, const void* d_X, void* stream, spo
   }
   std::sort(cand.begin(), cand.end());
   cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-  const int keep_splits = p->gram_splits;
+  // FFT tile widths with a compiled form that fits (pipelined FFT only)
+  std::vector<int> tiles;
+  if (p->pipe_ok) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    for (int tp : {16, 32}) {
+      const size_t sm = fft_pipe_smem_bytes(*p, tp);
+      if (sm > 0 && sm <= (size_t)optin) tiles.push_back(tp);
+    }
+  }
+  const int keep_splits = p->gram_splits, keep_tp = p->pipe_tp;
   const int prof = p->prof;
   p->prof = 0;
   cudaEvent_t e0, e1;
   SPOD_CUDA(cudaEventCreate(&e0), "event");
   SPOD_CUDA(cudaEventCreate(&e1), "event");
-  float best = 1e30f;
-  int best_c = keep_splits;
   spod_status st = SPOD_OK;
-  for (int c : cand) {
-    p->gram_splits = c;
-    st = spod_fit(p, d_X, stream);                       // warm-up
-    if (st != SPOD_OK) break;
+  // one warm-up fit, then two timed ones
+  auto time_fit = [&](float& ms) -> spod_status {
+    if (spod_status r = spod_fit(p, d_X, stream)) return r;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 2 && st == SPOD_OK; ++r) st = spod_fit(p, d_X, stream);
+    for (int r = 0; r < 2; ++r)
+      if (spod_status q = spod_fit(p, d_X, stream)) return q;
     cudaEventRecord(e1, s);
-    if (st != SPOD_OK) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune timing"); break; }
-    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune timing");
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_c = c; }
+    return SPOD_OK;
+  };
+  // the FFT tile first (at the current Gram split), then the Gram split
+  float best = 1e30f;
+  int best_tp = keep_tp;
+  for (int tp : tiles) {
+    if (st != SPOD_OK) break;
+    p->pipe_tp = tp;
+    ++p->version;
+    float ms = 0.f;
+    st = time_fit(ms);
+    if (st == SPOD_OK && ms < best) { best = ms; best_tp = tp; }
+  }
+  p->pipe_tp = st == SPOD_OK ? best_tp : keep_tp;
+  best = 1e30f;
+  int best_c = keep_splits;
+  for (int c : cand) {
+    if (st != SPOD_OK) break;
+    p->gram_splits = c;
+    float ms = 0.f;
+    st = time_fit(ms);
+    if (st == SPOD_OK && ms < best) { best = ms; best_c = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->gram_splits = st == SPOD_OK ? best_c : keep_splits;
+  if (st != SPOD_OK) p->pipe_tp = keep_tp;
   p->prof = prof;
   ++p->version;
   if (st != SPOD_OK) return st;

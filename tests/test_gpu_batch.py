@@ -94,6 +94,7 @@ def test_autotune_keeps_results(prec):
     lam0 = sp.eigs()
     t = _lib.spod_plan_autotune(sp.handle, wl.X, torch.cuda.current_stream())
     assert 1 <= t.gram_splits <= t.gram_splits_max
+    assert t.fft_tile_points in ((16, 32) if _lib.spod_plan_get_tuning(sp.handle).fft_tile_points else (0,))
     sp.fit(wl.X)
     lam1 = sp.eigs()
     # only the grouping of partial sums may change

@@ -603,3 +603,34 @@ def test_mean_in_fft_not_taken_where_it_does_not_fit():
     sp = SPOD(64, 1, 3000, 256, 128, precision="bf16x3")
     assert sp.mean_in_fft
     sp.close()
+
+
+@cuda
+@pytest.mark.parametrize("prec,nfft", [("bf16x3", 512), ("fp32", 512), ("bf16x3", 256)])
+def test_fft_tile_width_changes_only_the_launch_shape(prec, nfft):
+    # the pipelined FFT with 16- and 32-point tiles: every column goes through
+    # the same arithmetic, so the spectra, Gram and eigenvalues agree to the
+    # last bits (the two forms are separate compilations)
+    wl = jet_like(nx=24, nr=16, nvars=2, nt=6 * nfft, nfft=nfft, seed=71, dtype=torch.float32)
+    X = _trended(wl, 3).to(DEV).contiguous()
+    sp = SPOD(wl.npoints, 2, X.shape[0], nfft, nfft // 2, precision=prec, weights=wl.W)
+    t0 = _lib.spod_plan_get_tuning(sp.handle)
+    assert t0.fft_tile_points in (16, 32)
+    sp.fit(X)
+    lam_a, gram_a = sp.eigs(), sp.gram()
+    other = 16 if t0.fft_tile_points == 32 else 32
+    try:
+        _lib.spod_plan_set_tuning(sp.handle, fft_tile_points=other)
+    except SpodError:
+        pytest.skip(f"no {other}-point form of the pipelined FFT for this plan")
+    assert _lib.spod_plan_get_tuning(sp.handle).fft_tile_points == other
+    sp.fit(X)
+    lam_b, gram_b = sp.eigs(), sp.gram()
+    scale = np.abs(gram_a).max(axis=(1, 2))[:, None, None]
+    d = float((np.abs(gram_b - gram_a) / scale).max())
+    print(prec, nfft, "tile", t0.fft_tile_points, "->", other, "max Gram difference / max entry %.2e" % d)
+    assert d <= 1e-6
+    assert (np.abs(lam_b - lam_a).max(axis=1) / lam_a[:, 0]).max() <= 1e-6
+    with pytest.raises(SpodError):
+        _lib.spod_plan_set_tuning(sp.handle, fft_tile_points=24)
+    sp.close()
