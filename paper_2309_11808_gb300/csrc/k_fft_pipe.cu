@@ -400,11 +400,11 @@ __device__ __forceinline__ void pass_a512(const Tin* __restrict__ ring, int rb, 
   const int col = threadIdx.x % PC;
   const int n2 = threadIdx.x / PC;
   float2 v[16];
+  const int s0 = rb + n2;
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1) {
     const int n = 32 * n1 + n2;
-    int slot = rb + n;
-    if (slot >= N) slot -= N;
+    const int slot = (s0 + 32 * n1) & (N - 1);
     const float2 x = PairLoad<Tin>::get(ring + slot * PTP + 2 * col);
     const float wn = wsm[n];
     const float d0 = (x.x - mhi0) - mlo0, d1 = (x.y - mhi1) - mlo1;
@@ -443,19 +443,16 @@ __device__ __forceinline__ void pass_b512(const float2* __restrict__ src, float2
 // (z - conj zc) / 2i; sw carries sqrt(W) / 2.
 template <int OUTK>
 __device__ __forceinline__ void store_bin4(const float4 z, const float4 zc, const float (&sw)[4], const PipeArgs& a,
-                                           int f, int l, int64_t lm, void* __restrict__ qout,
-                                           void* __restrict__ qlo) {
+                                           int64_t o, void* __restrict__ qout, void* __restrict__ qlo) {
   const float r0 = (z.x + zc.x) * sw[0], i0 = (z.y - zc.y) * sw[0];
   const float r1 = (z.y + zc.y) * sw[1], i1 = (zc.x - z.x) * sw[1];
   const float r2 = (z.z + zc.z) * sw[2], i2 = (z.w - zc.w) * sw[2];
   const float r3 = (z.w + zc.w) * sw[3], i3 = (zc.z - z.z) * sw[3];
   if constexpr (OUTK == OUT_NATIVE) {
     float* q = static_cast<float*>(qout);
-    const int64_t o = ((int64_t)f * 2 * a.nb + l) * a.chunk + lm;
     *reinterpret_cast<float4*>(q + o) = make_float4(r0, r1, r2, r3);
     *reinterpret_cast<float4*>(q + o + (int64_t)a.nb * a.chunk) = make_float4(i0, i1, i2, i3);
   } else {
-    const int64_t o = qhat_blocked_offset(a.nf, a.qrows, f, l, lm);
     const int64_t imoff = (int64_t)a.nb * kQBlock;
     __nv_bfloat16* qh = static_cast<__nv_bfloat16*>(qout);
     const uint32_t hr01 = pack_bf16x2(r0, r1), hr23 = pack_bf16x2(r2, r3);
@@ -495,6 +492,10 @@ __device__ __forceinline__ void output_phase_512(const float2* __restrict__ U, c
   const int cp = threadIdx.x % kOutCp;
   const float4* U4 = reinterpret_cast<const float4*>(U);
   const int64_t lm = lm0 + 4 * cp;
+  // offset of row l at bin 0 and the step between bins (FP32 planar or BF16 blocked)
+  constexpr bool BLK = OUTK != OUT_NATIVE;
+  const int64_t o0 = BLK ? qhat_blocked_offset(a.nf, a.qrows, 0, l, lm) : (int64_t)l * a.chunk + lm;
+  const int64_t fstep = BLK ? (int64_t)a.qrows * kQBlock : (int64_t)2 * a.nb * a.chunk;
   for (int j = threadIdx.x / kOutCp; j <= 128; j += kItems) {
     const int k1 = j & 15, k2 = j >> 4;
     const int k1p = (16 - k1) & 15;
@@ -507,8 +508,8 @@ __device__ __forceinline__ void output_phase_512(const float2* __restrict__ U, c
     const float4 xf256 = c2sub(u0, u1);              // X[256 + f]
     const float4 xnf = j ? c2sub(v0, v1) : c2add(v0, v1);     // X[N - f]
     const float4 xg = j ? c2add(v0, v1) : c2sub(v0, v1);      // X[256 - f]
-    store_bin4<OUTK>(xf, xnf, sw, a, j, l, lm, qout, qlo);
-    if (j != 128) store_bin4<OUTK>(xg, xf256, sw, a, 256 - j, l, lm, qout, qlo);
+    store_bin4<OUTK>(xf, xnf, sw, a, o0 + j * fstep, qout, qlo);
+    if (j != 128) store_bin4<OUTK>(xg, xf256, sw, a, o0 + (256 - j) * fstep, qout, qlo);
   }
 }
 

@@ -74,6 +74,26 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float y) {
   s = t;
 }
 
+// The same on two independent pairs with packed FP32x2 instructions (each
+// lane rounds to nearest exactly as the scalar form: identical results, half
+// the instructions in the drains).
+__device__ __forceinline__ void kahan_add2(float& s0, float& s1, float& c0, float& c1, float y0, float y1) {
+  asm("{\n"
+      " .reg .b64 rs, rc, ry, ryy, rt, rd;\n"
+      " mov.b64 rs, {%0, %1};\n"
+      " mov.b64 rc, {%2, %3};\n"
+      " mov.b64 ry, {%4, %5};\n"
+      " sub.rn.f32x2 ryy, ry, rc;\n"
+      " add.rn.f32x2 rt, rs, ryy;\n"
+      " sub.rn.f32x2 rd, rt, rs;\n"
+      " sub.rn.f32x2 rc, rd, ryy;\n"
+      " mov.b64 {%0, %1}, rt;\n"
+      " mov.b64 {%2, %3}, rc;\n"
+      "}"
+      : "+f"(s0), "+f"(s1), "+f"(c0), "+f"(c1)
+      : "f"(y0), "f"(y1));
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -370,7 +390,9 @@ __global__ void __launch_bounds__(kThreadsGram, 1) k_gram_tc(const __grid_consta
         for (int c = 0; c < CH; ++c)
           if (c >= c_first) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) kahan_add(s1[c * 8 + e], c1[c * 8 + e], v[c * 8 + e]);
+            for (int e = 0; e < 8; e += 2)
+              kahan_add2(s1[c * 8 + e], s1[c * 8 + e + 1], c1[c * 8 + e], c1[c * 8 + e + 1], v[c * 8 + e],
+                         v[c * 8 + e + 1]);
           }
       } else {
         tc_fence_before();

@@ -30,6 +30,7 @@ namespace spod {
 namespace {
 
 constexpr int kMaxStages = 4;            // pipeline depth (fewer when shared memory is short)
+constexpr int kMaxImageModes = 128;      // modes of one image (nmodes <= nb; the tensor path keeps 2 nb <= 128)
 constexpr uint32_t kTmemCols = 256;       // two accumulators at columns 0 and 128
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
@@ -85,7 +86,21 @@ __global__ void k_mode_image(const float* __restrict__ bmat, int nb, int nm, int
                              const double* __restrict__ what, uint32_t img_bytes, uint8_t* __restrict__ img) {
   const int f = blockIdx.x;
   const float* Bf = bmat + (size_t)f * nb * nm * 2;
-  const double wr = what ? what[2 * f] : 0.0, wi = what ? what[2 * f + 1] : 0.0;
+  // folded mean: the correction row's entries -What_f c_k, c_k = sum_l B_f[l][k],
+  // one thread per mode (FP64 sums of the FP32 coefficients), before the image loop
+  __shared__ float2 corr[kMaxImageModes];
+  if (what) {
+    const double wr = what[2 * f], wi = what[2 * f + 1];
+    for (int k = threadIdx.x; k < nm; k += blockDim.x) {
+      double cr = 0.0, ci = 0.0;
+      for (int l = 0; l < nb; ++l) {
+        cr += (double)Bf[(l * nm + k) * 2];
+        ci += (double)Bf[(l * nm + k) * 2 + 1];
+      }
+      corr[k] = make_float2((float)-(wr * cr - wi * ci), (float)-(wr * ci + wi * cr));
+    }
+    __syncthreads();
+  }
   uint8_t* hi = img + (size_t)f * img_bytes * (x3 ? 2 : 1);
   uint8_t* lo = hi + img_bytes;
   const int katoms = (np + 63) / 64;
@@ -101,14 +116,8 @@ __global__ void k_mode_image(const float* __restrict__ bmat, int nb, int nm, int
       else v = kk < nb ? bi : br;
     } else if (what && kk == 2 * nb && k < nm) {
       // folded mean: Qhat rows are the spectra Z of x - c, row 2 nb is rho; the
-      // spectra of x - mu are Z - rho What_f, so column k gains
-      // -rho What_f c_k with c_k = sum_l B_f[l][k]
-      double cr = 0.0, ci = 0.0;
-      for (int l = 0; l < nb; ++l) {
-        cr += (double)Bf[(l * nm + k) * 2];
-        ci += (double)Bf[(l * nm + k) * 2 + 1];
-      }
-      v = (float)((n & 1) == 0 ? -(wr * cr - wi * ci) : -(wr * ci + wi * cr));
+      // spectra of x - mu are Z - rho What_f, so column k gains -rho What_f c_k
+      v = (n & 1) == 0 ? corr[k].x : corr[k].y;
     }
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const uint32_t off = (uint32_t)(kk >> 6) * (uint32_t)(nn * 128) + sw128_offset(n, kk & 63);
@@ -331,6 +340,7 @@ size_t modes_image_bytes(const spod_plan_s& p) {
 
 cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s) {
   const int np = modes_np(p), nn = modes_nn(nmodes);
+  if (nmodes > kMaxImageModes) return cudaErrorInvalidValue;
   k_mode_image<<<p.nf, 256, 0, s>>>(static_cast<const float*>(p.d_bmat), p.nb, nmodes, np, nn,
                                     p.desc.precision == SPOD_PREC_BF16X3 ? 1 : 0,
                                     p.mean_fold ? p.d_what : nullptr, modes_img_bytes(np, nn),
