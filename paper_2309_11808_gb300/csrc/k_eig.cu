@@ -247,10 +247,15 @@ __global__ void __launch_bounds__(128) k_modes_simt(const R* __restrict__ qhat, 
 #pragma unroll
       for (int j = 0; j < KG; ++j) {
         const V2 b = bl[j];
-        ar0[j] += qr.x * b.x - qi.x * b.y;
-        ai0[j] += qr.x * b.y + qi.x * b.x;
-        ar1[j] += qr.y * b.x - qi.y * b.y;
-        ai1[j] += qr.y * b.y + qi.y * b.x;
+        // q * b as FMA chains (four FMAs per complex product and point)
+        ar0[j] = fma(qr.x, b.x, ar0[j]);
+        ar0[j] = fma(-qi.x, b.y, ar0[j]);
+        ai0[j] = fma(qr.x, b.y, ai0[j]);
+        ai0[j] = fma(qi.x, b.x, ai0[j]);
+        ar1[j] = fma(qr.y, b.x, ar1[j]);
+        ar1[j] = fma(-qi.y, b.y, ar1[j]);
+        ai1[j] = fma(qr.y, b.y, ai1[j]);
+        ai1[j] = fma(qi.y, b.x, ai1[j]);
       }
     }
 #pragma unroll

@@ -6,7 +6,7 @@
 // Grid: (split s, frequency f, tile group).  Each CTA owns a contiguous range
 // of the chunk's points; four groups of 64 threads share it point by point,
 // one thread per 4x4 tile of the upper triangle of the nb x nb complex Gram
-// in each group.  FP32 partial sums are promoted to FP64 every 256 points of
+// in each group.  FP32 partial sums are promoted to FP64 every 512 points of
 // a thread (FP64 sums stay in registers).  Partials are kept per split in FP64 and added chunk after chunk in
 // stream order, then summed over splits in a fixed order by k_gram_reduce:
 // no atomics, so the result is bit-reproducible (the in-GPU counterpart of
@@ -22,8 +22,12 @@ constexpr int TK = 32;        // points staged per round
 constexpr int KSUB = 4;       // thread groups splitting a round's points (point k goes to group k % KSUB)
 constexpr int TPG = 64;       // threads per group: one 4x4 complex tile of the upper triangle each
 constexpr int kThreads = KSUB * TPG;
-constexpr int kFlushRounds = 32;
-constexpr size_t kGramSimtSmemMax = 227 * 1024;   // FP32 -> FP64 promotion every 32 rounds (TK * 32 / KSUB = 256 points a thread)
+// FP32 -> FP64 promotion every 64 rounds (TK * 64 / KSUB = 512 points a
+// thread): FP64 adds issue at a small fraction of the FP32 rate on this part,
+// so the promotion is kept rare; round-to-nearest FP32 runs of 512 products
+// keep the partial sums to ~sqrt(512) 2^-24 relative
+constexpr int kFlushRounds = 64;
+constexpr size_t kGramSimtSmemMax = 227 * 1024;
 
 // 4-wide shared loads (rows are padded to a multiple of 4)
 __device__ __forceinline__ void load4(const float* p, float* v) {
@@ -160,9 +164,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_gram_simt(
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            // conj(x_i) * y_j
-            ar[i][j] += xr[i] * yr[j] + xi[i] * yi[j];
-            ai[i][j] += xr[i] * yi[j] - xi[i] * yr[j];
+            // conj(x_i) * y_j as four FMAs (the sums' rounding order is the FMAs')
+            ar[i][j] = fma(xr[i], yr[j], ar[i][j]);
+            ar[i][j] = fma(xi[i], yi[j], ar[i][j]);
+            ai[i][j] = fma(xr[i], yi[j], ai[i][j]);
+            ai[i][j] = fma(-xi[i], yr[j], ai[i][j]);
           }
       }
       if (kPromote && (r + 1) % kFlushRounds == 0) flush();
