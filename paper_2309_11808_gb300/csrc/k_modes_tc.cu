@@ -322,7 +322,7 @@ uint32_t modes_img_bytes(int np, int nn) { return (uint32_t)((np + 63) / 64) * (
 size_t modes_tc_smem_stages(const spod_plan_s& p, int nst) {
   const int nops = p.desc.precision == SPOD_PREC_BF16X3 ? 2 : 1;
   const int np = modes_np(p);
-  const size_t img = modes_img_bytes(np, modes_nn(p.nb));
+  const size_t img = modes_img_bytes(np, modes_nn(std::max(p.nb, p.adj_cols)));   // the adjoint's extra column
   const size_t box = (size_t)np * 128;
   return 1024 + 1024 + nops * img + (size_t)nst * 2 * box * nops;
 }
@@ -335,7 +335,7 @@ size_t modes_tc_smem_bytes(const spod_plan_s& p) { return modes_tc_smem_stages(p
 // Per-frequency B images (hi [, lo]) for nmodes columns, in the plan's image buffer.
 size_t modes_image_bytes(const spod_plan_s& p) {
   const int nops = p.desc.precision == SPOD_PREC_BF16X3 ? 2 : 1;
-  return (size_t)p.nf * nops * modes_img_bytes(modes_np(p), modes_nn(p.nb));
+  return (size_t)p.nf * nops * modes_img_bytes(modes_np(p), modes_nn(std::max(p.nb, p.adj_cols)));
 }
 
 cudaError_t launch_mode_image(const spod_plan_s& p, int nmodes, cudaStream_t s) {

@@ -320,6 +320,7 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   if (d->nfft > 1024) return bail(SPOD_EUNSUPPORTED, "nfft > 1024 is not supported by the block FFT kernel");
   if (p->tensor && p->nb > 64)
     return bail(SPOD_EUNSUPPORTED, "BF16 / BF16X3 precisions support nb <= 64 (2 nb rows per MMA tile)");
+  p->adj_cols = p->nb + ((!p->tensor || 2 * (p->nb + 1) <= 128) ? 1 : 0);
   p->kappa = 1.0 / (d->norm == SPOD_NORM_NB ? (double)p->nb : (double)(p->nb - 1));
 
   p->w = make_window(*d);
@@ -427,18 +428,18 @@ spod_status spod_plan_create(const spod_plan_desc* d, spod_plan_t* out) {
   const size_t o_lam = carve(sizeof(double) * (size_t)nf * nb);
   const size_t o_psi = carve(sizeof(double) * 2 * (size_t)nf * nb * nb);
   const size_t o_eigws = nb > kEigSmemMaxNb ? carve(sizeof(double) * eig_tridiag_gws_doubles(nb, nf)) : 0;
-  const size_t o_bmat = carve(2 * R * (size_t)nf * nb * nb);
+  const size_t o_bmat = carve(2 * R * (size_t)nf * nb * p->adj_cols);
   const size_t o_bimg = p->tensor ? carve(modes_image_bytes(*p)) : 0;
   const size_t o_wc = carve(2 * R * (size_t)nf);
   const size_t o_what = carve(2 * sizeof(double) * (size_t)nf);
   // R_f of the adjoint, one column sub-chunk at a time: at most 2 GiB (real data only),
   // enough columns for several waves of the adjoint kernel's 16-point CTAs
   if (!p->cplx) {
-    const size_t rpp = 2 * R * (size_t)nf * nb;
+    const size_t rpp = 2 * R * (size_t)nf * p->adj_cols;
     const int64_t want = std::max<int64_t>(128, (int64_t)(((size_t)2 << 30) / rpp) / 128 * 128);
     p->radj_points = std::min<int64_t>((chunk + 127) / 128 * 128, want);
   }
-  const size_t o_radj = p->radj_points ? carve(2 * R * (size_t)nf * nb * (size_t)p->radj_points) : 0;
+  const size_t o_radj = p->radj_points ? carve(2 * R * (size_t)nf * p->adj_cols * (size_t)p->radj_points) : 0;
   const size_t o_qhat = carve(per_point * (size_t)chunk);
   p->ws.bytes = off;
   {
@@ -821,7 +822,7 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
   SPOD_CUDA(launch_adj_gmat(*p, d_dLdlambda, s), "adjoint G kernel");
   ph.n += 1;
   if (p->tensor) {
-    SPOD_CUDA(launch_mode_image(*p, p->nb, s), "adjoint operand image kernel");
+    SPOD_CUDA(launch_mode_image(*p, p->adj_cols, s), "adjoint operand image kernel");
     ph.n += 1;
   }
   alignas(64) CUtensorMap xmap;
@@ -844,12 +845,12 @@ spod_status spod_backward(spod_plan_t p, const double* d_dLdlambda, const void* 
     for (int64_t s0 = m0; s0 < m0 + mc; s0 += rw) {
       const int64_t sw = std::min<int64_t>(rw, m0 + mc - s0);
       if (p->tensor) {
-        SPOD_CUDA(launch_modes_tc_chunk(*p, s0, sw, p->nb, p->d_radj, s, true, 0, -1, s0 - m0, rw, s0),
+        SPOD_CUDA(launch_modes_tc_chunk(*p, s0, sw, p->adj_cols, p->d_radj, s, true, 0, -1, s0 - m0, rw, s0),
                   "adjoint R kernel (tensor cores)");
         ph.n += 1;
       } else {
         int nl = 0;
-        SPOD_CUDA(launch_modes_chunk(*p, s0, sw, p->nb, p->d_radj, s, &nl, true, 0, -1, s0 - m0, rw, s0),
+        SPOD_CUDA(launch_modes_chunk(*p, s0, sw, p->adj_cols, p->d_radj, s, &nl, true, 0, -1, s0 - m0, rw, s0),
                   "adjoint R kernel");
         ph.n += nl;
       }

@@ -129,7 +129,12 @@ struct spod_plan_s {
   void* d_bmat = nullptr;          // [nf][nb][nb] complex compute type: psi_k / sqrt(lambda_k / kappa), or G_f
   void* d_wc = nullptr;            // [nf] complex compute type: c sum_n w_n e^{+2 pi i f n / nfft}
   double* d_what = nullptr;        // [nf] complex FP64: What_f = c sum_n w_n e^{-2 pi i f n / nfft} (mean fold)
-  void* d_radj = nullptr;          // [nf][nb][radj_points] complex compute type: R_f of the adjoint, one column sub-chunk
+  void* d_radj = nullptr;          // [nf][adj_cols][radj_points] complex compute type: R_f of the adjoint, one column sub-chunk
+  // spod_backward: R carries, beside its nb columns, the column Wc_f sum_l R_f[.][l]
+  // (one more column of the G image) from which the kernels take the mean of
+  // dL/dxt; adj_cols = nb + 1 then (not when 2 (nb + 1) exceeds the tensor-core
+  // mode kernel's 128 accumulator columns: nb = 64)
+  int adj_cols = 0;
   int64_t radj_points = 0;         // points per adjoint sub-chunk (a multiple of 128; 0: no adjoint, complex data)
   unsigned* d_flags = nullptr;     // [4]: [0] condition bits (cleared per fit), [1] wait bound in us
 
