@@ -105,11 +105,12 @@ def test_autotune_keeps_results(prec):
 
 @cuda
 @pytest.mark.slow
-@pytest.mark.parametrize("which", [0, 1, 3])
+@pytest.mark.parametrize("which", [0, 1, 2, 3, 4, 5])
 def test_geo_dataset_full_size_against_oracle(which):
-    # three of the six one-year records at their full size (181 x 360 x 2,
-    # nt 2920, nfft 256; 361 x 720 x 2, nt 4380, nfft 384; 721 x 1440 x 2,
-    # nt 2920, nfft 720: the three FFT code paths of the batch), bf16x3 and
+    # the six one-year records at their full size (181 x 360 x 2, nt 2920,
+    # nfft 256; 361 x 720 x 2, nt 4380, nfft 384; 361 x 720 x 2, nt 8760,
+    # nfft 512 (the two-pass 512-point FFT); 721 x 1440 x 2, nt 2920 and 8760,
+    # nfft 720; 721 x 1440 x 2, nt 4380, nfft 256), bf16x3 and
     # FP32, against the oracle's Gram at the planted annual bin and the diurnal
     # bin (computed over spatial chunks from the DFT rows of those bins)
     from paper_2309_11808_gb300 import SPOD
