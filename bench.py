@@ -789,10 +789,11 @@ def e2e_leg(sp, X, nmodes, args, world):
     hPhi = torch.empty((sp.nf, nmodes, sp.M), dtype=torch.complex64 if cdt == np.complex64 else torch.complex128,
                        pin_memory=True)
     hlam = torch.empty((sp.nf, sp.nb), dtype=torch.float64, pin_memory=True)
-    # the public host entry over a run of steps: each step copies its X up and
-    # its modes and eigenvalues down (pinned host buffers); step i + 1's upload
-    # overlaps step i's download (spod_run_host_many)
-    reps = 4
+    # the public host entry over the run's K timed steps (at least 2): each
+    # step copies its X up and its modes and eigenvalues down (pinned host
+    # buffers); step i + 1's upload overlaps step i's download
+    # (spod_run_host_many)
+    reps = max(2, args.steps)
     _lib.spod_run_host_many(sp.handle, [hX] * 2, nmodes, [hPhi] * 2, [hlam] * 2)   # warm-up (allocates staging)
     t0 = time.perf_counter()
     _lib.spod_run_host_many(sp.handle, [hX] * reps, nmodes, [hPhi] * reps, [hlam] * reps)
