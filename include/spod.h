@@ -63,7 +63,7 @@ typedef enum {
   SPOD_ENANINPUT = 5,       /* X contained NaN or Inf */
   SPOD_ENOTCONVERGED = 6,   /* eigen-solver hit its iteration cap */
   SPOD_ETIMEOUT = 7,        /* a bounded device wait gave up */
-  SPOD_EUNSUPPORTED = 8     /* valid request this build does not implement */
+  SPOD_EUNSUPPORTED = 8     /* valid request the library does not implement */
 } spod_status;
 
 /* Element type of X.  SPOD_C64 / SPOD_C128: complex data (interleaved real,
