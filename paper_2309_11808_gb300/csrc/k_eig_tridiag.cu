@@ -133,7 +133,11 @@ __device__ __forceinline__ double dw_to_double(dw v) { return (double)v.h + (dou
 
 // One implicit QL sweep with a Wilkinson shift over the unreduced block
 // [l, mm] of (d, e) (one thread); records the rotations' cosines and sines for
-// the eigenvector update and returns their number.  FP64 form.
+// the eigenvector update and returns their number.  FP64 form.  The sweep is
+// the implicit shifted QL step for symmetric tridiagonal matrices of Bowdler,
+// Martin, Reinsch and Wilkinson (the tql2 procedure of the Handbook for
+// Automatic Computation, 1968/1971): a Givens chain chasing the bulge from
+// the bottom of the block to its top, in its published order of updates.
 __device__ __noinline__ int ql_sweep_f64(double* d, double* e, int l, int mm, double* rc, double* rsn) {
   // shift: g = (d_l+1 - d_l) / (2 e_l), r = sqrt(g^2 + 1), g = d_mm - d_l + e_l / (g + sign(g) r)
   double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
