@@ -283,6 +283,11 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
     for (int i = 0; i < nit; ++i, cu.next(ntp, a.nst)) {
       const int f = cu.f, tp = cu.tp;
       const int acc = i & 1;
+      // the point's output scale, requested before the wait for the
+      // accumulator so that its latency overlaps the item's copies and MMAs
+      const int64_t lm = tp * 128 + quad * 32 + lane;
+      const bool inrange = lm < a.mcount;
+      const float rw = inrange ? scale[a.m0 + lm] : 0.f;
       // one decision per warp: the tcgen05.ld below must be executed by the whole warp
       const bool got = mbar_wait(smem_u32(&hdr->accfull[acc]), (i >> 1) & 1, abort_flag, gflags);
       if (!__all_sync(0xffffffffu, got)) break;
@@ -295,10 +300,8 @@ __global__ void __launch_bounds__(kThreadsModes, 1) k_modes_tc(const __grid_cons
       tmem_wait_ld();
       tc_fence_before();
       mbar_arrive(smem_u32(&hdr->accempty[acc]));
-      const int64_t lm = tp * 128 + quad * 32 + lane;
-      if (lm < a.mcount) {
+      if (inrange) {
         const int64_t m = a.m0 + lm;
-        const float rw = scale[m];
         float2* out = phi + ((int64_t)f * nm + k0) * a.M + (m - a.phioff);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
