@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--mean-pass", action="store_true",
                     help="take the time mean in a separate pass over X instead of inside the FFT pass "
                          "(spod_plan_desc.mean_in_fft = 0), for comparison")
+    ap.add_argument("--bf16-input", action="store_true",
+                    help="the headline grid stored as BF16 (the FP32 field rounded once to BF16); the plan reads "
+                         "BF16 snapshots and computes at --precision; a separate measurement")
     ap.add_argument("--ooc", action="store_true",
                     help="time the out-of-core run (spod_run_host_ooc: X and Phi in pinned host memory, column "
                          "tiles over the host link) on the headline grid; a separate measurement")
@@ -79,12 +82,14 @@ def parse():
 
 def workload_config(args, nb, nf, nmodes):
     cx = getattr(args, "complex", False)
+    b16 = getattr(args, "bf16_input", False)
+    esz = 8 if cx else (2 if b16 else 4)
     return {"workload": f"jet-shaped {NX}x{NR}x{NVARS}, nt={NT}, nfft={NFFT}, 50% overlap"
-                        + (", complex (two-sided)" if cx else ""),
+                        + (", complex (two-sided)" if cx else "") + (", stored as BF16" if b16 else ""),
             "npoints": NX * NR, "nvars": NVARS, "M": NX * NR * NVARS, "nt": NT, "nfft": NFFT,
-            "noverlap": NOVERLAP, "nb": nb, "nf": nf, "nmodes": nmodes, "in_dtype": "c64" if cx else "f32",
+            "noverlap": NOVERLAP, "nb": nb, "nf": nf, "nmodes": nmodes, "in_dtype": "c64" if cx else ("bf16" if b16 else "f32"),
             "precision": args.precision, "window": "hamming", "weights": "r-weighted",
-            "l2": f"inputs larger than L2 ({NT * NX * NR * NVARS * (8 if cx else 4) / 1e9:.1f} GB per step)",
+            "l2": f"inputs larger than L2 ({NT * NX * NR * NVARS * esz / 1e9:.1f} GB per step)",
             "parallelism": "one GPU" if getattr(args, "gpus", 1) <= 1 else
                            f"{args.gpus} spatial slabs of one headline grid each, one all-gather of the slab Grams per step"}
 
@@ -216,6 +221,9 @@ def main():
         del im
         torch.cuda.empty_cache()
         args.no_e2e = args.no_cpu = args.no_compare = True
+    if args.bf16_input:
+        wl.X = wl.X.to(torch.bfloat16)
+        torch.cuda.empty_cache()
     X = wl.X
     M = X.shape[1]
     elem = X.element_size()
