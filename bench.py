@@ -507,9 +507,9 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, e
 # points processed (x 32) to the full grid; the summaries are in profiles/.
 # Absent entries: no capture of the current kernel version.
 TRAFFIC = {
-    ("fft", "bf16x3"): int((497.515264 + 923.481856) * 1e6 * 32),    # k_fft_pipe<float, 1, 32, 512> (two-pass, mean inside)
-    ("gram", "bf16x3"): int((979.329536 + 19.834112) * 1e6 * 32),    # k_gram_tc<1, 40> (packed Kahan drains, rho row)
-    ("modes", "bf16x3"): int((996.048640 + 908.622080) * 1e6 * 32),  # k_modes_tc<1> (rho row)
+    ("fft", "bf16x3"): int((497.484032 + 923.243520) * 1e6 * 32),    # k_fft_pipe<float, 1, 32, 512> (two-pass, mean inside)
+    ("gram", "bf16x3"): int((979.395584 + 19.955456) * 1e6 * 32),    # k_gram_tc<1, 40> (packed Kahan drains, rho row)
+    ("modes", "bf16x3"): int((996.140800 + 908.134400) * 1e6 * 32),  # k_modes_tc<1> (rho row, scales before the wait)
     ("gram", "fp32"): int((961.233 + 25.105920) * 1e6 * 32),         # k_gram_simt<float>
     # k_modes_simt changed (frequency range, Phi view) after its capture: no entry
 }
