@@ -417,9 +417,8 @@ spod_status spod_profile_read(spod_plan_t plan, double* ms, int64_t* launches);
  * nf = 1, and returns SPOD_EINVAL when that exceeds 32 MiB, or when nf < 1
  * or nb is outside 1..1024.  No device memory is allocated.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) and
- * keeps it for that device: make that first call before any stream capture
- * begins, and do not use this entry across a cudaDeviceReset (the kept
- * address would be stale).  The call enqueues the solver on `stream` on the
+ * keeps it for that device; do not use this entry across a cudaDeviceReset
+ * (the kept address would be stale).  The call enqueues the solver on `stream` on the
  * current device, then waits for that stream and returns SPOD_ENOTCONVERGED
  * if the solver hit its sweep cap.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other host threads) race on it and must
