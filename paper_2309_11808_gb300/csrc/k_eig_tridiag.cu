@@ -222,8 +222,9 @@ __device__ __noinline__ int ql_sweep_dw(float2* dd, float2* ee, int l, int mm, d
     p = dw_mul(s, u);
     setD(i + 1, dw_add(g, p));
     g = dw_sub(dw_mul(c, u), b);
-    rc[nrot] = dw_to_double(c);
-    rsn[nrot] = dw_to_double(s);
+    // handed to the appliers as (h, l) pairs: no FP64 operation in the chain
+    reinterpret_cast<float2*>(rc)[nrot] = make_float2(c.h, c.l);
+    reinterpret_cast<float2*>(rsn)[nrot] = make_float2(s.h, s.l);
     ++nrot;
   }
   setD(l, dw_sub(D(l), p));
@@ -318,27 +319,65 @@ __device__ void ql_producer(double* d, double* e, int n, double* rc, double* rsn
 }
 
 // Warps 1-2: apply each published sweep (columns i+1, i for i = mm-1 down) to
-// the rows of Z.
+// the rows of Z.  The value of column i a rotation leaves is the next
+// rotation's column i+1, so it stays in a register.  FP64 form: Z in FP64.
+// df64 form (kDW): the rotations arrive as (h, l) float pairs and each row of
+// Z is rotated in df64, held as float pairs in Z's storage; FP64 is the
+// scarce pipe on this part and the appliers of a CTA would otherwise occupy
+// it for every rotation of the chain.  Z returns to FP64 at the end.
+template <bool kDW>
 __device__ void ql_applier(double* Z, int ldz, int n, const double* rc, const double* rsn, const int* ctl) {
   const int t = threadIdx.x - 32;
+  float2* Zf = reinterpret_cast<float2*>(Z);
+  if constexpr (kDW) {
+    for (int row = t; row < n; row += 64)
+      for (int c = 0; c < n; ++c) Zf[(size_t)row * ldz + c] = make_float2((float)Z[(size_t)row * ldz + c], 0.0f);
+  }
   for (int q = 0;; ++q) {
     const int slot = q & 1;
     named_sync(kBarFull + slot, kRotThreads);
     const int mm = ctl[2 + 2 * slot], nrot = ctl[3 + 2 * slot];
     if (nrot < 0) break;
-    const double* rcs = rc + slot * n;
-    const double* rss = rsn + slot * n;
-    for (int row = t; row < n; row += 64) {
-      double* zr = Z + (size_t)row * ldz;
-      for (int j = 0; j < nrot; ++j) {
-        const int i = mm - 1 - j;
-        const double c = rcs[j], s = rss[j];
-        const double fz = zr[i + 1];
-        zr[i + 1] = fma(s, zr[i], c * fz);
-        zr[i] = fma(c, zr[i], -s * fz);
+    if constexpr (kDW) {
+      const float2* rcs = reinterpret_cast<const float2*>(rc) + slot * n;
+      const float2* rss = reinterpret_cast<const float2*>(rsn) + slot * n;
+      for (int row = t; row < n; row += 64) {
+        float2* zr = Zf + (size_t)row * ldz;
+        dw fz = {zr[mm].x, zr[mm].y};
+        for (int j = 0; j < nrot; ++j) {
+          const int i = mm - 1 - j;
+          const float2 c2 = rcs[j], s2 = rss[j];
+          const dw c = {c2.x, c2.y}, s = {s2.x, s2.y};
+          const float2 zi2 = zr[i];
+          const dw zi = {zi2.x, zi2.y};
+          const dw up = dw_add(dw_mul(s, zi), dw_mul(c, fz));
+          zr[i + 1] = make_float2(up.h, up.l);
+          fz = dw_sub(dw_mul(c, zi), dw_mul(s, fz));
+        }
+        if (nrot > 0) zr[mm - nrot] = make_float2(fz.h, fz.l);
+      }
+    } else {
+      const double* rcs = rc + slot * n;
+      const double* rss = rsn + slot * n;
+      for (int row = t; row < n; row += 64) {
+        double* zr = Z + (size_t)row * ldz;
+        for (int j = 0; j < nrot; ++j) {
+          const int i = mm - 1 - j;
+          const double c = rcs[j], s = rss[j];
+          const double fz = zr[i + 1];
+          zr[i + 1] = fma(s, zr[i], c * fz);
+          zr[i] = fma(c, zr[i], -s * fz);
+        }
       }
     }
     named_arrive(kBarEmpty + slot, kRotThreads);
+  }
+  if constexpr (kDW) {
+    for (int row = t; row < n; row += 64)
+      for (int c = 0; c < n; ++c) {
+        const float2 v = Zf[(size_t)row * ldz + c];
+        Z[(size_t)row * ldz + c] = (double)v.x + (double)v.y;
+      }
   }
 }
 
@@ -378,6 +417,175 @@ __device__ void form_q(const double2* A, double2* Qm, int lda, int n, const doub
   }
 }
 
+// ---- df64 complex numbers (re, im), stored as float4 (re.h, re.l, im.h, im.l):
+// the same 16 bytes as an FP64 complex entry.
+struct dc {
+  dw re, im;
+};
+__device__ __forceinline__ dc dc_ld(const float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 dc_st(dc a) { return make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
+__device__ __forceinline__ dc dc_zero() { return {{0.0f, 0.0f}, {0.0f, 0.0f}}; }
+__device__ __forceinline__ dc dc_add(dc a, dc b) { return {dw_add(a.re, b.re), dw_add(a.im, b.im)}; }
+__device__ __forceinline__ dc dc_sub(dc a, dc b) { return {dw_sub(a.re, b.re), dw_sub(a.im, b.im)}; }
+__device__ __forceinline__ dc dc_mul(dc a, dc b) {
+  return {dw_sub(dw_mul(a.re, b.re), dw_mul(a.im, b.im)), dw_add(dw_mul(a.re, b.im), dw_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dc dc_mulc(dc a, dc b) {   // conj(a) * b
+  return {dw_add(dw_mul(a.re, b.re), dw_mul(a.im, b.im)), dw_sub(dw_mul(a.re, b.im), dw_mul(a.im, b.re))};
+}
+
+// Block sum of a df64 complex value; every thread gets the same sum (the
+// warps' partials are added in warp order).
+__device__ dc block_sum_dc(dc v, float4* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    dc u;
+    u.re.h = __shfl_xor_sync(0xffffffffu, v.re.h, o);
+    u.re.l = __shfl_xor_sync(0xffffffffu, v.re.l, o);
+    u.im.h = __shfl_xor_sync(0xffffffffu, v.im.h, o);
+    u.im.l = __shfl_xor_sync(0xffffffffu, v.im.l, o);
+    v = dc_add(v, u);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = dc_st(v);
+  __syncthreads();
+  dc t = dc_ld(red[0]);
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = dc_add(t, dc_ld(red[i]));
+  return t;
+}
+
+// Step 1 in df64 for the non-FP64 plans: the same reflectors in the same
+// order as the FP64 form, on A scaled by the power of two sc that brings
+// max |A_ij| into [1, 2) (df64 has the exponent range of FP32).  FP64 is the
+// scarce pipe on this part, and the reduction's products and its reductions'
+// dependent adds were the longest phase of the solver in FP64.  On return d
+// and e hold the tridiagonal (FP64, unscaled; e[n-1] is the caller's), and
+// the reflectors below the subdiagonal of A and tau are FP64 complex, as the
+// Q-forming warps read them.  A coefficient column whose |alpha|^2 + |x|^2 is
+// below 2^-120 (entries below about 1e-18 of max |A_ij|) is left unreflected,
+// a perturbation far below the arithmetic's 2^-47.
+__device__ void householder_dw(const double2* __restrict__ G, double2* A, int lda, int n, double2* tau,
+                               double2* pv, double2* vv, double2* part, double* d, double* e, double2* red) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  float4* A4 = reinterpret_cast<float4*>(A);
+  float4* tau4 = reinterpret_cast<float4*>(tau);
+  float4* pv4 = reinterpret_cast<float4*>(pv);
+  float4* vv4 = reinterpret_cast<float4*>(vv);
+  float4* part4 = reinterpret_cast<float4*>(part);
+  float4* red4 = reinterpret_cast<float4*>(red);
+  double amax = 0.0;
+  for (int i = tid; i < n * n; i += nth) {
+    const double2 g = G[i];
+    amax = fmax(amax, fmax(fabs(g.x), fabs(g.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((tid & 31) == 0) red[tid >> 5].x = amax;
+  __syncthreads();
+  amax = 0.0;
+  for (int i = 0; i < (nth >> 5); ++i) amax = fmax(amax, red[i].x);
+  const double sc = amax > 0.0 ? scalbn(1.0, -ilogb(amax)) : 1.0;
+  for (int i = tid; i < n * n; i += nth) {
+    const int r = i / n, c = i - r * n;
+    const double2 g = G[i];
+    const dw re = dw_from_double(g.x * sc), im = dw_from_double(g.y * sc);
+    A4[(size_t)r * lda + c] = make_float4(re.h, re.l, im.h, im.l);
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;
+    dc pt = dc_zero();
+    for (int i = 1 + tid; i < m; i += nth) {
+      const dc x = dc_ld(A4[(size_t)(k + 1 + i) * lda + k]);
+      pt.re = dw_add(pt.re, dw_add(dw_mul(x.re, x.re), dw_mul(x.im, x.im)));
+    }
+    const dw xn2 = block_sum_dc(pt, red4).re;     // |x[1:]|^2
+    if (tid == 0) {
+      const dc alpha = dc_ld(A4[(size_t)(k + 1) * lda + k]);
+      dc t = dc_zero(), scale = dc_zero();
+      dw beta = alpha.re;                          // stays alpha when no reflection is needed
+      const dw a2 = dw_add(dw_add(dw_mul(alpha.re, alpha.re), dw_mul(alpha.im, alpha.im)), xn2);
+      if ((xn2.h > 0.0f || alpha.im.h != 0.0f) && a2.h > 0x1p-120f) {
+        const dw nrm = dw_mul(a2, dw_rsqrt(a2));
+        beta = alpha.re.h >= 0.0f ? dw_neg(nrm) : nrm;
+        t.re = dw_div(dw_sub(beta, alpha.re), beta);
+        t.im = dw_div(dw_neg(alpha.im), beta);
+        // scale = 1 / (alpha - beta)
+        const dc den = {dw_sub(alpha.re, beta), alpha.im};
+        const dw dd2 = dw_add(dw_mul(den.re, den.re), dw_mul(den.im, den.im));
+        scale.re = dw_div(den.re, dd2);
+        scale.im = dw_neg(dw_div(den.im, dd2));
+      }
+      tau4[k] = dc_st(t);
+      e[k] = dw_to_double(beta) / sc;
+      pv4[0] = dc_st(scale);                       // broadcast
+    }
+    __syncthreads();
+    const dc t = dc_ld(tau4[k]);
+    const dc scale = dc_ld(pv4[0]);
+    __syncthreads();
+    if (t.re.h == 0.0f && t.im.h == 0.0f) continue;
+    // v = (1, x[1:] * scale): in place below the subdiagonal and in vv
+    for (int i = tid; i < m; i += nth) {
+      float4* a = A4 + (size_t)(k + 1 + i) * lda + k;
+      const dc v = i == 0 ? dc{{1.0f, 0.0f}, {0.0f, 0.0f}} : dc_mul(dc_ld(*a), scale);
+      *a = dc_st(v);
+      vv4[i] = dc_st(v);
+    }
+    __syncthreads();
+    // p = tau * A22 v (A22 Hermitian: columns read), S partial sums per i in a fixed order
+    const int S = max(1, min(8, nth / m));
+    if (tid < S * m) {
+      const int i = tid % m, sidx = tid / m;
+      dc acc = dc_zero();
+      for (int j = sidx; j < m; j += S)
+        acc = dc_add(acc, dc_mulc(dc_ld(A4[(size_t)(k + 1 + j) * lda + (k + 1 + i)]), dc_ld(vv4[j])));
+      part4[sidx * m + i] = dc_st(acc);
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) {
+      dc acc = dc_ld(part4[i]);
+      for (int q = 1; q < S; ++q) acc = dc_add(acc, dc_ld(part4[q * m + i]));
+      pv4[i] = dc_st(dc_mul(t, acc));
+    }
+    __syncthreads();
+    // w = p - (tau/2) (p^H v) v
+    dc dot = dc_zero();
+    for (int i = tid; i < m; i += nth) dot = dc_add(dot, dc_mulc(dc_ld(pv4[i]), dc_ld(vv4[i])));
+    dot = block_sum_dc(dot, red4);
+    const dc half_t = {{-0.5f * t.re.h, -0.5f * t.re.l}, {-0.5f * t.im.h, -0.5f * t.im.l}};   // exact
+    const dc al = dc_mul(half_t, dot);
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) pv4[i] = dc_st(dc_add(dc_ld(pv4[i]), dc_mul(al, dc_ld(vv4[i]))));
+    __syncthreads();
+    // A22 -= v w^H + w v^H
+    for (int idx = tid; idx < m * m; idx += nth) {
+      const int i = idx / m, j = idx - i * m;
+      const dc vi = dc_ld(vv4[i]), vj = dc_ld(vv4[j]);
+      const dc wi = dc_ld(pv4[i]), wj = dc_ld(pv4[j]);
+      float4* a = A4 + (size_t)(k + 1 + i) * lda + (k + 1 + j);
+      // v_i conj(w_j) + w_i conj(v_j)
+      *a = dc_st(dc_sub(dc_ld(*a), dc_add(dc_mulc(wj, vi), dc_mulc(vj, wi))));
+    }
+    __syncthreads();
+  }
+  // the diagonal, then the reflectors (strictly below it) and tau to FP64 in place
+  for (int i = tid; i < n; i += nth) {
+    const float4 a = A4[(size_t)i * lda + i];
+    d[i] = ((double)a.x + (double)a.y) / sc;
+  }
+  for (int idx = tid; idx < n * n; idx += nth) {
+    const int r = idx / n, c = idx - r * n;
+    if (r > c) {
+      const float4 a = A4[(size_t)r * lda + c];
+      A[(size_t)r * lda + c] = make_double2((double)a.x + (double)a.y, (double)a.z + (double)a.w);
+    }
+  }
+  for (int k = tid; k + 1 < n; k += nth) {
+    const float4 t4 = tau4[k];
+    tau[k] = make_double2((double)t4.x + (double)t4.y, (double)t4.z + (double)t4.w);
+  }
+}
+
 template <bool kDW>
 __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restrict__ gram, int n,
                                                           double* __restrict__ lam, double* __restrict__ psi,
@@ -410,99 +618,103 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
   double2* Qm = A + (size_t)n * lda;
   double* Z = reinterpret_cast<double*>(Qm + (size_t)n * lda);
   const double2* G = reinterpret_cast<const double2*>(gram) + (size_t)f * n * n;
-  for (int i = tid; i < n * n; i += nth) {
-    const int r = i / n, c = i - r * n;
-    A[(size_t)r * lda + c] = G[i];
-  }
-  __syncthreads();
 
   // ---------------- 1. Householder reduction to real tridiagonal form
-  for (int k = 0; k + 1 < n; ++k) {
-    const int m = n - k - 1;                    // length of x = A[k+1:, k]
-    double2 pt = make_double2(0.0, 0.0);
-    for (int i = 1 + tid; i < m; i += nth) {
-      const double2 x = A[(size_t)(k + 1 + i) * lda + k];
-      pt.x += x.x * x.x + x.y * x.y;
+  if constexpr (kDW) {
+    householder_dw(G, A, lda, n, tau, pv, vv, part, d, e, red);
+  } else {
+    for (int i = tid; i < n * n; i += nth) {
+      const int r = i / n, c = i - r * n;
+      A[(size_t)r * lda + c] = G[i];
     }
-    const double xn2 = block_sum2(pt, red).x;   // |x[1:]|^2
-    if (tid == 0) {
-      const double2 alpha = A[(size_t)(k + 1) * lda + k];
-      double2 t = make_double2(0.0, 0.0);
-      double beta = alpha.x;                     // stays alpha when no reflection is needed
-      double2 scale = make_double2(0.0, 0.0);
-      if (xn2 > 0.0 || alpha.y != 0.0) {
-        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-        beta = alpha.x >= 0.0 ? -nrm : nrm;
-        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-        // scale = 1 / (alpha - beta)
-        const double2 den = make_double2(alpha.x - beta, alpha.y);
-        const double dd2 = den.x * den.x + den.y * den.y;
-        scale = make_double2(den.x / dd2, -den.y / dd2);
+    __syncthreads();
+    for (int k = 0; k + 1 < n; ++k) {
+      const int m = n - k - 1;                    // length of x = A[k+1:, k]
+      double2 pt = make_double2(0.0, 0.0);
+      for (int i = 1 + tid; i < m; i += nth) {
+        const double2 x = A[(size_t)(k + 1 + i) * lda + k];
+        pt.x += x.x * x.x + x.y * x.y;
       }
-      tau[k] = t;
-      e[k] = beta;
-      pv[0] = scale;                             // broadcast
-    }
-    __syncthreads();
-    const double2 t = tau[k];
-    const double2 scale = pv[0];
-    __syncthreads();
-    if (t.x == 0.0 && t.y == 0.0) continue;
-    // v = (1, x[1:] * scale): stored in place below the subdiagonal and in vv
-    for (int i = tid; i < m; i += nth) {
-      double2* a = A + (size_t)(k + 1 + i) * lda + k;
-      const double2 v = i == 0 ? make_double2(1.0, 0.0) : cmul(*a, scale);
-      *a = v;
-      vv[i] = v;
-    }
-    __syncthreads();
-    // p = tau * A22 v with A22 Hermitian: p_i = tau sum_j conj(A22[j][i]) v_j,
-    // S partial sums per i over j = s, s + S, ... (consecutive threads read
-    // consecutive columns), added in a fixed order
-    const int S = max(1, min(8, nth / m));
-    if (tid < S * m) {
-      const int i = tid % m, sidx = tid / m;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int j = sidx; j < m; j += S) {
-        const double2 c = cmulc(A[(size_t)(k + 1 + j) * lda + (k + 1 + i)], vv[j]);
-        acc.x += c.x; acc.y += c.y;
+      const double xn2 = block_sum2(pt, red).x;   // |x[1:]|^2
+      if (tid == 0) {
+        const double2 alpha = A[(size_t)(k + 1) * lda + k];
+        double2 t = make_double2(0.0, 0.0);
+        double beta = alpha.x;                     // stays alpha when no reflection is needed
+        double2 scale = make_double2(0.0, 0.0);
+        if (xn2 > 0.0 || alpha.y != 0.0) {
+          const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+          beta = alpha.x >= 0.0 ? -nrm : nrm;
+          t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+          // scale = 1 / (alpha - beta)
+          const double2 den = make_double2(alpha.x - beta, alpha.y);
+          const double dd2 = den.x * den.x + den.y * den.y;
+          scale = make_double2(den.x / dd2, -den.y / dd2);
+        }
+        tau[k] = t;
+        e[k] = beta;
+        pv[0] = scale;                             // broadcast
       }
-      part[sidx * m + i] = acc;
+      __syncthreads();
+      const double2 t = tau[k];
+      const double2 scale = pv[0];
+      __syncthreads();
+      if (t.x == 0.0 && t.y == 0.0) continue;
+      // v = (1, x[1:] * scale): stored in place below the subdiagonal and in vv
+      for (int i = tid; i < m; i += nth) {
+        double2* a = A + (size_t)(k + 1 + i) * lda + k;
+        const double2 v = i == 0 ? make_double2(1.0, 0.0) : cmul(*a, scale);
+        *a = v;
+        vv[i] = v;
+      }
+      __syncthreads();
+      // p = tau * A22 v with A22 Hermitian: p_i = tau sum_j conj(A22[j][i]) v_j,
+      // S partial sums per i over j = s, s + S, ... (consecutive threads read
+      // consecutive columns), added in a fixed order
+      const int S = max(1, min(8, nth / m));
+      if (tid < S * m) {
+        const int i = tid % m, sidx = tid / m;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = sidx; j < m; j += S) {
+          const double2 c = cmulc(A[(size_t)(k + 1 + j) * lda + (k + 1 + i)], vv[j]);
+          acc.x += c.x; acc.y += c.y;
+        }
+        part[sidx * m + i] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += nth) {
+        double2 acc = part[i];
+        for (int q = 1; q < S; ++q) { acc.x += part[q * m + i].x; acc.y += part[q * m + i].y; }
+        pv[i] = cmul(t, acc);
+      }
+      __syncthreads();
+      // w = p - (tau/2) (p^H v) v
+      double2 dot = make_double2(0.0, 0.0);
+      for (int i = tid; i < m; i += nth) {
+        const double2 c = cmulc(pv[i], vv[i]);
+        dot.x += c.x; dot.y += c.y;
+      }
+      dot = block_sum2(dot, red);
+      const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), dot);
+      __syncthreads();
+      for (int i = tid; i < m; i += nth) {
+        const double2 c = cmul(al, vv[i]);
+        pv[i] = make_double2(pv[i].x + c.x, pv[i].y + c.y);
+      }
+      __syncthreads();
+      // A22 -= v w^H + w v^H
+      for (int idx = tid; idx < m * m; idx += nth) {
+        const int i = idx / m, j = idx - i * m;
+        const double2 vi = vv[i], vj = vv[j];
+        const double2 wi = pv[i], wj = pv[j];
+        double2& a = A[(size_t)(k + 1 + i) * lda + (k + 1 + j)];
+        // v_i conj(w_j) + w_i conj(v_j)
+        a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
+        a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int i = tid; i < m; i += nth) {
-      double2 acc = part[i];
-      for (int q = 1; q < S; ++q) { acc.x += part[q * m + i].x; acc.y += part[q * m + i].y; }
-      pv[i] = cmul(t, acc);
-    }
-    __syncthreads();
-    // w = p - (tau/2) (p^H v) v
-    double2 dot = make_double2(0.0, 0.0);
-    for (int i = tid; i < m; i += nth) {
-      const double2 c = cmulc(pv[i], vv[i]);
-      dot.x += c.x; dot.y += c.y;
-    }
-    dot = block_sum2(dot, red);
-    const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), dot);
-    __syncthreads();
-    for (int i = tid; i < m; i += nth) {
-      const double2 c = cmul(al, vv[i]);
-      pv[i] = make_double2(pv[i].x + c.x, pv[i].y + c.y);
-    }
-    __syncthreads();
-    // A22 -= v w^H + w v^H
-    for (int idx = tid; idx < m * m; idx += nth) {
-      const int i = idx / m, j = idx - i * m;
-      const double2 vi = vv[i], vj = vv[j];
-      const double2 wi = pv[i], wj = pv[j];
-      double2& a = A[(size_t)(k + 1 + i) * lda + (k + 1 + j)];
-      // v_i conj(w_j) + w_i conj(v_j)
-      a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
-      a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
-    }
-    __syncthreads();
+    for (int i = tid; i < n; i += nth) d[i] = A[(size_t)i * lda + i].x;
   }
-  for (int i = tid; i < n; i += nth) d[i] = A[(size_t)i * lda + i].x;
   for (int idx = tid; idx < n * n; idx += nth) {
     const int r = idx / n, c = idx - r * n;
     Z[(size_t)r * lda + c] = r == c ? 1.0 : 0.0;
@@ -515,7 +727,7 @@ __global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restri
 
   // ---------------- 2. QL (warp 0) | Z updates (warps 1-2) | Q (warps 3-7)
   if (warp == 0) ql_producer<kDW>(d, e, n, rc, rsn, ctl, max_iter);
-  else if (warp < 3) ql_applier(Z, lda, n, rc, rsn, ctl);
+  else if (warp < 3) ql_applier<kDW>(Z, lda, n, rc, rsn, ctl);
   else form_q(A, Qm, lda, n, tau, pv);
   __syncthreads();
   if (tid == 0 && ctl[0]) atomicOr(flags, FLAG_NOTCONV);
