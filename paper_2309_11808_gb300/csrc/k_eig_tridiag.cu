@@ -115,14 +115,23 @@ __device__ __forceinline__ dw dw_div(dw x, dw y) {
   const float q3 = __fdividef(r2.h, y.h);
   return dw_add(fast_two_sum(q1, q2), dw_of(q3));
 }
-// 1 / sqrt(x), x > 0 normal: y0 = rsqrtf(x_h), e = 1 - x y0^2 in df64, then the
-// second-order step y = y0 (1 + e/2 + 3 e^2/8) (error O(e^3), e ~ 2^-22).
+// Sum of two non-negative df64 values (no cancellation: the short form of
+// the double-word sum, whose error bound holds for operands of one sign).
+__device__ __forceinline__ dw dw_add_pos(dw x, dw y) {
+  const dw s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+// 1 / sqrt(x), x > 0 normal: y0 = rsqrtf(x_h), then the second-order step
+// y = y0 (1 + e/2 + 3 e^2/8) on the residual e = 1 - x y0^2 (|e| ~ 2^-22),
+// formed with FMAs: x_h y0 = h + hl exactly, 1 - h y0 and the rest of x y0^2
+// folded in by one more FMA (error of e about 2^-45, of y about 2^-46).
 __device__ __forceinline__ dw dw_rsqrt(dw x) {
   const float y0 = rsqrtf(x.h);
-  const float p = __fmul_rn(y0, y0);
-  const dw y2 = {p, __fmaf_rn(y0, y0, -p)};           // y0^2 exactly
-  const dw e = dw_sub(dw_of(1.0f), dw_mul(x, y2));
-  const float u = __fmaf_rn(e.h, __fmaf_rn(0.375f, e.h, 0.5f), 0.5f * e.l);
+  const float h = __fmul_rn(x.h, y0);
+  const float hl = __fmaf_rn(x.h, y0, -h);
+  const float t = __fmaf_rn(x.l, y0, hl);             // x y0 - h
+  const float e = __fmaf_rn(-t, y0, __fmaf_rn(-h, y0, 1.0f));
+  const float u = __fmul_rn(e, __fmaf_rn(0.375f, e, 0.5f));
   return fast_two_sum(y0, __fmul_rn(y0, u));
 }
 __device__ __forceinline__ dw dw_from_double(double v) {
@@ -194,21 +203,26 @@ __device__ __noinline__ int ql_sweep_dw(float2* dd, float2* ee, int l, int mm, d
   g = dw_add(dw_sub(D(mm), dl), dw_div(el, g.h >= 0.0f ? dw_add(g, r0) : dw_sub(g, r0)));
   dw s = dw_of(1.0f), c = dw_of(1.0f), p = dw_of(0.0f);
   int nrot = 0;
+  // d[i+1], d[i] and e[i] of the rotation at i, loaded one rotation ahead
+  // (the rotation at i writes only d[i+1] and e[i+1]), so the chain does
+  // not wait on shared-memory loads
+  dw dn = D(mm), di = D(mm - 1), ei = E(mm - 1);
   for (int i = mm - 1; i >= l; --i) {
-    const dw ei = E(i);
+    const int inext = i > l ? i - 1 : i;
+    const dw di_next = D(inext), ei_next = E(inext);
     dw ff = dw_mul(s, ei), gg = g;
     const dw b = dw_mul(c, ei);
     float post = 1.0f;
-    dw r2 = dw_add(dw_mul(ff, ff), dw_mul(gg, gg));
+    dw r2 = dw_add_pos(dw_mul(ff, ff), dw_mul(gg, gg));
     if (r2.h < 0x1p-100f) {                 // tiny pair: rescale by an exact power of two
       ff = {ff.h * 0x1p64f, ff.l * 0x1p64f};
       gg = {gg.h * 0x1p64f, gg.l * 0x1p64f};
       post = 0x1p-64f;
-      r2 = dw_add(dw_mul(ff, ff), dw_mul(gg, gg));
+      r2 = dw_add_pos(dw_mul(ff, ff), dw_mul(gg, gg));
     }
     if (!(r2.h > 0x1p-120f)) {              // both negligible: the block splits at i + 1
       setE(i + 1, dw_of(0.0f));
-      setD(i + 1, dw_sub(D(i + 1), p));
+      setD(i + 1, dw_sub(dn, p));
       setE(mm, dw_of(0.0f));
       return nrot;
     }
@@ -217,8 +231,8 @@ __device__ __noinline__ int ql_sweep_dw(float2* dd, float2* ee, int l, int mm, d
     setE(i + 1, {rr.h * post, rr.l * post});
     s = dw_mul(ff, ri);
     c = dw_mul(gg, ri);
-    g = dw_sub(D(i + 1), p);
-    const dw u = dw_add(dw_mul(dw_sub(D(i), g), s), dw_mul2(dw_mul(c, b)));
+    g = dw_sub(dn, p);
+    const dw u = dw_add(dw_mul(dw_sub(di, g), s), dw_mul2(dw_mul(c, b)));
     p = dw_mul(s, u);
     setD(i + 1, dw_add(g, p));
     g = dw_sub(dw_mul(c, u), b);
@@ -226,6 +240,9 @@ __device__ __noinline__ int ql_sweep_dw(float2* dd, float2* ee, int l, int mm, d
     reinterpret_cast<float2*>(rc)[nrot] = make_float2(c.h, c.l);
     reinterpret_cast<float2*>(rsn)[nrot] = make_float2(s.h, s.l);
     ++nrot;
+    dn = di;
+    di = di_next;
+    ei = ei_next;
   }
   setD(l, dw_sub(D(l), p));
   setE(l, g);
