@@ -480,7 +480,9 @@ def kernel_roofline(phase, per_launch_ms, M, nb, nf, nmodes, peaks, precision, e
     if phase == "eig":
         # Householder 16/3 n^3, Q formation 16/3 n^3, V = Q Z 4 n^3, Z rotations ~6 n^3 (real flops)
         flops = (16.0 / 3 + 16.0 / 3 + 4.0 + 6.0) * nb ** 3 * nf
-        r = alu(flops, FP64_PEAK, "nominal GB300 FP64 rate (latency-bound kernel)")
+        r = alu(flops, FP64_PEAK, "nominal GB300 FP64 rate (context only: the kernel is bound by the latency of "
+                                  "its rotation chain; the non-FP64 plans run the reduction, the chain and the Z "
+                                  "rotations in double-FP32 on the FP32 pipe)")
         r["traffic"] = None
         return r
     overhead = None

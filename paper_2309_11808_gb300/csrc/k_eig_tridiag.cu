@@ -510,16 +510,19 @@ __device__ void householder_dw(const double2* __restrict__ G, double2* A, int ld
   __syncthreads();
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;
+    // alpha and x are read before the barriers of the sum below, after
+    // which the column is overwritten by v
+    const dc alpha = dc_ld(A4[(size_t)(k + 1) * lda + k]);
     dc pt = dc_zero();
     for (int i = 1 + tid; i < m; i += nth) {
       const dc x = dc_ld(A4[(size_t)(k + 1 + i) * lda + k]);
       pt.re = dw_add(pt.re, dw_add(dw_mul(x.re, x.re), dw_mul(x.im, x.im)));
     }
-    const dw xn2 = block_sum_dc(pt, red4).re;     // |x[1:]|^2
-    if (tid == 0) {
-      const dc alpha = dc_ld(A4[(size_t)(k + 1) * lda + k]);
-      dc t = dc_zero(), scale = dc_zero();
-      dw beta = alpha.re;                          // stays alpha when no reflection is needed
+    const dw xn2 = block_sum_dc(pt, red4).re;     // |x[1:]|^2, the same in every thread
+    // the reflector, computed by every thread from the same operands (no broadcast)
+    dc t = dc_zero(), scale = dc_zero();
+    dw beta = alpha.re;                            // stays alpha when no reflection is needed
+    {
       const dw a2 = dw_add(dw_add(dw_mul(alpha.re, alpha.re), dw_mul(alpha.im, alpha.im)), xn2);
       if ((xn2.h > 0.0f || alpha.im.h != 0.0f) && a2.h > 0x1p-120f) {
         const dw nrm = dw_mul(a2, dw_rsqrt(a2));
@@ -532,14 +535,11 @@ __device__ void householder_dw(const double2* __restrict__ G, double2* A, int ld
         scale.re = dw_div(den.re, dd2);
         scale.im = dw_neg(dw_div(den.im, dd2));
       }
+    }
+    if (tid == 0) {
       tau4[k] = dc_st(t);
       e[k] = dw_to_double(beta) / sc;
-      pv4[0] = dc_st(scale);                       // broadcast
     }
-    __syncthreads();
-    const dc t = dc_ld(tau4[k]);
-    const dc scale = dc_ld(pv4[0]);
-    __syncthreads();
     if (t.re.h == 0.0f && t.im.h == 0.0f) continue;
     // v = (1, x[1:] * scale): in place below the subdiagonal and in vv
     for (int i = tid; i < m; i += nth) {
@@ -559,19 +559,18 @@ __device__ void householder_dw(const double2* __restrict__ G, double2* A, int ld
       part4[sidx * m + i] = dc_st(acc);
     }
     __syncthreads();
+    // p_i and p^H v; then w = p - (tau/2) (p^H v) v, each thread on the i it formed
+    dc dot = dc_zero();
     for (int i = tid; i < m; i += nth) {
       dc acc = dc_ld(part4[i]);
       for (int q = 1; q < S; ++q) acc = dc_add(acc, dc_ld(part4[q * m + i]));
-      pv4[i] = dc_st(dc_mul(t, acc));
+      const dc pi = dc_mul(t, acc);
+      pv4[i] = dc_st(pi);
+      dot = dc_add(dot, dc_mulc(pi, dc_ld(vv4[i])));
     }
-    __syncthreads();
-    // w = p - (tau/2) (p^H v) v
-    dc dot = dc_zero();
-    for (int i = tid; i < m; i += nth) dot = dc_add(dot, dc_mulc(dc_ld(pv4[i]), dc_ld(vv4[i])));
     dot = block_sum_dc(dot, red4);
     const dc half_t = {{-0.5f * t.re.h, -0.5f * t.re.l}, {-0.5f * t.im.h, -0.5f * t.im.l}};   // exact
     const dc al = dc_mul(half_t, dot);
-    __syncthreads();
     for (int i = tid; i < m; i += nth) pv4[i] = dc_st(dc_add(dc_ld(pv4[i]), dc_mul(al, dc_ld(vv4[i]))));
     __syncthreads();
     // A22 -= v w^H + w v^H
@@ -604,7 +603,7 @@ __device__ void householder_dw(const double2* __restrict__ G, double2* A, int ld
 }
 
 template <bool kDW>
-__global__ void __launch_bounds__(kThreads) k_eig_tridiag(const double* __restrict__ gram, int n,
+__global__ void __launch_bounds__(kThreads, 2) k_eig_tridiag(const double* __restrict__ gram, int n,
                                                           double* __restrict__ lam, double* __restrict__ psi,
                                                           double* __restrict__ gws, unsigned* __restrict__ flags,
                                                           int max_iter) {
