@@ -73,18 +73,26 @@ typedef enum {
  * spod_backward returns SPOD_EUNSUPPORTED. */
 typedef enum { SPOD_F64 = 0, SPOD_F32 = 1, SPOD_BF16 = 2, SPOD_C64 = 3, SPOD_C128 = 4 } spod_dtype;
 
-/* Arithmetic of the bulk FFT / Gram / mode work.  The time mean is always
- * accumulated in FP64 and the eigen-decomposition always runs in FP64.
- *   FP64   : everything in FP64 (input F64 or F32).
+/* Arithmetic of the bulk FFT / Gram / mode work.
+ *   FP64   : everything in FP64 (input F64 or F32), the eigen-solve included.
  *   FP32   : FFT, Gram and modes in FP32 SIMT arithmetic; Gram partial sums
  *            promoted to FP64 every few hundred points.
  *   BF16   : FFT in FP32; Gram and mode products on the tensor cores from
  *            BF16-rounded operands, FP32 accumulation.
  *   BF16X3 : as BF16 but every operand x is split x = hi + lo (hi = bf16(x),
- *            lo = bf16(x - hi)), three tensor-core products per step.  Modes:
- *            hi*hi + hi*lo + lo*hi.  Gram (symmetric): A1 = hi hi^T + lo lo^T
- *            and A2 = hi lo^T in two accumulators, Y Y^T = A1 + A2 + A2^T, so
- *            no product term is dropped. */
+ *            lo = bf16(x - hi)).  Modes: hi*hi + hi*lo + lo*hi.  Gram
+ *            (symmetric): A1 = hi hi^T in short tensor-core runs drained into
+ *            compensated FP32 sums, A2 = hi lo^T, and the diagonal of lo lo^T:
+ *            Y Y^T = A1 + A2 + A2^T + diag(lo lo^T); the off-diagonal lo lo^T
+ *            terms (2^-16 of Y Y^T, uncorrelated rounding products) are left
+ *            out.
+ * Partial Grams are combined in FP64.  The time mean is accumulated in FP64
+ * by the separate mean pass or, taken inside the FFT pass (desc.mean_in_fft,
+ * BF16 / BF16X3), in compensated FP32 sums combined per point in FP64.  The
+ * eigen-solve reads the FP64 Gram; for the FP64 precision it runs in FP64,
+ * for the others its Householder reduction, QL rotation chain and
+ * eigenvector rotations run in double-FP32 (about 48 bits) and the rest of
+ * it in FP64. */
 typedef enum {
   SPOD_PREC_FP64 = 0,
   SPOD_PREC_FP32 = 1,

@@ -2,7 +2,7 @@
 // tridiagonalisation and implicit QL iteration (one 256-thread CTA per
 // frequency).
 //
-// 1. Reduction (n-1 steps, FP64): for column k, the reflector H_k = I - tau v v^H
+// 1. Reduction (n-1 steps): for column k, the reflector H_k = I - tau v v^H
 //    (v[0] = 1) with H_k^H (a, x)^T = (beta, 0)^T, beta real, annihilates
 //    A[k+2:, k] and makes the subdiagonal real; the trailing block is updated
 //    as A <- H_k^H A H_k = A - v w^H - w v^H with p = tau A v and
@@ -13,7 +13,7 @@
 //      sweep's chain of plane rotations and publishes (cosine, sine) into one
 //      of two buffers;
 //    * warps 1-2: apply each published sweep to the rows of the real
-//      eigenvector matrix Z (FP64), one buffer behind the chain;
+//      eigenvector matrix Z, one buffer behind the chain;
 //    * warps 3-7: form Q explicitly from the stored reflectors (FP64).
 //    Named barriers hand the two rotation buffers back and forth.
 // 3. V = Q Z (FP64, all threads).
@@ -22,10 +22,11 @@
 //
 // On this part a dependent FP64 operation costs about 14 times a FP32 one, and
 // every FP64 warp instruction occupies the FP64 pipe about as long whatever
-// the number of active lanes.  So the one-thread rotation chain, a long run of
-// dependent operations, runs in FP64 only for the FP64 precision; for the
-// others it runs in double-FP32 (an unevaluated sum of two floats, about 48
-// bits) on T scaled by a power of two.  Matrices keep odd row strides (in 8-
+// the number of active lanes.  So steps 1 and 2 run in FP64 only for the FP64
+// precision; for the others the reduction (on A scaled by a power of two),
+// the one-thread rotation chain (on T scaled by a power of two) and the Z
+// rotations run in double-FP32 (an unevaluated sum of two floats, about 48
+// bits), and Q, V = Q Z and step 4 in FP64.  Matrices keep odd row strides (in 8-
 // and 16-byte units) so column walks fall in distinct shared-memory banks, and
 // the reduction's matrix-vector product reads columns (A is Hermitian) split
 // over all warps.
