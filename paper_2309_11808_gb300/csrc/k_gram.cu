@@ -29,6 +29,19 @@ constexpr int kThreads = KSUB * TPG;
 constexpr int kFlushRounds = 64;
 constexpr size_t kGramSimtSmemMax = 227 * 1024;
 
+// Staged row stride: the row quads of a point padded to an odd count, so the
+// 16-byte staging stores of eight consecutive points (one shared-memory
+// phase) start in eight distinct groups of four banks.
+__host__ __device__ constexpr int staged_stride(int nb) { return 4 * (((nb + 3) / 4) | 1); }
+
+__device__ __forceinline__ void store4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // 4-wide shared loads (rows are padded to a multiple of 4)
 __device__ __forceinline__ void load4(const float* p, float* v) {
   const float4 a = *reinterpret_cast<const float4*>(p);
@@ -56,7 +69,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_gram_simt(
   const int s = blockIdx.x;
   const int f = blockIdx.y;
   const int ntl = (nb + 3) / 4;
-  const int RS = 4 * ntl;                       // staged row stride (rows padded with zeros)
+  const int RS = staged_stride(nb);             // staged row stride (rows padded with zeros)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* acc64 = reinterpret_cast<double*>(smem_raw);             // [32][kThreads]
   R* stage = kPromote ? reinterpret_cast<R*>(acc64 + 32 * kThreads)  // [nbuf][re, im][TK][RS]
@@ -84,43 +97,52 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_gram_simt(
   const R* qf = qhat + (int64_t)f * 2 * nb * rs;
   const int nrounds = p1 > p0 ? (int)((p1 - p0 + TK - 1) / TK) : 0;
 
-  // staging: element e of a round = (plane c, row l, point k), point fastest
-  // (coalesced).  Element tid + j * kThreads has point k = tid % TK (fixed per
-  // thread) and staged row tid / TK + j * (kThreads / TK) < 2 RS, so its plane
-  // and row follow from one comparison (no division in the round loop).
-  constexpr int kMaxPer = (2 * 64 * TK + kThreads - 1) / kThreads;   // nb <= 64
-  constexpr int kRowStep = kThreads / TK;
-  const int k_th = tid % TK, row_th = tid / TK;
-  R pre[kMaxPer];
+  // staging: item e of a round = (plane c, row quad u, point k), point
+  // fastest: each thread loads the quad's four rows at its point (coalesced
+  // over the warp's points) and stores them as one 16-byte (FP64: two)
+  // shared store at [c][k][4u].  Items past the prefetched ones (nb > 64) are
+  // copied directly.
+  const int nq = 2 * ntl;                       // row quads of both planes
+  constexpr int kMaxItems = (2 * 16 * TK + kThreads - 1) / kThreads;
+  R pre[kMaxItems][4];
+  auto item = [&](int it, int& k, int& c, int& u) {
+    k = it % TK;
+    const int qd = it / TK;
+    c = qd >= ntl ? 1 : 0;
+    u = qd - c * ntl;
+    return qd < nq;
+  };
   auto fetch = [&](int r) {
     const int64_t pb = p0 + (int64_t)r * TK;
-    const bool kin = pb + k_th < p1;
-    const R* src = qf + pb + k_th;
 #pragma unroll
-    for (int j = 0; j < kMaxPer; ++j) {
-      const int row = row_th + j * kRowStep;
-      const int c = row >= RS ? 1 : 0, l = row - c * RS;
-      R v = 0;
-      if (row < 2 * RS && l < nb && kin) v = src[((int64_t)c * nb + l) * rs];
-      pre[j] = v;
+    for (int j = 0; j < kMaxItems; ++j) {
+      int k, c, u;
+      const bool in = item(tid + j * kThreads, k, c, u) && pb + k < p1;
+      const R* src = qf + pb + k;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int l = 4 * u + e;
+        pre[j][e] = (in && l < nb) ? src[((int64_t)c * nb + l) * rs] : R(0);
+      }
     }
   };
   auto put = [&](int b, int r) {
     R* st = stage + b * buf_elems;
 #pragma unroll
-    for (int j = 0; j < kMaxPer; ++j) {
-      const int row = row_th + j * kRowStep;
-      const int c = row >= RS ? 1 : 0, l = row - c * RS;
-      if (row < 2 * RS) st[c * TK * RS + k_th * RS + l] = pre[j];
+    for (int j = 0; j < kMaxItems; ++j) {
+      int k, c, u;
+      if (item(tid + j * kThreads, k, c, u)) store4(st + c * TK * RS + k * RS + 4 * u, pre[j]);
     }
-    // rows beyond the prefetched ones (nb > 64) are copied directly
     const int64_t pb = p0 + (int64_t)r * TK;
-    for (int idx = kMaxPer * kThreads + tid; idx < buf_elems; idx += kThreads) {
-      const int row = idx / TK, k = idx - row * TK;
-      const int c = row / RS, l = row - c * RS;
-      R v = 0;
-      if (l < nb && pb + k < p1) v = qf[((int64_t)c * nb + l) * rs + pb + k];
-      st[c * TK * RS + k * RS + l] = v;
+    for (int it = kMaxItems * kThreads + tid; it < nq * TK; it += kThreads) {
+      int k, c, u;
+      item(it, k, c, u);
+      R v[4];
+      for (int e = 0; e < 4; ++e) {
+        const int l = 4 * u + e;
+        v[e] = (l < nb && pb + k < p1) ? qf[((int64_t)c * nb + l) * rs + pb + k] : R(0);
+      }
+      store4(st + c * TK * RS + k * RS + 4 * u, v);
     }
   };
 
@@ -248,7 +270,7 @@ __global__ void k_gram_sum_parts(const double* __restrict__ parts, int nparts, i
 // Staging buffers (two when they fit) and shared bytes for element size rb.
 int gram_simt_nbuf(int nb, size_t rb, size_t* smem_out) {
   const size_t acc = sizeof(double) * 32 * kThreads;
-  const size_t buf = 2 * (size_t)TK * 4 * ((nb + 3) / 4) * rb;
+  const size_t buf = 2 * (size_t)TK * staged_stride(nb) * rb;
   auto total = [&](int n) { return rb == 4 ? acc + n * buf : std::max(acc, n * buf); };
   const int nbuf = total(2) <= kGramSimtSmemMax ? 2 : 1;
   *smem_out = total(nbuf);
