@@ -318,14 +318,46 @@ cudaError_t launch_mode_coeffs(const spod_plan_s& p, int nmodes, cudaStream_t s)
   return cudaGetLastError();
 }
 
+#ifndef SPOD_MODES_KGMAX
+#define SPOD_MODES_KGMAX 16
+#endif
+// Modes per group of the FP32 kernel: the fewest groups of at most
+// SPOD_MODES_KGMAX modes, split evenly (38 modes: 13 + 13 + 12 instead of
+// 16 + 16 + 6 with six idle slots of the last group's FMAs per point).
+template <typename R, int KG>
+static cudaError_t modes_kernel(void (**kern)(const R*, int64_t, int, int, int, int64_t, int64_t, int64_t, const R*,
+                                              const R*, R*, int, int64_t, int64_t)) {
+  *kern = k_modes_simt<R, KG>;
+  return cudaSuccess;
+}
+
 template <typename R>
 static cudaError_t launch_modes_t(const spod_plan_s& p, int64_t m0, int64_t mcount, int nmodes, void* d_Phi,
                                   cudaStream_t s, int* nlaunch, bool adjoint, int f0, int f1, int64_t qoff,
                                   int64_t out_ld, int64_t out_off) {
-  constexpr int KG = sizeof(R) == 8 ? 8 : 16;
+  void (*kern)(const R*, int64_t, int, int, int, int64_t, int64_t, int64_t, const R*, const R*, R*, int, int64_t,
+               int64_t) = nullptr;
+  int KG = 8;
+  if constexpr (sizeof(R) == 8) {
+    modes_kernel<R, 8>(&kern);
+  } else {
+    const int groups = (nmodes + SPOD_MODES_KGMAX - 1) / SPOD_MODES_KGMAX;
+    const int need = (nmodes + groups - 1) / groups;
+    constexpr int kChoices[] = {4, 8, 10, 13, 16, 20};
+    KG = SPOD_MODES_KGMAX;
+    for (int c : kChoices)
+      if (c >= need && c <= SPOD_MODES_KGMAX) { KG = c; break; }
+    switch (KG) {
+      case 4: modes_kernel<R, 4>(&kern); break;
+      case 8: modes_kernel<R, 8>(&kern); break;
+      case 10: modes_kernel<R, 10>(&kern); break;
+      case 13: modes_kernel<R, 13>(&kern); break;
+      case 16: modes_kernel<R, 16>(&kern); break;
+      default: modes_kernel<R, SPOD_MODES_KGMAX>(&kern); KG = SPOD_MODES_KGMAX; break;
+    }
+  }
   const int nmp = (nmodes + KG - 1) / KG * KG;
   const size_t smem = sizeof(typename Cplx<R>::T) * (size_t)p.nb * nmp;
-  auto kern = k_modes_simt<R, KG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   constexpr int threads = 128;
