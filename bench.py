@@ -512,8 +512,8 @@ TRAFFIC = {
     ("fft", "bf16x3"): int((497.484032 + 923.243520) * 1e6 * 32),    # k_fft_pipe<float, 1, 32, 512> (two-pass, mean inside)
     ("gram", "bf16x3"): int((979.395584 + 19.955456) * 1e6 * 32),    # k_gram_tc<1, 40> (packed Kahan drains, rho row)
     ("modes", "bf16x3"): int((996.140800 + 908.134400) * 1e6 * 32),  # k_modes_tc<1> (rho row, scales before the wait)
-    ("gram", "fp32"): int((961.233 + 25.105920) * 1e6 * 32),         # k_gram_simt<float>
-    # k_modes_simt changed (frequency range, Phi view) after its capture: no entry
+    ("gram", "fp32"): int((961.185 + 24.225792) * 1e6 * 32),         # k_gram_simt<float> (quad staging)
+    ("modes", "fp32"): int((1017.999 + 917.710336) * 1e6 * 32),      # k_modes_simt<float, 13>
 }
 
 
